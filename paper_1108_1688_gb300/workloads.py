@@ -1,0 +1,192 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only draws and lays out parameters (curves, model constants, grid
+specifications, instruments). It contains none of the pricing arithmetic, so
+both the GPU library and the CPU oracle can be fed from it.
+
+Every item is a plain dict with four parts, mirroring the paper's statement of
+the problem:
+  curve : initial forward curve f(0,t) (Section 2). kind 0 = flat,
+          kind 1 = Nelson-Siegel forward form
+          f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}.
+  model : kappa, lambda, gamma, theta, epsilon, rho, v0 (Section 3.1).
+  grid  : node counts n_r x n_y x n_v, steps, physical domain, sinh metric
+          (Section 4.3 / 7.1) and scheme options (Section 5).
+  inst  : kind 0 = zero-coupon bond, kind 1 = caplet (Section 3.2). For a
+          caplet, strike_atm_relative = 1 means K is an offset from the ATM
+          forward rate, which each side computes from the curve itself.
+
+Domain recipe (the paper's rescaled values in Section 7.1 disagree with its
+figure captions, so the domain is set from the model's scales instead):
+  r in [min(0, -fb - W_r), fb + W_r], W_r = 7 lambda sqrt(v_max T), fb a
+      bound on |f(0,t)| (gamma = 0); r in [0, fb + W_r] when gamma > 0, with
+      lambda replaced by lambda (2 fb)^gamma here and in y;
+  v in [0, max(5, 1 + 10 epsilon / sqrt(2 theta))];
+  y in [0, 4 lambda^2 v_max (1 - e^{-2 kappa T}) / (2 kappa)] (T lambda^2 v_max
+      times 4 when kappa = 0);
+  sinh metric: centre in r at the strike (bond: at f(0,0)), in v at 1, in y at
+      0; width alpha = a fraction of each axis length.
+"""
+from __future__ import annotations
+
+import copy
+import math
+
+import numpy as np
+
+SEED_BASE = 1108000
+
+CONFIG1_MODEL = dict(kappa=0.1, lambda_=0.01, gamma=0.0, theta=1.0, epsilon=0.3,
+                     rho=-0.3, v0=1.0)
+
+# Metric widths as fractions of the axis length.
+ALPHA_FRAC_R = 0.25
+ALPHA_FRAC_V = 0.25
+ALPHA_FRAC_Y = 0.25
+
+
+def flat_curve(rate):
+    return dict(kind=0, flat_rate=float(rate), beta0=0.0, beta1=0.0, beta2=0.0, tau=1.0)
+
+
+def ns_curve(beta0, beta1, beta2, tau):
+    return dict(kind=1, flat_rate=0.0, beta0=float(beta0), beta1=float(beta1),
+                beta2=float(beta2), tau=float(tau))
+
+
+def model(kappa, lambda_, gamma, theta, epsilon, rho, v0=1.0):
+    return dict(kappa=float(kappa), lambda_=float(lambda_), gamma=float(gamma),
+                theta=float(theta), epsilon=float(epsilon), rho=float(rho), v0=float(v0))
+
+
+def bond(T):
+    return dict(kind=0, T=float(T), TM=float(T), K=0.0, strike_atm_relative=0)
+
+
+def caplet(T, TM, K=0.0, atm_relative=True):
+    return dict(kind=1, T=float(T), TM=float(TM), K=float(K),
+                strike_atm_relative=1 if atm_relative else 0)
+
+
+def curve_level_bound(curve):
+    """An upper bound on |f(0,t)| read off the parameters (x e^{-x} <= 1/e)."""
+    if curve["kind"] == 0:
+        return abs(curve["flat_rate"])
+    return abs(curve["beta0"]) + abs(curve["beta1"]) + abs(curve["beta2"]) / math.e
+
+
+def default_grid(curve, mdl, T, n_r, n_y, n_v, n_steps, *, r_width_sd=7.0,
+                 alpha_frac=(ALPHA_FRAC_R, ALPHA_FRAC_V, ALPHA_FRAC_Y),
+                 theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0, r_inf=None):
+    """Grid specification following the domain recipe in the module docstring."""
+    kap = mdl["kappa"]
+    v_max = max(5.0, 1.0 + 10.0 * mdl["epsilon"] / math.sqrt(2.0 * max(mdl["theta"], 1e-12)))
+    fb = curve_level_bound(curve)
+    # Normal volatility scale: lambda r^gamma taken at r = 2 fb when gamma > 0.
+    lam = mdl["lambda_"] * ((2.0 * fb) ** mdl["gamma"] if mdl["gamma"] > 0.0 else 1.0)
+    w_r = r_width_sd * lam * math.sqrt(v_max * T)
+    if mdl["gamma"] == 0.0:
+        r_min, r_max = min(0.0, -fb - w_r), fb + w_r
+    else:
+        r_min, r_max = 0.0, (r_inf if r_inf is not None else fb + w_r)
+    if kap > 0.0:
+        y_max = 4.0 * lam * lam * v_max * (-math.expm1(-2.0 * kap * T)) / (2.0 * kap)
+    else:
+        y_max = 4.0 * lam * lam * v_max * T
+    y_max = max(y_max, 1e-12)
+    return dict(n_r=int(n_r), n_y=int(n_y), n_v=int(n_v), n_steps=int(n_steps),
+                r_min=r_min, r_max=r_max, y_max=y_max, v_max=v_max,
+                alpha_r=alpha_frac[0] * (r_max - r_min),
+                alpha_v=alpha_frac[1] * v_max,
+                alpha_y=alpha_frac[2] * y_max,
+                k_r=0.0, k_v=1.0, center_r_on_strike=1,
+                theta_adi=float(theta_adi), y_boundary_order=int(y_boundary_order),
+                explicit_midpoint=int(explicit_midpoint))
+
+
+def item(curve, mdl, grid, inst):
+    return dict(curve=curve, model=mdl, grid=grid, inst=inst)
+
+
+def config1():
+    """5y zero-coupon bond, 40 x 20 x 20 (r x y x v), 100 steps, flat 3% forward,
+    kappa 0.1, lambda 0.01, theta 1, epsilon 0.3, rho -0.3, gamma 0. The exact
+    price is exp(-0.15)."""
+    c = flat_curve(0.03)
+    m = model(**CONFIG1_MODEL)
+    g = default_grid(c, m, 5.0, 40, 20, 20, 100)
+    return item(c, m, g, bond(5.0))
+
+
+def _ns_draw(rng):
+    return ns_curve(rng.uniform(0.02, 0.05), rng.uniform(-0.02, 0.02),
+                    rng.uniform(-0.02, 0.02), rng.uniform(1.0, 5.0))
+
+
+def config2_draws(n=100, seed=SEED_BASE + 2, n_r=128, n_y=64, n_v=64, n_steps=400):
+    """Seeded 5y-into-6m ATM caplets on 128 x 64 x 64 with 400 steps: Nelson-Siegel
+    curve (beta0 U[0.02,0.05], beta1, beta2 U[-0.02,0.02], tau U[1,5]),
+    epsilon U[0.1,0.6], rho U[-0.7,0.3]; kappa, lambda, theta as in config1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        c = _ns_draw(rng)
+        eps = rng.uniform(0.1, 0.6)
+        rho = rng.uniform(-0.7, 0.3)
+        m = model(CONFIG1_MODEL["kappa"], CONFIG1_MODEL["lambda_"], 0.0,
+                  CONFIG1_MODEL["theta"], eps, rho, 1.0)
+        g = default_grid(c, m, 5.0, n_r, n_y, n_v, n_steps)
+        out.append(item(c, m, g, caplet(5.0, 5.5, 0.0, True)))
+    return out
+
+
+def config3_batch(n=256, seed=SEED_BASE + 3, sizes=(64, 96, 128, 160, 192, 224, 256)):
+    """256 caplets with expiry U{1..10}, T_M = T + 0.5, strike ATM + U[-0.02, 0.02],
+    per-caplet curve and epsilon, rho as in config2, grids n_r in `sizes`,
+    n_y = n_v = n_r / 2, steps = 2 n_r."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        c = _ns_draw(rng)
+        eps = rng.uniform(0.1, 0.6)
+        rho = rng.uniform(-0.7, 0.3)
+        T = float(rng.integers(1, 11))
+        dk = rng.uniform(-0.02, 0.02)
+        nr = int(sizes[rng.integers(0, len(sizes))])
+        m = model(CONFIG1_MODEL["kappa"], CONFIG1_MODEL["lambda_"], 0.0,
+                  CONFIG1_MODEL["theta"], eps, rho, 1.0)
+        g = default_grid(c, m, T, nr, nr // 2, nr // 2, 2 * nr)
+        out.append(item(c, m, g, caplet(T, T + 0.5, dk, True)))
+    return out
+
+
+def config4(n_r=512, n_y=256, n_v=256, n_steps=1000):
+    """10y-into-6m ATM caplet on 512 x 256 x 256 with 1000 steps, flat 3%, config1
+    model parameters."""
+    c = flat_curve(0.03)
+    m = model(**CONFIG1_MODEL)
+    g = default_grid(c, m, 10.0, n_r, n_y, n_v, n_steps)
+    return item(c, m, g, caplet(10.0, 10.5, 0.0, True))
+
+
+def paper_2007_set(n_r=40, n_y=20, n_v=20, n_steps=100, T=5.0):
+    """The paper's 2007 market set (Section 3.3): p(0,T) = 1.04^{-T},
+    kappa 0.001, lambda 0.15, gamma 0.9, epsilon 1.5, theta 0.25, rho -0.75."""
+    c = flat_curve(math.log(1.04))
+    m = model(0.001, 0.15, 0.9, 0.25, 1.5, -0.75, 1.0)
+    # First-order y faces: with lambda = 0.15 the Courant number on the y = 0
+    # face exceeds the bound under which second-order faces are stable.
+    g = default_grid(c, m, T, n_r, n_y, n_v, n_steps, y_boundary_order=1)
+    return item(c, m, g, bond(T))
+
+
+def with_grid(it, **kw):
+    """Copy of an item with some grid fields replaced."""
+    out = copy.deepcopy(it)
+    out["grid"].update(kw)
+    return out
+
+
+def point_steps(it):
+    g = it["grid"]
+    return g["n_r"] * g["n_y"] * g["n_v"] * g["n_steps"]

@@ -1,0 +1,656 @@
+"""Pins of the CPU oracle against what the paper and mathematics fix.
+
+The oracle is only trusted because of these tests; none of them compares the
+oracle with itself. Each names the passage of the paper (Valero et al., "Fast
+resolution of a single factor HJM model with stochastic volatility") it
+follows. Together they are chosen so that a plausible mistake anywhere in the
+oracle (a dropped term, a wrong sign or index, a transposed operand) fails at
+least one of them:
+
+  curve, closed forms  discount factor vs quadrature of f (Section 2); G(s) as
+                       an integral (Section 3.1); the bond formula solves the
+                       PDE of Eq. (1) (Sections 3.1, 3.2, 4.1); the Gaussian
+                       caplet vs an independent lognormal quadrature
+  metric               J, J2 vs finite differences of z(xi) (Sections 4.3, 7.1)
+  explicit operator    exact on polynomials of degree <= 2 on uniform grids
+                       against Eq. (1) applied analytically; second order on
+                       sinh grids; A_v U = A_0 U = 0 for v-independent fields
+  implicit rows        interior rows reproduce the explicit operator; face
+                       rows are first-order one-sided differences
+  line solves          equal to a dense LU solve (Section 5, tridiagonal)
+  Douglas step         equal to the dense product of the three inverses
+                       (Section 5.1) on tiny grids (brute force)
+  payoff average       equal to brute-force quadrature (Section 7.2)
+  readout              exact on bicubic polynomials
+  march                bond reproduces P(0,T) within 1e-5 (Sections 4.1, 6.1)
+                       for many volatilities and the gamma = 0.9 set (Section
+                       3.3); Gaussian caplet limit converges to the closed
+                       form; observed space-time order >= 1.8; first- and
+                       second-order y faces agree (Section 7.3); price smooth
+                       in strike after softening (Section 7.2)
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_1108_1688_gb300 import workloads as W
+
+
+# ---------------------------------------------------------------- helpers
+
+def pde_coeffs(m, curve_f, curve_dfdt, t, r, v, y):
+    """Coefficients of Eq. (1), Section 3.2 (zeta(t) read as gamma(t))."""
+    lam, gam, eps, rho, kap, th = (m["lambda_"], m["gamma"], m["epsilon"], m["rho"],
+                                   m["kappa"], m["theta"])
+    rg = 1.0 if gam == 0.0 else r ** gam
+    return dict(
+        zrr=0.5 * lam ** 2 * rg ** 2 * v,
+        zvv=0.5 * eps ** 2 * v,
+        zrv=lam * rg * eps * rho * v,
+        mur=curve_dfdt(t) - kap * (r - curve_f(t)) + y,
+        muv=th * (1.0 - v),
+        muy=lam ** 2 * rg ** 2 * v - 2.0 * kap * y,
+    )
+
+
+def small_item(n_r=9, n_y=8, n_v=7, n_steps=10, uniform=True, gamma=0.0, kind=0,
+               curve=None, rho=-0.4, eps=0.5, T=2.0):
+    c = curve or W.ns_curve(0.03, -0.01, 0.015, 2.0)
+    m = W.model(0.12, 0.02 if gamma == 0 else 0.15, gamma, 0.8, eps, rho)
+    g = W.default_grid(c, m, T, n_r, n_y, n_v, n_steps)
+    if uniform:
+        g.update(alpha_r=0.0, alpha_v=0.0, alpha_y=0.0)
+    inst = W.bond(T) if kind == 0 else W.caplet(T, T + 0.5, 0.002, True)
+    return W.item(c, m, g, inst)
+
+
+def fields(X):
+    r, _, _ = X.axis(0)
+    v, _, _ = X.axis(1)
+    y, _, _ = X.axis(2)
+    Y, V, R = np.meshgrid(y, v, r, indexing="ij")
+    return R, V, Y
+
+
+# ------------------------------------------------------- curve and closed forms
+
+@pytest.mark.parametrize("curve", [W.flat_curve(0.03), W.ns_curve(0.03, -0.01, 0.015, 2.0),
+                                   W.ns_curve(0.045, 0.02, -0.02, 4.5)])
+def test_discount_is_exp_minus_integral_of_forward(orc, curve):
+    # Section 2: p(0,T) = exp(-int_0^T f(0,s) ds), f = -d ln p / dT.
+    for T in (0.5, 3.0, 10.0):
+        I, _ = integrate.quad(lambda s: orc.curve_f(curve, s), 0.0, T, epsabs=1e-14)
+        assert orc.curve_P(curve, T) == pytest.approx(math.exp(-I), rel=1e-12)
+        h = 1e-5
+        fd = -(math.log(orc.curve_P(curve, T + h)) - math.log(orc.curve_P(curve, T - h))) / (2 * h)
+        assert fd == pytest.approx(orc.curve_f(curve, T), abs=1e-9)
+        dfd = (orc.curve_f(curve, T + h) - orc.curve_f(curve, T - h)) / (2 * h)
+        assert orc.curve_dfdt(curve, T) == pytest.approx(dfd, abs=1e-9)
+
+
+def test_G_is_integral_of_decay(orc):
+    # Section 3.1: G(s) = (1 - e^{-kappa s}) / kappa = int_0^s e^{-kappa u} du.
+    for kap in (0.0, 1e-9, 0.001, 0.1, 2.0):
+        for s in (0.25, 1.0, 7.0):
+            I, _ = integrate.quad(lambda u: math.exp(-kap * u), 0.0, s, epsabs=1e-15)
+            assert orc.G(kap, s) == pytest.approx(I, rel=1e-10)
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.9])
+def test_bond_formula_solves_the_pde(orc, gamma):
+    # Sections 3.1-3.2 and 4.1: the affine bond price solves Eq. (1) with
+    # terminal value 1, for any volatility (it does not depend on v).
+    c = W.ns_curve(0.035, -0.012, 0.02, 2.5)
+    m = W.model(0.15, 0.02 if gamma == 0 else 0.15, gamma, 0.7, 0.4, -0.5)
+    T = 6.0
+    f = lambda t: orc.curve_f(c, t)
+    dfdt = lambda t: orc.curve_dfdt(c, t)
+    C = lambda t, r, y: orc.bond(c, m, t, T, r, y)
+    assert C(T, 0.07, 0.003) == pytest.approx(1.0, abs=1e-15)
+    assert C(0.0, f(0.0), 0.0) == pytest.approx(orc.curve_P(c, T), rel=1e-14)
+    for (t, r, y, v) in [(0.5, 0.02, 0.001, 1.0), (2.0, 0.06, 0.004, 2.5), (4.0, 0.01, 0.0, 0.3)]:
+        q = pde_coeffs(m, f, dfdt, t, r, v, y)
+        ht, hr, hy = 1e-4, 1e-4, 1e-5
+        Ct = (C(t + ht, r, y) - C(t - ht, r, y)) / (2 * ht)
+        Cr = (C(t, r + hr, y) - C(t, r - hr, y)) / (2 * hr)
+        Crr = (C(t, r + hr, y) - 2 * C(t, r, y) + C(t, r - hr, y)) / hr ** 2
+        Cy = (C(t, r, y + hy) - C(t, r, y - hy)) / (2 * hy)
+        res = Ct + q["zrr"] * Crr + q["mur"] * Cr + q["muy"] * Cy - r * C(t, r, y)
+        assert abs(res) < 1e-6 * C(t, r, y)
+
+
+def test_gaussian_caplet_matches_lognormal_quadrature(orc):
+    # With gamma = 0, epsilon = 0, v = 1 the factor x(T) is Gaussian; under the
+    # T-forward measure E[p(T,T_M)] = P(0,T_M)/P(0,T) and ln p(T,T_M) has
+    # variance G(T_M-T)^2 Var x(T), Var x(T) = int_0^T lambda^2 e^{-2 kappa (T-s)} ds.
+    # The caplet pays max(1 - Delta_M p(T,T_M), 0) at T (Section 3.2).
+    for curve in (W.flat_curve(0.03), W.ns_curve(0.04, -0.015, 0.01, 3.0)):
+        m = W.model(0.1, 0.01, 0.0, 1.0, 0.0, 0.0)
+        for T, TM, dK in [(5.0, 5.5, 0.0), (2.0, 2.25, 0.01), (8.0, 9.0, -0.005)]:
+            K = orc.atm_strike(curve, T, TM) + dK
+            DM = 1.0 + (TM - T) * K
+            var_x, _ = integrate.quad(lambda s: m["lambda_"] ** 2 * math.exp(-2 * m["kappa"] * (T - s)), 0, T)
+            sig = orc.G(m["kappa"], TM - T) * math.sqrt(var_x)
+            fwd = orc.curve_P(curve, TM) / orc.curve_P(curve, T)
+            mu = math.log(fwd) - 0.5 * sig ** 2
+            pay = lambda z: max(1.0 - DM * math.exp(mu + sig * z), 0.0) * math.exp(-0.5 * z * z) / math.sqrt(2 * math.pi)
+            zk = (math.log(1.0 / DM) - mu) / sig  # payoff is positive below zk
+            E, _ = integrate.quad(pay, -12.0, zk, epsabs=1e-15, epsrel=1e-13)
+            exact = orc.curve_P(curve, T) * E
+            assert orc.gauss_caplet(curve, m, T, TM, K) == pytest.approx(exact, rel=1e-9, abs=1e-15)
+
+
+def test_atm_strike_is_simple_forward(orc):
+    c = W.ns_curve(0.03, -0.01, 0.015, 2.0)
+    K = orc.atm_strike(c, 3.0, 3.5)
+    # ATM: 1 + delta K = P(0,T)/P(0,T_M).
+    assert 1.0 + 0.5 * K == pytest.approx(orc.curve_P(c, 3.0) / orc.curve_P(c, 3.5), rel=1e-15)
+
+
+# ------------------------------------------------------------------ metric
+
+def test_metric_jacobians_are_derivatives_of_the_map(orc):
+    # Section 4.3: z = K + alpha sinh(c2 xi + c1 (1 - xi)); J = dz/dxi,
+    # J2 = d2z/dxi2 (Section 7.1 prints sinh for J; the derivative is cosh).
+    it = small_item(n_r=2001, n_y=1501, n_v=1801, uniform=False)
+    with orc.Ctx(it) as X:
+        g = it["grid"]
+        for axis, lo, hi in [(0, g["r_min"], g["r_max"]), (1, 0.0, g["v_max"]), (2, 0.0, g["y_max"])]:
+            z, J, J2 = X.axis(axis)
+            n = len(z)
+            h = 1.0 / (n - 1)
+            assert z[0] == pytest.approx(lo, abs=1e-12 * (hi - lo))
+            assert z[-1] == pytest.approx(hi, rel=1e-12)
+            assert np.all(np.diff(z) > 0)
+            fdJ = (z[2:] - z[:-2]) / (2 * h)
+            fdJ2 = (J[2:] - J[:-2]) / (2 * h)
+            assert np.max(np.abs(fdJ - J[1:-1])) < 1e-5 * np.max(np.abs(J))
+            assert np.max(np.abs(fdJ2 - J2[1:-1])) < 1e-5 * np.max(np.abs(J2))
+    it = small_item(uniform=True)
+    with orc.Ctx(it) as X:
+        z, J, J2 = X.axis(0)
+        g = it["grid"]
+        assert np.allclose(J, g["r_max"] - g["r_min"], rtol=1e-15) and np.all(J2 == 0.0)
+        assert np.allclose(z, np.linspace(g["r_min"], g["r_max"], len(z)), rtol=0, atol=1e-15)
+
+
+# -------------------------------------------------------- explicit operator
+
+def poly_cases():
+    # U and its derivatives (U_r, U_rr, U_v, U_vv, U_rv, U_y).
+    return {
+        "r": (lambda R, V, Y: R, lambda R, V, Y: (1 + 0 * R, 0 * R, 0 * R, 0 * R, 0 * R, 0 * R)),
+        "r2": (lambda R, V, Y: R * R, lambda R, V, Y: (2 * R, 2 + 0 * R, 0 * R, 0 * R, 0 * R, 0 * R)),
+        "v": (lambda R, V, Y: V, lambda R, V, Y: (0 * R, 0 * R, 1 + 0 * R, 0 * R, 0 * R, 0 * R)),
+        "v2": (lambda R, V, Y: V * V, lambda R, V, Y: (0 * R, 0 * R, 2 * V, 2 + 0 * R, 0 * R, 0 * R)),
+        "y": (lambda R, V, Y: Y, lambda R, V, Y: (0 * R, 0 * R, 0 * R, 0 * R, 0 * R, 1 + 0 * R)),
+        "y2": (lambda R, V, Y: Y * Y, lambda R, V, Y: (0 * R, 0 * R, 0 * R, 0 * R, 0 * R, 2 * Y)),
+        "rv": (lambda R, V, Y: R * V, lambda R, V, Y: (V, 0 * R, R, 0 * R, 1 + 0 * R, 0 * R)),
+        "mix": (lambda R, V, Y: 3 * R * R - 2 * R * V + V * V - 5 * Y + 7 * R * Y,
+                lambda R, V, Y: (6 * R - 2 * V + 7 * Y, 6 + 0 * R, -2 * R + 2 * V, 2 + 0 * R,
+                                 -2 + 0 * R, -5 + 7 * R)),
+    }
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.9])
+@pytest.mark.parametrize("name", list(poly_cases()))
+def test_operator_exact_on_quadratics(orc, gamma, name):
+    # Section 5: centred differences are exact on polynomials of degree <= 2 on a
+    # uniform grid, so each split operator must equal Eq. (1)'s terms applied
+    # analytically. Degenerate faces (reading R8): physical second derivative
+    # and mixed term dropped, second-order one-sided first derivative (exact
+    # for degree <= 2).
+    it = small_item(n_r=9, n_y=8, n_v=7, gamma=gamma, uniform=True)
+    Uf, dU = poly_cases()[name]
+    with orc.Ctx(it) as X:
+        R, V, Y = fields(X)
+        U = Uf(R, V, Y)
+        Ur, Urr, Uv, Uvv, Urv, Uy = dU(R, V, Y)
+        c = it["curve"]
+        t = 0.7
+        q = pde_coeffs(it["model"], lambda s: orc.curve_f(c, s), lambda s: orc.curve_dfdt(c, s), t, R, V, Y)
+        nr, nv = X.n[0], X.n[1]
+        i = np.arange(nr)[None, None, :]
+        k = np.arange(nv)[None, :, None]
+        r_int = (i > 0) & (i < nr - 1)
+        v_int = (k > 0) & (k < nv - 1)
+        dirichlet = (i == nr - 1) | ((i == 0) & (gamma == 0.0))
+        expect = {
+            0: np.where(r_int, q["zrr"] * Urr, 0.0) + q["mur"] * Ur - R * U,
+            1: np.where(v_int, q["zvv"] * Uvv, 0.0) + q["muv"] * Uv,
+            2: q["muy"] * Uy,
+            3: np.where(r_int & v_int, q["zrv"] * Urv, 0.0),
+        }
+        scale = np.max(np.abs(U)) + 1.0
+        total = 0.0
+        for d in range(4):
+            got = X.apply_dir(d, t, U)
+            want = np.where(dirichlet, 0.0, np.broadcast_to(expect[d], U.shape))
+            assert np.max(np.abs(got - want)) < 1e-11 * scale * (1 + np.max(np.abs(want))), (d, name)
+            total = total + got
+        assert np.allclose(X.apply_F(t, U), total, rtol=0, atol=1e-13 * scale)
+
+
+def test_operator_second_order_on_sinh_grid(orc):
+    # Section 4.3: with the metric transforms g1..g6 the centred operator is
+    # second order on a stretched grid. Errors at interior nodes must fall by
+    # ~4 per refinement.
+    def U_and_L(X, it, t):
+        R, V, Y = fields(X)
+        a, b, cc, d = 8.0, 0.3, 0.05, -20.0
+        E = np.exp(-a * R)
+        Pv = 1 + b * V + cc * V * V
+        Qy = 1 + d * Y
+        U = E * Pv * Qy
+        Ur, Urr = -a * U, a * a * U
+        Uv, Uvv = E * (b + 2 * cc * V) * Qy, E * 2 * cc * Qy
+        Urv = -a * Uv
+        Uy = E * Pv * d
+        c = it["curve"]
+        q = pde_coeffs(it["model"], lambda s: orc.curve_f(c, s), lambda s: orc.curve_dfdt(c, s), t, R, V, Y)
+        L = [q["zrr"] * Urr + q["mur"] * Ur - R * U, q["zvv"] * Uvv + q["muv"] * Uv,
+             q["muy"] * Uy, q["zrv"] * Urv]
+        return U, L
+
+    errs = []
+    for s in (1, 2, 4):
+        it = small_item(n_r=12 * s, n_y=10 * s, n_v=11 * s, uniform=False)
+        with orc.Ctx(it) as X:
+            U, L = U_and_L(X, it, 0.4)
+            e = []
+            for d in range(4):
+                got = X.apply_dir(d, 0.4, U)
+                sl = (slice(1, -1), slice(1, -1), slice(1, -1))
+                e.append(np.max(np.abs(got[sl] - L[d][sl])) / np.max(np.abs(L[d][sl])))
+            errs.append(e)
+    errs = np.array(errs)
+    order = np.log2(errs[1] / errs[2])
+    assert np.all(order > 1.8), (errs, order)
+
+
+def test_v_independent_field_has_no_v_or_mixed_terms(orc):
+    # The bond price does not depend on v (Section 3.2); the discrete v and
+    # mixed operators of such a field vanish identically.
+    it = small_item(n_r=11, n_y=9, n_v=8, uniform=False)
+    rng = np.random.default_rng(5)
+    with orc.Ctx(it) as X:
+        base = rng.standard_normal((X.n[2], 1, X.n[0]))
+        U = np.repeat(base, X.n[1], axis=1)
+        assert np.max(np.abs(X.apply_dir(1, 0.3, U))) <= 1e-14
+        assert np.max(np.abs(X.apply_dir(3, 0.3, U))) <= 1e-14
+
+
+# ---------------------------------------------------- implicit rows, solves
+
+def _line_apply(X, d, t, U):
+    """(A_d U) built from the tridiagonal rows: (I - M) U / (theta dt)."""
+    w = X.item["grid"]["theta_adi"] * X.dt
+    out = np.zeros_like(U)
+    nr, nv, ny = X.n[0], X.n[1], X.n[2]
+    Ul = np.moveaxis(U, {0: 2, 1: 1, 2: 0}[d], -1)  # lines last
+    Ol = np.moveaxis(out, {0: 2, 1: 1, 2: 0}[d], -1)
+    lines = Ul.reshape(-1, X.n[d])
+    olines = Ol.reshape(-1, X.n[d])
+    other = {0: (nv, ny), 1: (nr, ny), 2: (nr, nv)}[d]
+    for a in range(lines.shape[0]):
+        # line index: lower other axis fastest
+        if d == 0:
+            j, k = divmod(a, nv); line = k + nv * j
+        elif d == 1:
+            j, i = divmod(a, nr); line = i + nr * j
+        else:
+            k, i = divmod(a, nr); line = i + nr * k
+        sub, dia, sup = X.line_matrix(d, t, line)
+        M = np.diag(dia) + np.diag(sub[1:], -1) + np.diag(sup[:-1], 1)
+        olines[a] = (lines[a] - M @ lines[a]) / w
+    del other
+    return np.moveaxis(olines.reshape(Ol.shape), -1, {0: 2, 1: 1, 2: 0}[d])
+
+
+@pytest.mark.parametrize("gamma", [0.0, 0.9])
+def test_implicit_rows_reproduce_operator(orc, gamma):
+    # Section 5: L_r, L_v, L_y are the tridiagonal parts of F. In the interior
+    # they must reproduce F's split operators; on degenerate faces they use
+    # the first-order one-sided difference (reading R8), exact for linear U.
+    it = small_item(n_r=10, n_y=9, n_v=8, gamma=gamma, uniform=False)
+    rng = np.random.default_rng(1)
+    with orc.Ctx(it) as X:
+        t = 1.1
+        U = rng.standard_normal(X.shape)
+        for d in range(3):
+            got = _line_apply(X, d, t, U)
+            want = X.apply_dir(d, t, U)
+            sl = [slice(None)] * 3
+            sl[{0: 2, 1: 1, 2: 0}[d]] = slice(1, -1)
+            assert np.allclose(got[tuple(sl)], want[tuple(sl)], rtol=1e-10, atol=1e-10 * np.max(np.abs(want)))
+    # Fields linear in the grid coordinate: faces agree too (first- and
+    # second-order one-sided differences are both exact there).
+    it = small_item(n_r=10, n_y=9, n_v=8, gamma=gamma, uniform=True)
+    with orc.Ctx(it) as X:
+        R, V, Y = fields(X)
+        for d, Ulin in [(0, 2.0 * R + 1.0), (1, 3.0 * V - 1.0), (2, 5.0 * Y + 2.0)]:
+            got = _line_apply(X, d, 1.1, Ulin)
+            want = X.apply_dir(d, 1.1, Ulin)
+            assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * np.max(np.abs(want))), d
+
+
+@pytest.mark.parametrize("d", [0, 1, 2])
+def test_line_solves_equal_dense_lu(orc, d):
+    # Section 5: each directional system is tridiagonal; the Thomas solution
+    # must equal a dense LU solve.
+    it = small_item(n_r=13, n_y=9, n_v=11, uniform=False, kind=1)
+    rng = np.random.default_rng(2 + d)
+    with orc.Ctx(it) as X:
+        t = X.time(3.5)
+        rhs = rng.standard_normal(X.shape)
+        out, bad = X.solve_dir(d, t, rhs, return_bad=True)
+        assert bad == 0
+        nr, nv, ny = X.n[0], X.n[1], X.n[2]
+        nl = {0: nv * ny, 1: nr * ny, 2: nr * nv}[d]
+        for line in range(nl):
+            sub, dia, sup = X.line_matrix(d, t, line)
+            M = np.diag(dia) + np.diag(sub[1:], -1) + np.diag(sup[:-1], 1)
+            if d == 0:
+                k, j = line % nv, line // nv
+                idx = (j, k, slice(None))
+            elif d == 1:
+                i, j = line % nr, line // nr
+                idx = (j, slice(None), i)
+            else:
+                i, k = line % nr, line // nr
+                idx = (slice(None), k, i)
+            x = np.linalg.solve(M, rhs[idx])
+            assert np.allclose(out[idx], x, rtol=1e-12, atol=1e-12 * np.max(np.abs(x)))
+
+
+def _dense(X, d, t):
+    nr, nv, ny = X.n[0], X.n[1], X.n[2]
+    N = nr * nv * ny
+    M = np.zeros((N, N))
+    nl = {0: nv * ny, 1: nr * ny, 2: nr * nv}[d]
+    for line in range(nl):
+        sub, dia, sup = X.line_matrix(d, t, line)
+        for p in range(X.n[d]):
+            if d == 0:
+                i, k, j = p, line % nv, line // nv
+            elif d == 1:
+                i, k, j = line % nr, p, line // nr
+            else:
+                i, k, j = line % nr, line // nr, p
+            row = i + nr * (k + nv * j)
+            step = {0: 1, 1: nr, 2: nr * nv}[d]
+            M[row, row] = dia[p]
+            if p > 0:
+                M[row, row - step] = sub[p]
+            if p < X.n[d] - 1:
+                M[row, row + step] = sup[p]
+    return M
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_douglas_step_equals_dense_product(orc, kind):
+    # Section 5.1: dU0 = dt F(U^n); three directional solves; U^{n+1} = U^n + dU3,
+    # checked by brute force with dense matrices on a tiny grid.
+    it = small_item(n_r=6, n_y=5, n_v=7, n_steps=4, uniform=False, kind=kind)
+    rng = np.random.default_rng(7)
+    with orc.Ctx(it) as X:
+        n = 2
+        U = X.terminal() + 0.01 * rng.standard_normal(X.shape)
+        dU0 = X.explicit(n, U)
+        # explicit stage: dt F at t^n off Dirichlet faces, g(t^{n+1}) - U on them
+        F = X.apply_F(X.time(n), U)
+        r, _, _ = X.axis(0)
+        y, _, _ = X.axis(2)
+        want = X.dt * F
+        for j in range(X.n[2]):
+            for i in (0, X.n[0] - 1):
+                want[j, :, i] = X.dirichlet(X.time(n + 1), r[i], y[j]) - U[j, :, i]
+        assert np.allclose(dU0, want, rtol=1e-13, atol=1e-15)
+        th = X.time(n + 0.5)
+        v = dU0.reshape(-1)
+        for d in range(3):
+            v = np.linalg.solve(_dense(X, d, th), v)
+        expect = U + v.reshape(X.shape)
+        assert np.allclose(X.step(n, U), expect, rtol=1e-12, atol=1e-14)
+
+
+def test_dirichlet_data(orc):
+    # Reading R8: bond faces carry the exact bond; caplet faces carry
+    # max(P(t,T) - Delta_M P(t,T_M), 0), which is the payoff at t = T.
+    it = small_item(kind=1, uniform=False)
+    with orc.Ctx(it) as X:
+        c, m = it["curve"], it["model"]
+        T, TM = it["inst"]["T"], it["inst"]["TM"]
+        DM = 1.0 + (TM - T) * X.strike
+        for (t, r, y) in [(0.3, 0.1, 0.001), (1.5, -0.05, 0.0), (T, 0.02, 0.002)]:
+            want = max(orc.bond(c, m, t, T, r, y) - DM * orc.bond(c, m, t, TM, r, y), 0.0)
+            assert X.dirichlet(t, r, y) == pytest.approx(want, rel=1e-14, abs=1e-16)
+        assert X.strike == pytest.approx(orc.atm_strike(c, T, TM) + 0.002, rel=1e-14)
+    it = small_item(kind=0)
+    with orc.Ctx(it) as X:
+        assert X.dirichlet(0.4, 0.05, 0.001) == pytest.approx(
+            orc.bond(it["curve"], it["model"], 0.4, it["inst"]["T"], 0.05, 0.001), rel=1e-15)
+
+
+# ---------------------------------------------------------- payoff, readout
+
+def test_payoff_cell_average_matches_brute_force(orc):
+    # Section 7.2: U^0 at a node is the payoff averaged over its control volume
+    # (reading R11: physical cell between the half nodes, clipped to the
+    # domain; v plays no role). Brute force: 1000 x 1000 midpoint rule of
+    # max(1 - Delta_M p(T,T_M; r, y), 0), with ln p affine in (r, y) as the
+    # bond formula of Section 3.1 states (coefficients read off the pinned
+    # bond function).
+    it = small_item(n_r=21, n_y=11, n_v=6, uniform=False, kind=1, T=3.0)
+    it["model"]["lambda_"] = 0.01
+    it["grid"] = W.default_grid(it["curve"], it["model"], 3.0, 21, 11, 6, 10)
+    fine = W.with_grid(it, n_r=41, n_y=21)  # its odd nodes are the half nodes
+    c, m = it["curve"], it["model"]
+    T, TM = it["inst"]["T"], it["inst"]["TM"]
+    a0 = math.log(orc.bond(c, m, T, TM, 0.0, 0.0))
+    a1 = math.log(orc.bond(c, m, T, TM, 1.0, 0.0)) - a0
+    a2 = math.log(orc.bond(c, m, T, TM, 0.0, 1.0)) - a0
+    with orc.Ctx(it) as X, orc.Ctx(fine) as Xf:
+        U0 = X.terminal()
+        assert np.all(U0 == U0[:, :1, :])
+        DM = 1.0 + (TM - T) * X.strike
+        rh, _, _ = Xf.axis(0)
+        yh, _, _ = Xf.axis(2)
+        nq = 1000
+        u = (np.arange(nq) + 0.5) / nq
+        hits = 0
+        for (i, j) in [(0, 0), (9, 0), (10, 3), (11, 5), (13, 10), (20, 2), (7, 7), (12, 1)]:
+            ra, rb = rh[max(2 * i - 1, 0)], rh[min(2 * i + 1, 40)]
+            ya, yb = yh[max(2 * j - 1, 0)], yh[min(2 * j + 1, 20)]
+            rr = (ra + (rb - ra) * u)[None, :]
+            yy = (ya + (yb - ya) * u)[:, None]
+            pay = np.maximum(1.0 - DM * np.exp(a0 + a1 * rr + a2 * yy), 0.0)
+            brute = pay.mean()
+            got = U0[j, 0, i]
+            hits += 0.0 < brute < pay.max()
+            assert abs(got - brute) <= 1e-6 * max(abs(brute), 1e-3), (i, j, got, brute)
+        assert hits >= 2  # some sampled cells straddle the payoff kink
+
+
+def test_payoff_average_exact_in_r(orc):
+    # The r-average is closed form: compare with adaptive quadrature (1e-10).
+    it = small_item(n_r=21, n_y=5, n_v=5, uniform=False, kind=1, T=3.0)
+    it["grid"]["y_max"] = 1e-9  # y cells ~0: the average is over r only
+    fine = W.with_grid(it, n_r=41)
+    c, m = it["curve"], it["model"]
+    T, TM = it["inst"]["T"], it["inst"]["TM"]
+    with orc.Ctx(it) as X, orc.Ctx(fine) as Xf:
+        U0 = X.terminal()
+        DM = 1.0 + (TM - T) * X.strike
+        rh, _, _ = Xf.axis(0)
+        for i in range(21):
+            ra, rb = rh[max(2 * i - 1, 0)], rh[min(2 * i + 1, 40)]
+            I, _ = integrate.quad(lambda r_: max(1.0 - DM * orc.bond(c, m, T, TM, r_, 0.0), 0.0),
+                                  ra, rb, epsabs=1e-15, epsrel=1e-12, limit=200)
+            assert U0[0, 0, i] == pytest.approx(I / (rb - ra), rel=1e-7, abs=1e-12)
+
+
+def test_readout_exact_on_bicubics(orc):
+    # Reading R10: cubic Lagrange in (xi_r, xi_v) at r = f(0,0), v = v0, y = 0.
+    it = small_item(n_r=12, n_y=6, n_v=9, uniform=True)
+    rng = np.random.default_rng(11)
+    a = rng.standard_normal(4)
+    b = rng.standard_normal(4)
+    with orc.Ctx(it) as X:
+        R, V, Y = fields(X)
+        U = np.polyval(a, R) * np.polyval(b, V) + 3.0 * Y
+        r0 = orc.curve_f(it["curve"], 0.0)
+        v0 = it["model"]["v0"]
+        assert X.readout(U) == pytest.approx(np.polyval(a, r0) * np.polyval(b, v0), rel=1e-12)
+
+
+# ------------------------------------------------------------------ march
+
+def test_config1_bond_price(orc):
+    # Sections 4.1 and 6.1: the bond price reproduces P(0,T) = exp(-0.15); the
+    # paper's error is below 1e-5 on every mesh.
+    p = orc.price(W.config1())
+    assert abs(p - math.exp(-0.15)) < 1e-5
+
+
+@pytest.mark.parametrize("lam,eps,rho", [(0.005, 0.1, -0.7), (0.01, 0.6, 0.3), (0.02, 0.3, 0.0),
+                                         (0.02, 0.6, -0.7)])
+def test_bond_reproduces_curve_for_any_volatility(orc, lam, eps, rho):
+    # The bond price is independent of the volatility parameters (Section 3.1).
+    c = W.flat_curve(0.03)
+    m = W.model(0.1, lam, 0.0, 1.0, eps, rho)
+    g = W.default_grid(c, m, 5.0, 40, 20, 20, 100)
+    p = orc.price(W.item(c, m, g, W.bond(5.0)))
+    assert abs(p - math.exp(-0.15)) < 1e-5
+
+
+def test_bond_gamma_09_paper_set(orc):
+    # Section 3.3's 2007 parameters (gamma = 0.9, r >= 0, p(0,T) = 1.04^-T).
+    it = W.paper_2007_set()
+    p = orc.price(it)
+    assert abs(p - 1.04 ** -5.0) < 1e-5
+
+
+def test_bond_field_converges_to_exact(orc):
+    # Section 6.1, error map: the whole field converges to the exact bond in
+    # the zone of interest (r within 0.06 of f(0,0), v <= 3), at second order.
+    errs = []
+    for s in (1, 2, 4):
+        it = W.with_grid(W.config1(), n_r=20 * s, n_y=10 * s, n_v=10 * s, n_steps=25 * s)
+        with orc.Ctx(it) as X:
+            U = X.march()
+            R, V, Y = fields(X)
+            ex = np.vectorize(lambda r_, y_: orc.bond(it["curve"], it["model"], 0.0, 5.0, r_, y_))(R, Y)
+            zone = (np.abs(R - 0.03) < 0.06) & (V <= 3.0)
+            errs.append(np.max(np.abs(U - ex)[zone]))
+    assert errs[2] < errs[1] < errs[0]
+    # max norm over a zone whose node set changes with refinement: order ~2
+    assert math.log2(errs[0] / errs[1]) > 1.6 and math.log2(errs[1] / errs[2]) > 1.6, errs
+
+
+def test_bond_ns_curve_converges(orc):
+    # Nelson-Siegel curve: with the implicit operators at t^{n+1/2} and F at
+    # t^n (Section 5, delta form) the error is first order in time; taking F at
+    # t^{n+1/2} too makes the time error vanish to the level of the spatial one.
+    d = W.config2_draws(1, n_r=40, n_y=20, n_v=20, n_steps=100)[0]
+    d["inst"] = W.bond(5.0)
+    P = orc.curve_P(d["curve"], 5.0)
+    e100 = abs(orc.price(d) - P)
+    e400 = abs(orc.price(W.with_grid(d, n_steps=400)) - P)
+    assert e400 < e100 / 3.0
+    m100 = abs(orc.price(W.with_grid(d, explicit_midpoint=1)) - P)
+    assert m100 < 5e-5
+    m_fine = abs(orc.price(W.with_grid(d, explicit_midpoint=1, n_r=80, n_y=40, n_v=40, n_steps=100)) - P)
+    assert m_fine < m100 / 3.0
+
+
+@pytest.mark.parametrize("curve", [W.flat_curve(0.03), W.ns_curve(0.025, 0.0, -0.018, 4.6)])
+def test_gaussian_limit_converges_to_closed_form(orc, curve):
+    # Deterministic volatility (gamma = 0, epsilon = 0, v0 = 1): the caplet
+    # must converge at second order to the closed-form Gaussian price.
+    m = W.model(0.1, 0.01, 0.0, 1.0, 0.0, 0.0)
+    K = orc.atm_strike(curve, 5.0, 5.5)
+    exact = orc.gauss_caplet(curve, m, 5.0, 5.5, K)
+    errs = []
+    for nr in (32, 64, 128):
+        g = W.default_grid(curve, m, 5.0, nr, 8, 8, 100, explicit_midpoint=1)
+        errs.append(abs(orc.price(W.item(curve, m, g, W.caplet(5.0, 5.5))) - exact))
+    assert errs[2] < 1e-5
+    assert math.log2(errs[0] / errs[1]) > 1.8 and math.log2(errs[1] / errs[2]) > 1.5, errs
+
+
+@pytest.mark.parametrize("rho", [0.0, -0.7])
+def test_space_time_order(orc, rho):
+    # Refining (n_r, n_y, n_v, n_steps) by 2 shows second-order convergence;
+    # with rho != 0 Douglas is first order in theory, reported here as measured.
+    c = W.flat_curve(0.03)
+    m = W.model(0.1, 0.01, 0.0, 1.0, 0.3, rho)
+    ps = []
+    for s in (1, 2, 4):
+        g = W.default_grid(c, m, 5.0, 16 * s, 8 * s, 8 * s, 20 * s)
+        ps.append(orc.price(W.item(c, m, g, W.caplet(5.0, 5.5))))
+    order = math.log2(abs(ps[0] - ps[1]) / abs(ps[1] - ps[2]))
+    if rho == 0.0:
+        assert order > 1.8, (ps, order)
+    else:
+        assert order > 0.9, (ps, order)
+
+
+def test_y_face_order_makes_no_significant_difference(orc):
+    # Section 7.3: first- and second-order one-sided differences at the y
+    # faces give no significant difference.
+    it = W.config2_draws(1, n_r=48, n_y=24, n_v=24, n_steps=100)[0]
+    p2 = orc.price(it)
+    p1 = orc.price(W.with_grid(it, y_boundary_order=1))
+    assert abs(p1 - p2) < 1e-5
+
+
+def test_softened_price_is_smooth_in_strike(orc):
+    # Section 7.2: with the cell-averaged payoff on a grid that does not follow
+    # the strike, the price error varies smoothly across strikes (no sawtooth
+    # as the strike crosses nodes): second differences of the error across 41
+    # strikes stay far below the error itself.
+    c = W.flat_curve(0.03)
+    m = W.model(0.1, 0.01, 0.0, 1.0, 0.0, 0.0)
+    g = W.default_grid(c, m, 5.0, 40, 6, 6, 50)
+    g.update(center_r_on_strike=0, k_r=0.03)
+    K0 = orc.atm_strike(c, 5.0, 5.5)
+    errs = []
+    for dk in np.linspace(-0.01, 0.01, 41):
+        it = W.item(c, m, g, W.caplet(5.0, 5.5, float(dk), True))
+        errs.append(orc.price(it) - orc.gauss_caplet(c, m, 5.0, 5.5, K0 + dk))
+    errs = np.array(errs)
+    d2 = np.abs(np.diff(errs, 2))
+    assert np.max(d2) < 0.1 * np.max(np.abs(errs)), (np.max(d2), np.max(np.abs(errs)))
+
+
+# ------------------------------------------------------------ validation
+
+@pytest.mark.parametrize("field,value", [("n_r", 4), ("n_steps", 0), ("y_boundary_order", 3),
+                                         ("theta_adi", 1.5), ("explicit_midpoint", 2)])
+def test_invalid_grid_rejected(orc, field, value):
+    it = W.with_grid(W.config1(), **{field: value})
+    with pytest.raises(orc.OracleError):
+        orc.price(it)
+
+
+def test_invalid_model_and_instrument_rejected(orc):
+    it = W.config1()
+    bad = [("model", "rho", 1.5), ("model", "gamma", 1.2), ("model", "kappa", -0.1),
+           ("inst", "T", 0.0), ("curve", "flat_rate", float("nan"))]
+    for part, key, val in bad:
+        x = W.config1()
+        x[part][key] = val
+        with pytest.raises(orc.OracleError):
+            orc.price(x)
+    x = W.paper_2007_set()
+    x["grid"]["r_min"] = -0.01  # gamma > 0 needs r >= 0
+    with pytest.raises(orc.OracleError):
+        orc.price(x)
+    x = W.config2_draws(1, n_r=16, n_y=8, n_v=8, n_steps=4)[0]
+    x["inst"]["TM"] = x["inst"]["T"]
+    with pytest.raises(orc.OracleError):
+        orc.price(x)
+    assert it["grid"]["n_r"] == 40
