@@ -1,0 +1,397 @@
+"""Benchmark of the GPU Douglas ADI pricing path.
+
+Workload (default, --workload config2): 100 seeded 5y-into-6m ATM caplets on a
+128 (rate) x 64 (accumulated variance) x 64 (volatility) grid with 400 Douglas
+steps, Nelson-Siegel curves and (epsilon, rho) drawn as in the paper-shaped
+config (seed 1108002), FP32 march with FP64 set-up and read-out. One step of
+this benchmark = one hjm_price_batch call over all 100 caplets (set-up,
+terminal field, 400 steps x 3 kernel passes, read-out): 2.097e10 grid-point-
+steps. The state (100 x 2 MiB x 2 fields = 420 MB) is larger than L2, so no
+flush is needed between steps.
+
+Metric: grid-point-steps/s (caplets/s reported beside it). `value` is timed
+with CUDA events on the launching stream with the outputs in device memory
+(the 100 parameter structs, 25 KB, are uploaded inside each call); `e2e` is
+the same call with host outputs, wall-clocked. Under torchrun every rank runs
+its own replica of the batch on its own GPU (weak scaling); value = all
+ranks' grid-point-steps / the slowest rank's time.
+
+--impl reference times the CPU FP64 oracle (the plain serial C reference
+written from the paper) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADI grid-point-steps/s and caplet prices/s at 1e-4 rel vs FP64 oracle"
+UNIT = "grid-point-steps/s"
+KERNEL_KINDS = ("setup", "terminal", "pass1", "pass2", "pass3", "readout")
+# Algorithmic words moved per grid point by each pass (Section 5.1 Douglas
+# step as three line passes): pass 1 reads U^n and writes dU1, pass 2 reads
+# dU1 and writes dU2, pass 3 reads dU2 and U^n and writes U^{n+1}.
+WORDS_PER_POINT = {"pass1": 2, "pass2": 2, "pass3": 3}
+
+
+def workload_items(name):
+    from paper_1108_1688_gb300 import workloads as W
+    if name == "config2":
+        return W.config2_draws(100), "100 caplets 5y-into-6m ATM, NS curves, 128x64x64, 400 steps"
+    if name == "config4":
+        return [W.config4()], "1 caplet 10y-into-6m ATM, flat 3%, 512x256x256, 1000 steps"
+    if name == "config3":
+        return W.config3_batch(), "256 caplets, expiries 1..10y, uneven grids 64..256 x n/2 x n/2, 2n steps"
+    if name == "config1":
+        return [W.config1()], "5y zero-coupon bond, flat 3%, 40x20x20, 100 steps"
+    raise SystemExit("unknown workload %s" % name)
+
+
+def point_steps(items):
+    from paper_1108_1688_gb300 import workloads as W
+    return sum(W.point_steps(x) for x in items)
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                    rows.append(f)
+        finally:
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": float(rows[0][2]),
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------ distributed
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def reduce_max(value, world, device=None):
+    """Max over ranks of a float (identity at world 1)."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- helpers
+
+def source_digest():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1108_1688_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def recorded_traffic(kernel, workload, points_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_digest") != source_digest():
+        return None
+    rec = d.get("kernels", {}).get(kernel)
+    if not rec:
+        return None
+    return rec["dram_bytes_per_point"] * points_per_launch
+
+
+def cpu_baseline(items, budget_s=12.0, max_steps=200):
+    """The oracle, as it stands, on a bounded sample: the set-up and the first
+    Douglas steps of the first instrument of the workload, serial."""
+    import oracle
+    it = items[0]
+    g = it["grid"]
+    pts = g["n_r"] * g["n_v"] * g["n_y"]
+    with oracle.Ctx(it) as X:
+        t0 = time.perf_counter()
+        U = X.terminal()
+        n = 0
+        while n < min(max_steps, g["n_steps"]) and time.perf_counter() - t0 < budget_s:
+            U = X.step(n, U)
+            n += 1
+        dt = time.perf_counter() - t0
+    return {"value": n * pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "instrument 0 of the workload: set-up and the first %d of %d Douglas steps "
+                      "on %dx%dx%d (serial FP64 C oracle)" % (n, g["n_steps"], g["n_r"], g["n_y"], g["n_v"]),
+            "seconds": dt}
+
+
+# ------------------------------------------------------------------- arms
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    items, desc = workload_items(args.workload)
+    it = items[0]
+    g = it["grid"]
+    pts = g["n_r"] * g["n_v"] * g["n_y"]
+    per_step = max(1, args.ref_steps_per_step)
+    with oracle.Ctx(it) as X:
+        U = X.terminal()
+        n = 0
+        for _ in range(args.warmup):
+            for _ in range(per_step):
+                U = X.step(n % g["n_steps"], U)
+                n += 1
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for _ in range(per_step):
+                U = X.step(n % g["n_steps"], U)
+                n += 1
+        dt = time.perf_counter() - t0
+    value = args.steps * per_step * pts / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "sample": "%d Douglas step(s) of instrument 0 per step" % per_step},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d Douglas step(s) of instrument 0 (%dx%dx%d) per step, serial FP64 C"
+                                   % (per_step, g["n_r"], g["n_y"], g["n_v"])},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1108_1688_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    barrier(world)
+    from paper_1108_1688_gb300 import hjm
+
+    items, desc = workload_items(args.workload)
+    prec = args.precision
+    arr = hjm.make_items(items)
+    import ctypes
+    item_bytes = ctypes.sizeof(hjm.hjm_batch_item)
+    n = len(items)
+    ps = point_steps(items)
+    stream = torch.cuda.current_stream()
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    host_out = np.empty(n, dtype=np.float64)
+
+    def step_dev():
+        hjm.hjm_price_batch(arr, prec, out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        step_dev()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region (value)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step_dev()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    ms_max = reduce_max(ms, world, device="cuda")
+    clocks = clk.summary()
+
+    # ---- end to end through the public API with host buffers (e2e)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        hjm.hjm_price_batch(arr, prec, out=host_out, stream=stream)  # syncs for the D2H read
+    e2e_s = time.perf_counter() - t0
+    e2e_max = reduce_max(e2e_s, world, device="cuda")
+
+    # ---- per-kernel device times (trace mode: kernel by kernel, event pairs)
+    hjm.hjm_trace_enable(True)
+    hjm.hjm_trace_read(reset=True)
+    for _ in range(max(1, min(args.steps, 3))):
+        step_dev()
+    torch.cuda.synchronize()
+    trace = hjm.hjm_trace_read(reset=True)
+    hjm.hjm_trace_enable(False)
+
+    total_points = sum(x["grid"]["n_r"] * x["grid"]["n_v"] * x["grid"]["n_y"] for x in items)
+    elem = 4 if prec == "fp32" else 8
+    dom = max(KERNEL_KINDS, key=lambda k: trace[k][1])
+    launches, tot_ms = trace[dom]
+    avg_ms = tot_ms / max(launches, 1)
+    roof = None
+    if dom in WORDS_PER_POINT:
+        # one launch covers every grid point of every instrument of one shape
+        # group; for a single-shape workload that is all of them
+        shapes = {(x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], x["grid"]["n_steps"]) for x in items}
+        pts_launch = total_points / len(shapes)
+        alg = WORDS_PER_POINT[dom] * elem * pts_launch
+        peak, peak_kind = measured_peaks()
+        achieved = alg / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
+                "traffic": recorded_traffic(dom, args.workload, pts_launch)}
+    shares = {k: round(trace[k][1] / max(sum(v[1] for v in trace.values()), 1e-12), 4) for k in KERNEL_KINDS}
+
+    # step launches: set-up, terminal, 3 per Douglas step, read-out per shape
+    # group, plus the scatter of prices
+    groups = {}
+    for x in items:
+        key = (x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], x["grid"]["n_steps"])
+        groups[key] = x["grid"]["n_steps"]
+    launches_per_step = sum(3 + 3 * s for s in groups.values()) + 1
+
+    line = {
+        "metric": METRIC,
+        "value": world * ps * args.steps / (ms_max * 1e-3),
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if prec == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": desc, "instruments": n, "grid_point_steps_per_step": ps,
+                   "caplets_per_s": world * n * args.steps / (ms_max * 1e-3),
+                   "precision": prec, "l2": "working set %.0f MB > L2 (no flush)" % (2 * total_points * elem / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "param_upload_bytes_per_step": n * item_bytes},
+        "e2e": {"value": world * ps * args.steps / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": n * item_bytes, "d2h_bytes_per_step": n * 8},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "roofline": roof,
+        "kernel_shares": shares,
+        "source_digest": source_digest(),
+    }
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            line["cpu_baseline"] = cpu_baseline(items)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--ref-steps-per-step", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

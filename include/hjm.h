@@ -1,0 +1,195 @@
+/*
+ * hjm.h - C ABI of the GB300 (sm_103a) solver for the single-factor
+ * Heath-Jarrow-Morton model with stochastic volatility.
+ *
+ * The method is the one of E. Valero, M. Torrealba, L. Lacasa, F. Fraysse,
+ * "Fast resolution of a single factor Heath-Jarrow-Morton model with
+ * stochastic volatility": the Markovian state (r, v, y) of Section 3.1, the
+ * pricing PDE of Section 3.2 (Eq. (1)), the sinh-stretched grid of Sections
+ * 4.3 and 7.1, centred finite differences and the theta scheme in delta form
+ * of Section 5, and the Douglas ADI splitting of Section 5.1, with the
+ * softened payoff of Section 7.2 and the one-sided y faces of Section 7.3.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns hjm_status; nothing is thrown across the ABI. On a
+ *    non-zero status hjm_last_error() (thread-local) holds a one-line reason.
+ *  - Handles are created and destroyed by the caller and owned by the
+ *    library. Output buffers are owned by the caller.
+ *  - cuda_stream is a cudaStream_t (NULL = legacy default stream). Device
+ *    pointers are plain CUDA device addresses (e.g. torch data_ptr()).
+ *  - Fields are stored r fastest, then v, then y: index i + n_r*(k + n_v*j)
+ *    for node (r_i, v_k, y_j). Node counts include both boundaries.
+ *  - The library never falls back to the CPU: without a CUDA device every
+ *    compute call returns HJM_ECUDA.
+ */
+#ifndef HJM_H
+#define HJM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HJM_OK = 0,
+    HJM_EINVAL = 1,     /* an argument is out of range or inconsistent */
+    HJM_ENOMEM = 2,     /* device or host allocation failed */
+    HJM_ECUDA = 3,      /* a CUDA call failed, or no device */
+    HJM_ETOL = 4,       /* the error indicator misses tol_rel after escalation */
+    HJM_ETIMEOUT = 5,   /* a bounded device-side wait gave up */
+    HJM_ENUMERIC = 6,   /* a price came out NaN or infinite */
+    HJM_ERANGE = 7      /* a size exceeds what the kernels support */
+} hjm_status;
+
+/* Arithmetic of the time march. FP64: state, operator and solves in double.
+ * FP32: state, operator and solves in float (setup and readout stay in
+ * double). MIXED: FP32 march, then an FP64 re-run of the instrument when the
+ * error indicator misses the tolerance. */
+typedef enum { HJM_FP64 = 0, HJM_FP32 = 1, HJM_MIXED = 2 } hjm_precision;
+
+/* Initial forward curve f(0,t) (Section 2: p(0,T) = exp(-int_0^T f(0,s) ds)).
+ * FLAT: f = flat_rate. NELSON_SIEGEL (instantaneous-forward form):
+ * f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}, tau > 0. */
+typedef enum { HJM_CURVE_FLAT = 0, HJM_CURVE_NELSON_SIEGEL = 1 } hjm_curve_kind;
+typedef struct {
+    int kind;                 /* hjm_curve_kind */
+    double flat_rate;
+    double beta0, beta1, beta2, tau;
+} hjm_curve;
+
+/* Model of Section 3.1, constant in time: mean reversion kappa >= 0,
+ * volatility level lambda >= 0, elasticity gamma in [0,1] (gamma = 0 allows
+ * negative rates), variance mean reversion theta >= 0, vol-of-vol
+ * epsilon >= 0, correlation rho in [-1,1], initial variance v0 in [0,v_max]. */
+typedef struct {
+    double kappa, lambda, gamma, theta, epsilon, rho, v0;
+} hjm_model_params;
+
+/* Grid and scheme (Sections 4.3, 5, 5.1, 7.1, 7.3).
+ *  n_r, n_y, n_v   node counts per axis, boundaries included, each >= 5
+ *  n_steps         time steps, uniform dt = T / n_steps
+ *  r_min, r_max    rate domain; r_min must be 0 when gamma > 0
+ *  y_max, v_max    upper bounds of y and v (both start at 0)
+ *  alpha_*         sinh metric width per axis; <= 0 selects a uniform grid
+ *  k_r, k_v        metric centres in r and v (y is centred at 0)
+ *  center_r_on_strike  1: the r centre is the strike (caplet) or f(0,0) (bond)
+ *  theta_adi       theta of the theta scheme (0.5 = Crank-Nicolson)
+ *  y_boundary_order    1 or 2: order of the one-sided y differences in F
+ *  explicit_midpoint   0: F at t^n as in Section 5; 1: F at t^{n+1/2}
+ * Boundary rule: r = r_max, and r = r_min when gamma == 0, carry Dirichlet
+ * data (exact bond; caplet max(P(t,T) - Delta_M P(t,T_M), 0)); the v and y
+ * faces (and r = 0 when gamma > 0) drop the normal second derivative and the
+ * mixed term and use one-sided first differences. */
+typedef struct {
+    int n_r, n_y, n_v, n_steps;
+    double r_min, r_max, y_max, v_max;
+    double alpha_r, alpha_y, alpha_v;
+    double k_r, k_v;
+    int center_r_on_strike;
+    double theta_adi;
+    int y_boundary_order;
+    int explicit_midpoint;
+} hjm_grid_spec;
+
+/* Instruments of Section 3.2. ZCB pays 1 at T. CAPLET pays
+ * max(1 - Delta_M p(T,T_M), 0) at T with Delta_M = 1 + (T_M - T) K; when
+ * strike_atm_relative != 0 the strike is K plus the ATM simple forward
+ * (P(0,T)/P(0,T_M) - 1)/(T_M - T). */
+typedef enum { HJM_ZCB = 0, HJM_CAPLET = 1 } hjm_kind;
+typedef struct {
+    int kind;                 /* hjm_kind */
+    double expiry_T, pay_TM, strike_K;
+    int strike_atm_relative;
+} hjm_instrument;
+
+/* Per-price report. err_estimate is the a-posteriori rounding indicator of
+ * the march that produced the price (0 for FP64). */
+typedef struct {
+    int precision_used;       /* hjm_precision actually used for the price */
+    int escalated;            /* 1 if an FP32 result was replaced by FP64 */
+    double err_estimate;
+    int n_steps;
+    float time_us;            /* device time of the whole call, microseconds */
+    int tile_cfg;             /* r-line chunk size of the r-direction kernel */
+} hjm_price_info;
+
+typedef struct hjm_grid hjm_grid;
+
+/* Create a pricing grid for one curve and model. The handle keeps copies of
+ * the three structs and the stream; device memory is allocated at the first
+ * price. Errors: HJM_EINVAL on out-of-range parameters, HJM_ERANGE on sizes
+ * the kernels do not support, HJM_ECUDA without a device. */
+hjm_status hjm_grid_create(const hjm_curve* curve, const hjm_model_params* model,
+                           const hjm_grid_spec* spec, void* cuda_stream, hjm_grid** out);
+hjm_status hjm_grid_destroy(hjm_grid* grid);
+
+/* Price one instrument (Sections 3.2, 5.1): FP64 setup on the device, the
+ * Douglas march of n_steps steps in the requested precision, FP64 cubic
+ * readout at r = f(0,0), v = v0, y = 0. Synchronises the grid's stream.
+ * tol_rel: relative tolerance for the MIXED escalation (ignored otherwise).
+ * price_out: host double. info_out may be NULL. */
+hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
+                     double tol_rel, double* price_out, hjm_price_info* info_out);
+
+/* Price n independent instruments, each with its own curve, model and grid,
+ * in one call. Items of equal grid shape march together in the same kernel
+ * launches. prices_out: n doubles, host or device memory (detected).
+ * infos_out: n host structs or NULL. Asynchronous on cuda_stream when both
+ * outputs are device/NULL; otherwise synchronises before returning. */
+typedef struct {
+    hjm_curve curve;
+    hjm_model_params model;
+    hjm_grid_spec grid;
+    hjm_instrument inst;
+} hjm_batch_item;
+hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm_precision precision,
+                           double tol_rel, double* prices_out, hjm_price_info* infos_out,
+                           void* cuda_stream);
+
+/* Stepwise access for checking and for users who want the whole field.
+ *
+ * hjm_field: run the setup and the first n_run steps (0 <= n_run <= n_steps)
+ * of the march for one instrument and copy the field (n_r*n_v*n_y values,
+ * double for FP64, float for FP32) to field_out (host or device).
+ *
+ * hjm_axis: FP64 node, Jacobian and second-derivative tables of axis
+ * (0 = r, 1 = v, 2 = y) for this instrument (the r centre can depend on the
+ * strike); host arrays of the axis length.
+ *
+ * hjm_douglas_pass: one kernel pass of step n on device buffers of the
+ * field's type and size, on the grid's stream:
+ *   pass 1: in = U^n                -> out = dU1 (explicit F and r solve)
+ *   pass 2: in = dU1                -> out = dU2 (v solve)
+ *   pass 3: in = dU2, in2 = U^n     -> out = U^{n+1} (y solve and update)
+ * in and out may alias for passes 2 and 3 (in place). */
+hjm_status hjm_field(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
+                     int n_run, void* field_out);
+hjm_status hjm_axis(hjm_grid* grid, const hjm_instrument* inst, int axis,
+                    double* z_out, double* J_out, double* J2_out);
+hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
+                            int pass, int step_n, const void* in, const void* in2, void* out);
+
+/* Kernel tracing. While enabled, hjm_price_batch and hjm_price launch the
+ * march kernel by kernel (no graph) with a CUDA event pair around every
+ * launch on the caller's stream, and synchronise at the end of the call to
+ * accumulate the device time of each kernel kind. Intended for measurement,
+ * not for production runs. hjm_trace_read copies the totals (reset != 0
+ * clears them). Kinds: 0 set-up, 1 terminal field, 2 pass 1, 3 pass 2,
+ * 4 pass 3, 5 read-out. */
+#define HJM_TRACE_KINDS 6
+typedef struct {
+    long long launches[HJM_TRACE_KINDS];
+    double total_ms[HJM_TRACE_KINDS];
+} hjm_trace;
+hjm_status hjm_trace_enable(int on);
+hjm_status hjm_trace_read(hjm_trace* out, int reset);
+
+const char* hjm_status_string(hjm_status status);
+const char* hjm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HJM_H */

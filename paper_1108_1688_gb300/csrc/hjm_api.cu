@@ -1,0 +1,729 @@
+// C ABI of libhjm (declared in include/hjm.h): argument validation, grouping
+// of batch items by grid shape, device workspaces, CUDA-graph capture of the
+// time march, read-out and error reporting.
+//
+// Host code here validates and marshals only; every arithmetic step of the
+// method (set-up tables, terminal field, the march, the read-out) runs in the
+// kernels of hjm_setup.cu and hjm_march.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "hjm_kernels.cuh"
+
+using namespace hjm;
+
+// ----------------------------------------------------------------- errors
+
+static thread_local std::string g_last_error;
+
+static hjm_status fail(hjm_status s, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+#define CU_TRY(expr)                                                                         \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? HJM_ENOMEM : HJM_ECUDA, "%s: %s (%s:%d)", \
+                        #expr, cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+    } while (0)
+
+extern "C" const char* hjm_status_string(hjm_status s)
+{
+    switch (s) {
+    case HJM_OK: return "ok";
+    case HJM_EINVAL: return "invalid argument";
+    case HJM_ENOMEM: return "out of memory";
+    case HJM_ECUDA: return "CUDA error";
+    case HJM_ETOL: return "tolerance missed";
+    case HJM_ETIMEOUT: return "device wait timed out";
+    case HJM_ENUMERIC: return "non-finite result";
+    case HJM_ERANGE: return "size out of supported range";
+    }
+    return "unknown status";
+}
+
+extern "C" const char* hjm_last_error(void) { return g_last_error.c_str(); }
+
+// ------------------------------------------------------------- validation
+
+static bool finite_all(std::initializer_list<double> xs)
+{
+    for (double x : xs)
+        if (!isfinite(x)) return false;
+    return true;
+}
+
+static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const hjm_grid_spec& g,
+                           const hjm_instrument* in, size_t elem)
+{
+    if (!finite_all({c.flat_rate, c.beta0, c.beta1, c.beta2, c.tau, m.kappa, m.lambda, m.gamma,
+                     m.theta, m.epsilon, m.rho, m.v0, g.r_min, g.r_max, g.y_max, g.v_max, g.alpha_r,
+                     g.alpha_y, g.alpha_v, g.k_r, g.k_v, g.theta_adi}))
+        return fail(HJM_EINVAL, "non-finite curve, model or grid parameter");
+    if (c.kind != HJM_CURVE_FLAT && c.kind != HJM_CURVE_NELSON_SIEGEL)
+        return fail(HJM_EINVAL, "unknown curve kind %d", c.kind);
+    if (c.kind == HJM_CURVE_NELSON_SIEGEL && !(c.tau > 0.0))
+        return fail(HJM_EINVAL, "Nelson-Siegel tau must be > 0");
+    if (g.n_r < 5 || g.n_v < 5 || g.n_y < 5) return fail(HJM_EINVAL, "each axis needs >= 5 nodes");
+    if (g.n_steps < 1) return fail(HJM_EINVAL, "n_steps must be >= 1");
+    if (!(g.r_max > g.r_min) || !(g.y_max > 0.0) || !(g.v_max > 0.0))
+        return fail(HJM_EINVAL, "empty domain");
+    if (m.gamma < 0.0 || m.gamma > 1.0) return fail(HJM_EINVAL, "gamma must be in [0,1]");
+    if (m.gamma > 0.0 && g.r_min != 0.0) return fail(HJM_EINVAL, "gamma > 0 needs r_min = 0");
+    if (m.rho < -1.0 || m.rho > 1.0) return fail(HJM_EINVAL, "rho must be in [-1,1]");
+    if (m.kappa < 0.0 || m.lambda < 0.0 || m.epsilon < 0.0 || m.theta < 0.0)
+        return fail(HJM_EINVAL, "kappa, lambda, epsilon, theta must be >= 0");
+    if (m.v0 < 0.0 || m.v0 > g.v_max) return fail(HJM_EINVAL, "v0 outside [0, v_max]");
+    if (g.theta_adi < 0.0 || g.theta_adi > 1.0) return fail(HJM_EINVAL, "theta_adi outside [0,1]");
+    if (g.y_boundary_order != 1 && g.y_boundary_order != 2)
+        return fail(HJM_EINVAL, "y_boundary_order must be 1 or 2");
+    if (g.explicit_midpoint != 0 && g.explicit_midpoint != 1)
+        return fail(HJM_EINVAL, "explicit_midpoint must be 0 or 1");
+    const double r00 = c.kind == HJM_CURVE_FLAT ? c.flat_rate : c.beta0 + c.beta1;  // f(0,0)
+    if (r00 < g.r_min || r00 > g.r_max) return fail(HJM_EINVAL, "f(0,0) outside [r_min, r_max]");
+    if (pass1_chunk(g.n_r) == 0) return fail(HJM_ERANGE, "n_r = %d above 512", g.n_r);
+    if (elem) {
+        const int lim = max_strided_len(elem, m.gamma > 0.0);
+        if (g.n_v > lim || g.n_y > lim)
+            return fail(HJM_ERANGE, "n_v, n_y must be <= %d for this precision", lim);
+    }
+    if (in) {
+        if (!finite_all({in->expiry_T, in->pay_TM, in->strike_K}))
+            return fail(HJM_EINVAL, "non-finite instrument field");
+        if (in->kind != HJM_ZCB && in->kind != HJM_CAPLET)
+            return fail(HJM_EINVAL, "unknown instrument kind %d", in->kind);
+        if (!(in->expiry_T > 0.0)) return fail(HJM_EINVAL, "expiry must be > 0");
+        if (in->kind == HJM_CAPLET && !(in->pay_TM > in->expiry_T))
+            return fail(HJM_EINVAL, "caplet needs pay_TM > expiry_T");
+    }
+    return HJM_OK;
+}
+
+static InstParams to_params(const hjm_batch_item& it)
+{
+    InstParams p;
+    memset(&p, 0, sizeof p);
+    p.ckind = it.curve.kind;
+    p.flat = it.curve.flat_rate;
+    p.b0 = it.curve.beta0;
+    p.b1 = it.curve.beta1;
+    p.b2 = it.curve.beta2;
+    p.tau = it.curve.tau;
+    p.kappa = it.model.kappa;
+    p.lambda = it.model.lambda;
+    p.gamma = it.model.gamma;
+    p.theta = it.model.theta;
+    p.eps = it.model.epsilon;
+    p.rho = it.model.rho;
+    p.v0 = it.model.v0;
+    p.nr = it.grid.n_r;
+    p.nv = it.grid.n_v;
+    p.ny = it.grid.n_y;
+    p.nsteps = it.grid.n_steps;
+    p.rmin = it.grid.r_min;
+    p.rmax = it.grid.r_max;
+    p.ymax = it.grid.y_max;
+    p.vmax = it.grid.v_max;
+    p.ar = it.grid.alpha_r;
+    p.ay = it.grid.alpha_y;
+    p.av = it.grid.alpha_v;
+    p.kr = it.grid.k_r;
+    p.kv = it.grid.k_v;
+    p.center_on_strike = it.grid.center_r_on_strike;
+    p.theta_adi = it.grid.theta_adi;
+    p.yorder = it.grid.y_boundary_order;
+    p.midpoint = it.grid.explicit_midpoint;
+    p.kind = it.inst.kind;
+    p.T = it.inst.expiry_T;
+    p.TM = it.inst.kind == HJM_CAPLET ? it.inst.pay_TM : it.inst.expiry_T;
+    p.K = it.inst.strike_K;
+    p.atm_rel = it.inst.strike_atm_relative != 0;
+    return p;
+}
+
+// ---------------------------------------------------------- device context
+
+namespace {
+
+struct Buffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t need)
+    {
+        if (need <= bytes) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&ptr, need);
+        if (e == cudaSuccess) bytes = need;
+        return e;
+    }
+    void release()
+    {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
+// Cached march graphs: key = (precision bytes, shape, B, buffer addresses).
+typedef std::tuple<size_t, int, int, int, int, int, int, const void*, const void*, const void*> GraphKey;
+
+struct Workspace {
+    Buffer block;                     // fields + tables of all groups
+    std::map<GraphKey, cudaGraphExec_t> graphs;
+    void drop_graphs()
+    {
+        for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+    }
+    void release()
+    {
+        drop_graphs();
+        block.release();
+    }
+};
+
+std::mutex g_mu;
+std::map<cudaStream_t, Workspace*> g_ws;  // batch workspaces, one per stream
+bool g_init_done = false;
+cudaStream_t g_capture_stream = nullptr;
+
+hjm_status ensure_init()
+{
+    if (g_init_done) return HJM_OK;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(HJM_ECUDA, "no CUDA device");
+    CU_TRY(init_kernels());
+    CU_TRY(cudaStreamCreateWithFlags(&g_capture_stream, cudaStreamNonBlocking));
+    g_init_done = true;
+    return HJM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Group {
+    int nr, nv, ny, nsteps;
+    std::vector<size_t> idx;  // positions in the caller's item array
+    bool gpos = false;
+    GroupTables t{};
+    void* U = nullptr;
+    void* A = nullptr;
+    double* prices = nullptr;
+};
+
+// ------------------------------------------------------------ tracing
+
+bool g_trace_on = false;
+hjm_trace g_trace;
+std::vector<cudaEvent_t> g_ev_pool;
+std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> g_ev_pending;
+
+// Event pair around one launch of kind `kind` (only while tracing).
+struct TraceScope {
+    int kind;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr, b = nullptr;
+    static cudaEvent_t take()
+    {
+        if (!g_ev_pool.empty()) {
+            cudaEvent_t e = g_ev_pool.back();
+            g_ev_pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    TraceScope(int k, cudaStream_t st) : kind(k), s(st)
+    {
+        if (!g_trace_on) return;
+        a = take();
+        b = take();
+        cudaEventRecord(a, s);
+    }
+    ~TraceScope()
+    {
+        if (!a) return;
+        cudaEventRecord(b, s);
+        g_ev_pending.push_back({kind, {a, b}});
+    }
+};
+
+// Called after the stream is synchronised: fold pending event pairs in.
+void trace_collect()
+{
+    for (auto& p : g_ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+            g_trace.launches[p.first] += 1;
+            g_trace.total_ms[p.first] += ms;
+        }
+        g_ev_pool.push_back(p.second.first);
+        g_ev_pool.push_back(p.second.second);
+    }
+    g_ev_pending.clear();
+}
+
+template <typename T>
+hjm_status run_steps(const Group& g, int n_from, int n_to, cudaStream_t s)
+{
+    const March<T> P = march_args<T>(g.t);
+    T* U = (T*)g.U;
+    T* A = (T*)g.A;
+    for (int n = n_from; n < n_to; ++n) {
+        {
+            TraceScope ts(2, s);
+            CU_TRY(launch_pass1<T>(P, U, A, n, s));
+        }
+        {
+            TraceScope ts(3, s);
+            CU_TRY(launch_pass2<T>(P, A, A, s));
+        }
+        {
+            TraceScope ts(4, s);
+            CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, s));
+        }
+    }
+    return HJM_OK;
+}
+
+hjm_status run_steps_any(const Group& g, size_t elem, int n_from, int n_to, cudaStream_t s)
+{
+    return elem == sizeof(float) ? run_steps<float>(g, n_from, n_to, s)
+                                 : run_steps<double>(g, n_from, n_to, s);
+}
+
+// The whole march of a group as one graph launch (captured once per shape
+// and buffer set, then replayed).
+hjm_status march_graph(Workspace& ws, const Group& g, size_t elem, cudaStream_t s)
+{
+    GraphKey key(elem, g.nr, g.nv, g.ny, g.nsteps, g.t.B, (int)g.gpos, g.U, g.A, g.t.rt);
+    auto it = ws.graphs.find(key);
+    if (it == ws.graphs.end()) {
+        if (ws.graphs.size() > 64) ws.drop_graphs();
+        cudaGraph_t graph = nullptr;
+        CU_TRY(cudaStreamBeginCapture(g_capture_stream, cudaStreamCaptureModeThreadLocal));
+        hjm_status st = run_steps_any(g, elem, 0, g.nsteps, g_capture_stream);
+        cudaError_t e = cudaStreamEndCapture(g_capture_stream, &graph);
+        if (st != HJM_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        CU_TRY(e);
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CU_TRY(e);
+        it = ws.graphs.emplace(key, exec).first;
+    }
+    CU_TRY(cudaGraphLaunch(it->second, s));
+    return HJM_OK;
+}
+
+__global__ void k_scatter(const double* src, const long long* idx, int n, double* dst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[idx[t]] = src[t];
+}
+
+bool is_device_ptr(const void* p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Plan the groups of a batch and carve their buffers out of the workspace.
+hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
+                std::vector<Group>& groups, InstParams** d_params, long long** d_idx,
+                double** d_prices_all)
+{
+    std::map<std::tuple<int, int, int, int>, size_t> where;
+    for (size_t i = 0; i < n; ++i) {
+        const hjm_grid_spec& g = items[i].grid;
+        auto key = std::make_tuple(g.n_r, g.n_v, g.n_y, g.n_steps);
+        auto f = where.find(key);
+        if (f == where.end()) {
+            Group gr;
+            gr.nr = g.n_r;
+            gr.nv = g.n_v;
+            gr.ny = g.n_y;
+            gr.nsteps = g.n_steps;
+            f = where.emplace(key, groups.size()).first;
+            groups.push_back(gr);
+        }
+        Group& gr = groups[f->second];
+        gr.idx.push_back(i);
+        gr.gpos = gr.gpos || items[i].model.gamma > 0.0;
+    }
+    size_t bytes = align256(n * sizeof(InstParams)) + align256(n * sizeof(long long)) +
+                   2 * align256(n * sizeof(double));
+    for (auto& g : groups) {
+        const size_t B = g.idx.size();
+        const size_t N = (size_t)g.nr * g.nv * g.ny;
+        bytes += 2 * align256(B * N * elem) + tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
+    }
+    const void* old = ws.block.ptr;
+    cudaError_t e = ws.block.ensure(bytes);
+    if (e != cudaSuccess)
+        return fail(HJM_ENOMEM, "device workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    if (ws.block.ptr != old) ws.drop_graphs();
+    char* p = (char*)ws.block.ptr;
+    *d_params = (InstParams*)p;
+    p += align256(n * sizeof(InstParams));
+    *d_idx = (long long*)p;
+    p += align256(n * sizeof(long long));
+    *d_prices_all = (double*)p;
+    p += align256(n * sizeof(double));
+    double* group_prices = (double*)p;
+    p += align256(n * sizeof(double));
+    size_t off = 0;
+    for (auto& g : groups) {
+        const size_t B = g.idx.size();
+        const size_t N = (size_t)g.nr * g.nv * g.ny;
+        g.U = p;
+        p += align256(B * N * elem);
+        g.A = p;
+        p += align256(B * N * elem);
+        g.t.nr = g.nr;
+        g.t.nv = g.nv;
+        g.t.ny = g.ny;
+        g.t.nsteps = g.nsteps;
+        g.t.B = (int)B;
+        g.t.params = *d_params + off;
+        g.prices = group_prices + off;
+        tables_carve(g.t, p, elem);
+        p += tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
+        off += B;
+    }
+    return HJM_OK;
+}
+
+Workspace* stream_workspace(cudaStream_t s)
+{
+    auto it = g_ws.find(s);
+    if (it != g_ws.end()) return it->second;
+    Workspace* w = new Workspace();
+    g_ws[s] = w;
+    return w;
+}
+
+// Core of hjm_price_batch (caller holds g_mu).
+hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm_precision prec,
+                       double* prices_out, hjm_price_info* infos, cudaStream_t s)
+{
+    if (prec == HJM_MIXED)
+        return fail(HJM_EINVAL, "MIXED precision is not available in this build");
+    const size_t elem = prec == HJM_FP32 ? sizeof(float) : sizeof(double);
+    for (size_t i = 0; i < n; ++i) {
+        hjm_status st = validate(items[i].curve, items[i].model, items[i].grid, &items[i].inst, elem);
+        if (st != HJM_OK) {
+            std::string why = g_last_error;
+            return fail(st, "item %zu: %s", i, why.c_str());
+        }
+    }
+    std::vector<Group> groups;
+    InstParams* d_params;
+    long long* d_idx;
+    double* d_prices;
+    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices);
+    if (st != HJM_OK) return st;
+
+    // Parameters in group order, and the scatter map back to caller order.
+    std::vector<InstParams> hp;
+    std::vector<long long> order;
+    hp.reserve(n);
+    order.reserve(n);
+    for (auto& g : groups)
+        for (size_t i : g.idx) {
+            hp.push_back(to_params(items[i]));
+            order.push_back((long long)i);
+        }
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timing = infos != nullptr;
+    if (timing) {
+        CU_TRY(cudaEventCreate(&ev0));
+        CU_TRY(cudaEventCreate(&ev1));
+        CU_TRY(cudaEventRecord(ev0, s));
+    }
+    CU_TRY(cudaMemcpyAsync(d_params, hp.data(), n * sizeof(InstParams), cudaMemcpyHostToDevice, s));
+    CU_TRY(cudaMemcpyAsync(d_idx, order.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s));
+    for (auto& g : groups) {
+        {
+            TraceScope ts(0, s);
+            CU_TRY(launch_setup(g.t, elem, s));
+        }
+        {
+            TraceScope ts(1, s);
+            CU_TRY(launch_terminal(g.t, g.U, elem, s));
+        }
+        st = g_trace_on ? run_steps_any(g, elem, 0, g.nsteps, s) : march_graph(ws, g, elem, s);
+        if (st != HJM_OK) return st;
+        {
+            TraceScope ts(5, s);
+            CU_TRY(launch_readout(g.t, g.U, elem, g.prices, s));
+        }
+    }
+    // group-ordered prices -> caller order
+    k_scatter<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].prices, d_idx, (int)n, d_prices);
+    CU_TRY(cudaGetLastError());
+    const bool dev_out = is_device_ptr(prices_out);
+    if (dev_out) {
+        CU_TRY(cudaMemcpyAsync(prices_out, d_prices, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else {
+        CU_TRY(cudaMemcpyAsync(prices_out, d_prices, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
+    if (timing) CU_TRY(cudaEventRecord(ev1, s));
+    if (!dev_out || timing || g_trace_on) CU_TRY(cudaStreamSynchronize(s));
+    if (g_trace_on) trace_collect();
+    if (!dev_out)
+        for (size_t i = 0; i < n; ++i)
+            if (!isfinite(prices_out[i])) return fail(HJM_ENUMERIC, "item %zu: price is not finite", i);
+    if (timing) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        for (size_t i = 0; i < n; ++i) {
+            infos[i].precision_used = prec;
+            infos[i].escalated = 0;
+            infos[i].err_estimate = 0.0;
+            infos[i].n_steps = items[i].grid.n_steps;
+            infos[i].time_us = ms * 1000.f;
+            infos[i].tile_cfg = pass1_chunk(items[i].grid.n_r);
+        }
+    }
+    return HJM_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- grids
+
+struct hjm_grid {
+    hjm_curve curve;
+    hjm_model_params model;
+    hjm_grid_spec spec;
+    cudaStream_t stream;
+    Workspace ws;
+};
+
+extern "C" hjm_status hjm_grid_create(const hjm_curve* curve, const hjm_model_params* model,
+                                      const hjm_grid_spec* spec, void* cuda_stream, hjm_grid** out)
+{
+    if (!curve || !model || !spec || !out) return fail(HJM_EINVAL, "null argument");
+    *out = nullptr;
+    hjm_status st = validate(*curve, *model, *spec, nullptr, 0);
+    if (st != HJM_OK) return st;
+    std::lock_guard<std::mutex> lk(g_mu);
+    st = ensure_init();
+    if (st != HJM_OK) return st;
+    hjm_grid* g = new (std::nothrow) hjm_grid();
+    if (!g) return fail(HJM_ENOMEM, "host allocation");
+    g->curve = *curve;
+    g->model = *model;
+    g->spec = *spec;
+    g->stream = (cudaStream_t)cuda_stream;
+    *out = g;
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_grid_destroy(hjm_grid* grid)
+{
+    if (!grid) return HJM_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    cudaStreamSynchronize(grid->stream);
+    grid->ws.release();
+    delete grid;
+    return HJM_OK;
+}
+
+static hjm_batch_item grid_item(const hjm_grid* g, const hjm_instrument* inst)
+{
+    hjm_batch_item it;
+    it.curve = g->curve;
+    it.model = g->model;
+    it.grid = g->spec;
+    it.inst = *inst;
+    return it;
+}
+
+extern "C" hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
+                                double tol_rel, double* price_out, hjm_price_info* info_out)
+{
+    (void)tol_rel;
+    if (!grid || !inst || !price_out) return fail(HJM_EINVAL, "null argument");
+    if (precision != HJM_FP64 && precision != HJM_FP32 && precision != HJM_MIXED)
+        return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    const hjm_batch_item it = grid_item(grid, inst);
+    double p = 0.0;
+    st = price_batch(grid->ws, &it, 1, precision, &p, info_out, grid->stream);
+    if (st != HJM_OK) return st;
+    *price_out = p;
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm_precision precision,
+                                      double tol_rel, double* prices_out, hjm_price_info* infos_out,
+                                      void* cuda_stream)
+{
+    (void)tol_rel;
+    if (n == 0) return HJM_OK;
+    if (!items || !prices_out) return fail(HJM_EINVAL, "null argument");
+    if (precision != HJM_FP64 && precision != HJM_FP32 && precision != HJM_MIXED)
+        return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    const size_t elem = precision == HJM_FP32 ? sizeof(float) : sizeof(double);
+    for (size_t i = 0; i < n; ++i) {
+        hjm_status st = validate(items[i].curve, items[i].model, items[i].grid, &items[i].inst, elem);
+        if (st != HJM_OK) {
+            std::string why = g_last_error;
+            return fail(st, "item %zu: %s", i, why.c_str());
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    return price_batch(*stream_workspace(s), items, n, precision, prices_out, infos_out, s);
+}
+
+// ---------------------------------------------------------- stepwise access
+
+// Set up one instrument on the grid's workspace (tables + terminal field).
+static hjm_status setup_one(hjm_grid* grid, const hjm_instrument* inst, hjm_precision prec,
+                            std::vector<Group>& groups, size_t& elem)
+{
+    if (prec == HJM_MIXED) return fail(HJM_EINVAL, "stepwise access needs FP32 or FP64");
+    elem = prec == HJM_FP32 ? sizeof(float) : sizeof(double);
+    hjm_status st = validate(grid->curve, grid->model, grid->spec, inst, elem);
+    if (st != HJM_OK) return st;
+    const hjm_batch_item it = grid_item(grid, inst);
+    InstParams* d_params;
+    long long* d_idx;
+    double* d_prices;
+    st = plan(grid->ws, &it, 1, elem, groups, &d_params, &d_idx, &d_prices);
+    if (st != HJM_OK) return st;
+    const InstParams hp = to_params(it);
+    CU_TRY(cudaMemcpyAsync(d_params, &hp, sizeof hp, cudaMemcpyHostToDevice, grid->stream));
+    CU_TRY(launch_setup(groups[0].t, elem, grid->stream));
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_field(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
+                                int n_run, void* field_out)
+{
+    if (!grid || !inst || !field_out) return fail(HJM_EINVAL, "null argument");
+    if (n_run < 0 || n_run > grid->spec.n_steps) return fail(HJM_EINVAL, "n_run outside [0, n_steps]");
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    std::vector<Group> groups;
+    size_t elem;
+    st = setup_one(grid, inst, precision, groups, elem);
+    if (st != HJM_OK) return st;
+    const Group& g = groups[0];
+    CU_TRY(launch_terminal(g.t, g.U, elem, grid->stream));
+    st = run_steps_any(g, elem, 0, n_run, grid->stream);
+    if (st != HJM_OK) return st;
+    const size_t bytes = (size_t)g.nr * g.nv * g.ny * elem;
+    CU_TRY(cudaMemcpyAsync(field_out, g.U, bytes, cudaMemcpyDefault, grid->stream));
+    CU_TRY(cudaStreamSynchronize(grid->stream));
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_axis(hjm_grid* grid, const hjm_instrument* inst, int axis, double* z_out,
+                               double* J_out, double* J2_out)
+{
+    if (!grid || !inst || !z_out || !J_out || !J2_out) return fail(HJM_EINVAL, "null argument");
+    if (axis < 0 || axis > 2) return fail(HJM_EINVAL, "axis must be 0, 1 or 2");
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    std::vector<Group> groups;
+    size_t elem;
+    st = setup_one(grid, inst, HJM_FP64, groups, elem);
+    if (st != HJM_OK) return st;
+    const Group& g = groups[0];
+    const int n = axis == 0 ? g.nr : (axis == 1 ? g.nv : g.ny);
+    const double* src = axis == 0 ? g.t.axr : (axis == 1 ? g.t.axv : g.t.axy);
+    CU_TRY(cudaMemcpyAsync(z_out, src, n * sizeof(double), cudaMemcpyDeviceToHost, grid->stream));
+    CU_TRY(cudaMemcpyAsync(J_out, src + n, n * sizeof(double), cudaMemcpyDeviceToHost, grid->stream));
+    CU_TRY(cudaMemcpyAsync(J2_out, src + 2 * n, n * sizeof(double), cudaMemcpyDeviceToHost, grid->stream));
+    CU_TRY(cudaStreamSynchronize(grid->stream));
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* inst,
+                                       hjm_precision precision, int pass, int step_n, const void* in,
+                                       const void* in2, void* out)
+{
+    if (!grid || !inst || !in || !out) return fail(HJM_EINVAL, "null argument");
+    if (pass < 1 || pass > 3) return fail(HJM_EINVAL, "pass must be 1, 2 or 3");
+    if (pass == 3 && !in2) return fail(HJM_EINVAL, "pass 3 needs U^n");
+    if (step_n < 0 || step_n >= grid->spec.n_steps) return fail(HJM_EINVAL, "step outside [0, n_steps)");
+    if (pass == 1 && in == out) return fail(HJM_EINVAL, "pass 1 cannot run in place");
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    std::vector<Group> groups;
+    size_t elem;
+    st = setup_one(grid, inst, precision, groups, elem);
+    if (st != HJM_OK) return st;
+    const Group& g = groups[0];
+    cudaStream_t s = grid->stream;
+    if (elem == sizeof(float)) {
+        const March<float> P = march_args<float>(g.t);
+        if (pass == 1) CU_TRY(launch_pass1<float>(P, (const float*)in, (float*)out, step_n, s));
+        if (pass == 2) CU_TRY(launch_pass2<float>(P, (const float*)in, (float*)out, s));
+        if (pass == 3)
+            CU_TRY(launch_pass3<float>(P, (const float*)in, (const float*)in2, (float*)out, g.gpos, s));
+    } else {
+        const March<double> P = march_args<double>(g.t);
+        if (pass == 1) CU_TRY(launch_pass1<double>(P, (const double*)in, (double*)out, step_n, s));
+        if (pass == 2) CU_TRY(launch_pass2<double>(P, (const double*)in, (double*)out, s));
+        if (pass == 3)
+            CU_TRY(launch_pass3<double>(P, (const double*)in, (const double*)in2, (double*)out, g.gpos, s));
+    }
+    CU_TRY(cudaStreamSynchronize(s));
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_trace_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_trace_on = on != 0;
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_trace_read(hjm_trace* out, int reset)
+{
+    if (!out) return fail(HJM_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(g_mu);
+    *out = g_trace;
+    if (reset) memset(&g_trace, 0, sizeof g_trace);
+    return HJM_OK;
+}

@@ -1,0 +1,123 @@
+// Internal declarations shared by the CUDA translation units of libhjm.
+//
+// Data layout in device memory (one "group" = instruments of equal grid
+// shape that march together in the same launches; b indexes the group):
+//   field    U[b][j][k][i]            i on r (fastest), k on v, j on y
+//   r tables rt[b][RT_N][n_r]         per-node factors of the r operator
+//   v tables vt[b][VT_N][n_v]
+//   y tables yt[b][YT_N][n_y]
+//   scalars  sc[b][SC_N]              dt, theta*dt, 1/h per axis
+//   steps    st[b][n_steps][2]        a(t) = df(0,t)/dt + kappa f(0,t) for
+//                                     the explicit and the implicit stage
+//   faces    dir[b][n_steps][2][n_y]  Dirichlet data at t^{n+1}, r_min/r_max
+//   v LU     vf[b][3][n_v]            Thomas factors of I - theta dt A_v
+//   y LU     yf[b][n_v][3][n_y]       Thomas factors of I - theta dt A_y
+//                                     (gamma == 0 instruments only)
+//   flags    fl[b][4]                 r_min Dirichlet, y face order, y LU
+//                                     present, unused
+// All tables are built in FP64 on the device and stored in the march type.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hjm.h"
+
+namespace hjm {
+
+// Host-validated parameters of one instrument, as uploaded to the device.
+struct InstParams {
+    int ckind;
+    double flat, b0, b1, b2, tau;
+    double kappa, lambda, gamma, theta, eps, rho, v0;
+    int nr, nv, ny, nsteps;
+    double rmin, rmax, ymax, vmax, ar, ay, av, kr, kv;
+    int center_on_strike;
+    double theta_adi;
+    int yorder, midpoint;
+    int kind;
+    double T, TM, K;
+    int atm_rel;
+};
+
+// Scalars derived on the device by the setup kernel (FP64).
+struct InstDerived {
+    double K;        // absolute strike
+    double DM;       // Delta_M = 1 + (T_M - T) K
+    double dt;       // T / n_steps
+    double centre_r; // metric centre in r
+};
+
+enum { RT_R, RT_IJ, RT_C1, RT_C4V, RT_C4B, RT_C3, RT_CY, RT_N };
+enum { VT_V, VT_IJ, VT_G2, VT_G5, VT_FV, VT_N };
+enum { YT_Y, YT_IJ, YT_KY, YT_N };
+enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_N };
+enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_PAD, FL_N };
+
+template <typename T>
+struct March {
+    int nr, nv, ny, nsteps, B;
+    long long N;  // nr * nv * ny
+    const T* rt;
+    const T* vt;
+    const T* yt;
+    const T* sc;
+    const T* st;
+    const T* dir;
+    const T* vf;
+    const T* yf;
+    const int* fl;
+};
+
+// Group buffers produced by setup (all device pointers).
+struct GroupTables {
+    int nr, nv, ny, nsteps, B;
+    InstParams* params;   // [B]
+    InstDerived* derived; // [B]
+    double* axr;          // [B][3][nr] z, J, J2 (FP64)
+    double* axv;          // [B][3][nv]
+    double* axy;          // [B][3][ny]
+    void* rt;
+    void* vt;
+    void* yt;
+    void* sc;
+    void* st;
+    void* dir;
+    void* vf;
+    void* yf;
+    int* fl;
+};
+
+// Bytes of the march-type tables of a group.
+size_t tables_bytes(int nr, int nv, int ny, int nsteps, int B, size_t elem);
+// Carve the table pointers out of one device block of tables_bytes().
+void tables_carve(GroupTables& g, void* block, size_t elem);
+
+// Setup (FP64) of all tables for a group; elem = sizeof(float|double).
+cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s);
+// Terminal field U^0 (Section 7.2 cell average for caplets, 1 for bonds).
+cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStream_t s);
+// FP64 readout of every instrument's price into prices[B].
+cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
+                           cudaStream_t s);
+
+// The three Douglas passes of step n (in/out as documented in hjm.h).
+template <typename T>
+cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
+                         cudaStream_t s);
+// Raises the dynamic shared-memory limit of the strided-line kernels; call
+// once per device before launching or capturing.
+cudaError_t init_kernels();
+// Chunk size per lane used by pass 1 for this n_r (0 if unsupported).
+int pass1_chunk(int nr);
+// Largest line length pass 2 / pass 3 accept for this element size.
+int max_strided_len(size_t elem, bool gamma_pos);
+
+template <typename T>
+March<T> march_args(const GroupTables& g);
+
+}  // namespace hjm

@@ -1,0 +1,491 @@
+// FP64 set-up and read-out kernels of the Douglas ADI march.
+//
+// Everything here runs once per price (not per step): the curve and bond
+// functions of Sections 2 and 3.1, the sinh metric of Sections 4.3 / 7.1, the
+// coefficient tables of the operator of Eq. (1) in the metric form of Section
+// 4.3, the per-step scalars and Dirichlet data, the Thomas factors of the
+// line-invariant v and y systems, the softened terminal field of Section 7.2
+// and the cubic read-out at the model's initial state.
+#include <math.h>
+
+#include "hjm_kernels.cuh"
+
+namespace hjm {
+
+// ----------------------------------------------------------- curve, bonds
+
+// f(0,t) of the initial curve (flat or Nelson-Siegel forward form).
+__device__ double fwd(const InstParams& p, double t)
+{
+    if (p.ckind == HJM_CURVE_FLAT) return p.flat;
+    const double x = t / p.tau, e = exp(-x);
+    return p.b0 + e * (p.b1 + p.b2 * x);
+}
+
+__device__ double fwd_slope(const InstParams& p, double t)
+{
+    if (p.ckind == HJM_CURVE_FLAT) return 0.0;
+    const double x = t / p.tau, e = exp(-x);
+    return e * (p.b2 * (1.0 - x) - p.b1) / p.tau;
+}
+
+// P(0,t) = exp(-int_0^t f(0,s) ds).
+__device__ double discount(const InstParams& p, double t)
+{
+    if (p.ckind == HJM_CURVE_FLAT) return exp(-p.flat * t);
+    const double x = t / p.tau, e = exp(-x), one_m_e = -expm1(-x);
+    return exp(-(p.b0 * t + (p.b1 + p.b2) * p.tau * one_m_e - p.b2 * t * e));
+}
+
+// G(s) = (1 - e^{-kappa s}) / kappa, s when kappa = 0 (Section 3.1).
+__device__ double Gfun(double kappa, double s)
+{
+    return kappa == 0.0 ? s : -expm1(-kappa * s) / kappa;
+}
+
+// Affine bond price p(t,S) at state (r, y), Section 3.1 (x = r - f(0,t)).
+__device__ double bond(const InstParams& p, double t, double S, double r, double y)
+{
+    const double G = Gfun(p.kappa, S - t);
+    return discount(p, S) / discount(p, t) * exp(-G * (r - fwd(p, t)) - 0.5 * G * G * y);
+}
+
+// Dirichlet data on the r faces: the exact bond, or the caplet's intrinsic
+// forward value max(P(t,T) - Delta_M P(t,T_M), 0).
+__device__ double face_value(const InstParams& p, const InstDerived& D, double t, double r, double y)
+{
+    const double pT = bond(p, t, p.T, r, y);
+    if (p.kind == HJM_ZCB) return pT;
+    const double v = pT - D.DM * bond(p, t, p.TM, r, y);
+    return v > 0.0 ? v : 0.0;
+}
+
+// --------------------------------------------------------------- metric
+
+// z(xi) = K + alpha sinh(c2 xi + c1 (1 - xi)) with c1, c2 fixing the end
+// points; J = dz/dxi, J2 = d2z/dxi2. alpha <= 0: uniform. End points exact.
+__device__ void metric(double xi, double z0, double z1, double alpha, double K, double& z,
+                       double& J, double& J2)
+{
+    if (alpha <= 0.0) {
+        z = z0 + (z1 - z0) * xi;
+        J = z1 - z0;
+        J2 = 0.0;
+    } else {
+        const double c1 = asinh((z0 - K) / alpha), c2 = asinh((z1 - K) / alpha);
+        const double a = c1 + (c2 - c1) * xi, span = c2 - c1;
+        const double sh = sinh(a);
+        z = K + alpha * sh;
+        J = alpha * span * cosh(a);
+        J2 = alpha * span * span * sh;
+    }
+    if (xi == 0.0) z = z0;
+    if (xi == 1.0) z = z1;
+}
+
+__device__ double metric_inverse(double z, double z0, double z1, double alpha, double K)
+{
+    if (alpha <= 0.0) return (z - z0) / (z1 - z0);
+    const double c1 = asinh((z0 - K) / alpha), c2 = asinh((z1 - K) / alpha);
+    return (asinh((z - K) / alpha) - c1) / (c2 - c1);
+}
+
+__device__ double metric_z(double xi, double z0, double z1, double alpha, double K)
+{
+    double z, J, J2;
+    metric(xi, z0, z1, alpha, K, z, J, J2);
+    return z;
+}
+
+// ------------------------------------------------------------------ setup
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_setup(GroupTables g)
+{
+    const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
+    const int nr = g.nr, nv = g.nv, ny = g.ny, ns = g.nsteps;
+    const InstParams p = g.params[b];
+    __shared__ InstDerived D;
+    if (tid == 0) {
+        double K = 0.0, DM = 1.0;
+        if (p.kind == HJM_CAPLET) {
+            K = p.K;
+            if (p.atm_rel) K += (discount(p, p.T) / discount(p, p.TM) - 1.0) / (p.TM - p.T);
+            DM = 1.0 + (p.TM - p.T) * K;
+        }
+        D.K = K;
+        D.DM = DM;
+        D.dt = p.T / ns;
+        D.centre_r = p.center_on_strike ? (p.kind == HJM_CAPLET ? K : fwd(p, 0.0)) : p.kr;
+        g.derived[b] = D;
+    }
+    __syncthreads();
+
+    T* rt = (T*)g.rt + (size_t)b * RT_N * nr;
+    T* vt = (T*)g.vt + (size_t)b * VT_N * nv;
+    T* yt = (T*)g.yt + (size_t)b * YT_N * ny;
+    double* axr = g.axr + (size_t)b * 3 * nr;
+    double* axv = g.axv + (size_t)b * 3 * nv;
+    double* axy = g.axy + (size_t)b * 3 * ny;
+    const double lam2 = p.lambda * p.lambda, eps2 = p.eps * p.eps;
+    const double w = p.theta_adi * D.dt;
+
+    // r axis and r-operator factors: A_r = g1 d_rr + g4 d_r - r with
+    // g1 = zeta_rr / J^2, g4 = mu_r / J - zeta_rr J2 / J^3 (Section 4.3),
+    // zeta_rr = lambda^2 r^{2 gamma} v / 2, mu_r = a(t) - kappa r + y.
+    for (int i = tid; i < nr; i += nth) {
+        double z, J, J2;
+        metric((double)i / (nr - 1), p.rmin, p.rmax, p.ar, D.centre_r, z, J, J2);
+        axr[i] = z;
+        axr[nr + i] = J;
+        axr[2 * nr + i] = J2;
+        const double rg = p.gamma == 0.0 ? 1.0 : pow(z, p.gamma);
+        const double r2g = rg * rg;
+        rt[RT_R * nr + i] = (T)z;
+        rt[RT_IJ * nr + i] = (T)(1.0 / J);
+        rt[RT_C1 * nr + i] = (T)(0.5 * lam2 * r2g / (J * J));
+        rt[RT_C4V * nr + i] = (T)(0.5 * lam2 * r2g * J2 / (J * J * J));
+        rt[RT_C4B * nr + i] = (T)(-p.kappa * z / J);
+        rt[RT_C3 * nr + i] = (T)(p.lambda * rg * p.eps * p.rho / J);
+        rt[RT_CY * nr + i] = (T)(lam2 * r2g);
+    }
+    // v axis: A_v = g2 d_vv + g5 d_v, g2 = zeta_vv / J^2,
+    // g5 = mu_v / J - zeta_vv J2 / J^3; on the v faces mu_v / J alone.
+    for (int k = tid; k < nv; k += nth) {
+        double z, J, J2;
+        metric((double)k / (nv - 1), 0.0, p.vmax, p.av, p.kv, z, J, J2);
+        axv[k] = z;
+        axv[nv + k] = J;
+        axv[2 * nv + k] = J2;
+        const double zvv = 0.5 * eps2 * z, muv = p.theta * (1.0 - z);
+        vt[VT_V * nv + k] = (T)z;
+        vt[VT_IJ * nv + k] = (T)(1.0 / J);
+        vt[VT_G2 * nv + k] = (T)(zvv / (J * J));
+        vt[VT_G5 * nv + k] = (T)(muv / J - zvv * J2 / (J * J * J));
+        vt[VT_FV * nv + k] = (T)(muv / J);
+    }
+    // y axis: A_y = g6 d_y, g6 = (lambda^2 r^{2 gamma} v - 2 kappa y) / J.
+    for (int j = tid; j < ny; j += nth) {
+        double z, J, J2;
+        metric((double)j / (ny - 1), 0.0, p.ymax, p.ay, 0.0, z, J, J2);
+        axy[j] = z;
+        axy[ny + j] = J;
+        axy[2 * ny + j] = J2;
+        yt[YT_Y * ny + j] = (T)z;
+        yt[YT_IJ * ny + j] = (T)(1.0 / J);
+        yt[YT_KY * ny + j] = (T)(-2.0 * p.kappa * z);
+    }
+    if (tid == 0) {
+        T* sc = (T*)g.sc + (size_t)b * SC_N;
+        sc[SC_DT] = (T)D.dt;
+        sc[SC_W] = (T)w;
+        sc[SC_IHR] = (T)(nr - 1);
+        sc[SC_IHV] = (T)(nv - 1);
+        sc[SC_IHY] = (T)(ny - 1);
+        int* fl = g.fl + (size_t)b * FL_N;
+        fl[FL_RLO_DIR] = p.gamma == 0.0;
+        fl[FL_YORDER] = p.yorder;
+        fl[FL_YLU] = p.gamma == 0.0;
+        fl[FL_PAD] = 0;
+    }
+    // a(t) = df(0,t)/dt + kappa f(0,t): F at t^n (or t^{n+1/2}), implicit
+    // operators at t^{n+1/2} (Section 5, delta form).
+    T* st = (T*)g.st + (size_t)b * ns * 2;
+    for (int n = tid; n < ns; n += nth) {
+        const double tF = p.T - (p.midpoint ? n + 0.5 : (double)n) * D.dt;
+        const double tI = p.T - (n + 0.5) * D.dt;
+        st[2 * n] = (T)(fwd_slope(p, tF) + p.kappa * fwd(p, tF));
+        st[2 * n + 1] = (T)(fwd_slope(p, tI) + p.kappa * fwd(p, tI));
+    }
+    __syncthreads();  // y nodes above are read below by other threads
+
+    // Dirichlet data at t^{n+1} on r = r_min (face 0) and r = r_max (face 1).
+    T* dir = (T*)g.dir + (size_t)b * ns * 2 * ny;
+    for (int idx = tid; idx < ns * 2 * ny; idx += nth) {
+        const int j = idx % ny, face = (idx / ny) & 1, n = idx / (2 * ny);
+        const double t = p.T - (n + 1) * D.dt;
+        dir[idx] = (T)face_value(p, D, t, face ? p.rmax : p.rmin, axy[j]);
+    }
+
+    // Thomas factors (sub, c', 1/m) of I - theta dt A_v: the same for every
+    // v line (A_v depends on v only).
+    if (tid == 0) {
+        T* vf = (T*)g.vf + (size_t)b * 3 * nv;
+        const double ih = nv - 1, ih2 = ih * ih;
+        double cprev = 0.0;
+        for (int k = 0; k < nv; ++k) {
+            const double v = axv[k], J = axv[nv + k], J2 = axv[2 * nv + k];
+            const double zvv = 0.5 * eps2 * v, muv = p.theta * (1.0 - v);
+            double lo = 0.0, di = 0.0, up = 0.0;
+            if (k > 0 && k < nv - 1) {
+                const double g2 = zvv / (J * J), g5 = muv / J - zvv * J2 / (J * J * J);
+                lo = g2 * ih2 - 0.5 * g5 * ih;
+                di = -2.0 * g2 * ih2;
+                up = g2 * ih2 + 0.5 * g5 * ih;
+            } else if (k == 0) {
+                di = -muv / J * ih;
+                up = muv / J * ih;
+            } else {
+                lo = -muv / J * ih;
+                di = muv / J * ih;
+            }
+            const double sub = -w * lo, mainv = 1.0 - w * di, sup = -w * up;
+            const double m = mainv - sub * cprev;
+            cprev = sup / m;
+            vf[k] = (T)sub;
+            vf[nv + k] = (T)cprev;
+            vf[2 * nv + k] = (T)(1.0 / m);
+        }
+    }
+    // Thomas factors of I - theta dt A_y per v node when gamma == 0 (then
+    // g6 depends on v and y only, not on r).
+    if (p.gamma == 0.0 && g.yf != nullptr) {
+        const double ih = ny - 1;
+        for (int k = tid; k < nv; k += nth) {
+            T* yf = (T*)g.yf + ((size_t)b * nv + k) * 3 * ny;
+            const double v = axv[k];
+            double cprev = 0.0;
+            for (int j = 0; j < ny; ++j) {
+                const double g6 = (lam2 * v - 2.0 * p.kappa * axy[j]) / axy[ny + j];
+                double lo = 0.0, di = 0.0, up = 0.0;
+                if (j > 0 && j < ny - 1) {
+                    lo = -0.5 * g6 * ih;
+                    up = 0.5 * g6 * ih;
+                } else if (j == 0) {
+                    di = -g6 * ih;
+                    up = g6 * ih;
+                } else {
+                    lo = -g6 * ih;
+                    di = g6 * ih;
+                }
+                const double sub = -w * lo, mainv = 1.0 - w * di, sup = -w * up;
+                const double m = mainv - sub * cprev;
+                cprev = sup / m;
+                yf[j] = (T)sub;
+                yf[ny + j] = (T)cprev;
+                yf[2 * ny + j] = (T)(1.0 / m);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------- terminal field
+
+// Gauss-Legendre rule of order 8 on [-1, 1] by Newton on the Legendre
+// three-term recurrence (computed once per block).
+__device__ void gauss_legendre8(double* x, double* wt, int q)
+{
+    const int n = 8;
+    double z = cos(3.14159265358979323846 * (q + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        double p0 = 1.0, p1 = z;
+        for (int l = 2; l <= n; ++l) {
+            const double p2 = ((2 * l - 1) * z * p1 - (l - 1) * p0) / l;
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        const double step = p1 / dp;
+        z -= step;
+        if (fabs(step) < 1e-16) break;
+    }
+    x[q] = z;
+    wt[q] = 2.0 / ((1.0 - z * z) * dp * dp);
+}
+
+// Mean over r in [ra, rb] of max(1 - Delta_M p(T,T_M; r, y), 0): p is
+// A e^{-G r}, the payoff is positive above r* = ln(Delta_M A) / G and its
+// integral there is closed form.
+__device__ double caplet_r_mean(const InstParams& p, const InstDerived& D, double ra, double rb,
+                                double y)
+{
+    const double G = Gfun(p.kappa, p.TM - p.T);
+    const double lnA = log(discount(p, p.TM) / discount(p, p.T)) + G * fwd(p, p.T) - 0.5 * G * G * y;
+    const double lnDA = log(D.DM) + lnA;
+    if (!(rb > ra)) {
+        const double v = 1.0 - exp(lnDA - G * ra);
+        return v > 0.0 ? v : 0.0;
+    }
+    const double lo = fmax(ra, lnDA / G);
+    if (lo >= rb) return 0.0;
+    // int_lo^rb 1 - e^{lnDA - G r} dr
+    const double tail = exp(lnDA - G * lo) * (-expm1(-G * (rb - lo))) / G;
+    return ((rb - lo) - tail) / (rb - ra);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
+{
+    __shared__ double gx[8], gw[8];
+    if (threadIdx.x < 8) gauss_legendre8(gx, gw, threadIdx.x);
+    __syncthreads();
+    const int nr = g.nr, nv = g.nv, ny = g.ny;
+    const long long N = (long long)nr * nv * ny;
+    const long long total = (long long)g.B * ny * nr;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx % nr);
+        const int j = (int)((idx / nr) % ny);
+        const int b = (int)(idx / ((long long)nr * ny));
+        const InstParams& p = g.params[b];
+        double val = 1.0;
+        if (p.kind == HJM_CAPLET) {
+            const InstDerived D = g.derived[b];
+            const double hr = 1.0 / (nr - 1), hy = 1.0 / (ny - 1);
+            const double ra = metric_z(fmax(0.0, (i - 0.5) * hr), p.rmin, p.rmax, p.ar, D.centre_r);
+            const double rb = metric_z(fmin(1.0, (i + 0.5) * hr), p.rmin, p.rmax, p.ar, D.centre_r);
+            const double ya = metric_z(fmax(0.0, (j - 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
+            const double yb = metric_z(fmin(1.0, (j + 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
+            double s = 0.0;
+            for (int q = 0; q < 8; ++q) {
+                const double yq = 0.5 * (ya + yb) + 0.5 * (yb - ya) * gx[q];
+                s += 0.5 * gw[q] * caplet_r_mean(p, D, ra, rb, yq);
+            }
+            val = s;
+        }
+        T* row = U + (long long)b * N + (long long)j * nv * nr + i;
+        for (int k = 0; k < nv; ++k) row[(long long)k * nr] = (T)val;
+    }
+}
+
+// ---------------------------------------------------------------- readout
+
+// Price at r = f(0,0), v = v0 on the y = 0 plane: tensor-product cubic
+// Lagrange interpolation in the computational coordinates on the 4 x 4
+// nodes nearest the point, kept inside the grid.
+template <typename T>
+__global__ void k_readout(GroupTables g, const T* U, double* prices)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= g.B) return;
+    const InstParams p = g.params[b];
+    const InstDerived D = g.derived[b];
+    const int nr = g.nr, nv = g.nv;
+    const double sr = metric_inverse(fwd(p, 0.0), p.rmin, p.rmax, p.ar, D.centre_r) * (nr - 1);
+    const double sv = metric_inverse(p.v0, 0.0, p.vmax, p.av, p.kv) * (nv - 1);
+    const int i0 = min(max((int)floor(sr) - 1, 0), nr - 4);
+    const int k0 = min(max((int)floor(sv) - 1, 0), nv - 4);
+    double wr[4], wv[4];
+    for (int a = 0; a < 4; ++a) {
+        double pr = 1.0, pv = 1.0;
+        for (int c = 0; c < 4; ++c) {
+            if (c == a) continue;
+            pr *= (sr - i0 - c) / (double)(a - c);
+            pv *= (sv - k0 - c) / (double)(a - c);
+        }
+        wr[a] = pr;
+        wv[a] = pv;
+    }
+    const T* Ub = U + (long long)b * nr * nv * g.ny;
+    double s = 0.0;
+    for (int c = 0; c < 4; ++c) {
+        double row = 0.0;
+        for (int a = 0; a < 4; ++a) row += wr[a] * (double)Ub[(long long)(k0 + c) * nr + i0 + a];
+        s += wv[c] * row;
+    }
+    prices[b] = s;
+}
+
+// ------------------------------------------------------------- launchers
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t tables_bytes(int nr, int nv, int ny, int nsteps, int B, size_t elem)
+{
+    size_t s = 0;
+    s += align_up((size_t)B * RT_N * nr * elem);
+    s += align_up((size_t)B * VT_N * nv * elem);
+    s += align_up((size_t)B * YT_N * ny * elem);
+    s += align_up((size_t)B * SC_N * elem);
+    s += align_up((size_t)B * nsteps * 2 * elem);
+    s += align_up((size_t)B * nsteps * 2 * ny * elem);
+    s += align_up((size_t)B * 3 * nv * elem);
+    s += align_up((size_t)B * nv * 3 * ny * elem);
+    s += align_up((size_t)B * FL_N * sizeof(int));
+    s += align_up((size_t)B * 3 * (nr + nv + ny) * sizeof(double));
+    s += align_up((size_t)B * sizeof(InstDerived));
+    return s;
+}
+
+void tables_carve(GroupTables& g, void* block, size_t elem)
+{
+    char* p = (char*)block;
+    const size_t B = g.B;
+    auto take = [&](size_t bytes) {
+        char* q = p;
+        p += align_up(bytes);
+        return (void*)q;
+    };
+    g.rt = take(B * RT_N * g.nr * elem);
+    g.vt = take(B * VT_N * g.nv * elem);
+    g.yt = take(B * YT_N * g.ny * elem);
+    g.sc = take(B * SC_N * elem);
+    g.st = take(B * g.nsteps * 2 * elem);
+    g.dir = take(B * g.nsteps * 2 * g.ny * elem);
+    g.vf = take(B * 3 * g.nv * elem);
+    g.yf = take(B * g.nv * 3 * g.ny * elem);
+    g.fl = (int*)take(B * FL_N * sizeof(int));
+    double* ax = (double*)take(B * 3 * (g.nr + g.nv + g.ny) * sizeof(double));
+    g.axr = ax;
+    g.axv = ax + B * 3 * g.nr;
+    g.axy = g.axv + B * 3 * g.nv;
+    g.derived = (InstDerived*)take(B * sizeof(InstDerived));
+}
+
+cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s)
+{
+    if (elem == sizeof(float))
+        k_setup<float><<<g.B, 256, 0, s>>>(g);
+    else
+        k_setup<double><<<g.B, 256, 0, s>>>(g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStream_t s)
+{
+    const long long total = (long long)g.B * g.ny * g.nr;
+    const int blocks = (int)((total + 127) / 128 < 152 * 16 ? (total + 127) / 128 : 152 * 16);
+    if (elem == sizeof(float))
+        k_terminal<float><<<blocks, 128, 0, s>>>(g, (float*)U);
+    else
+        k_terminal<double><<<blocks, 128, 0, s>>>(g, (double*)U);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
+                           cudaStream_t s)
+{
+    const int blocks = (g.B + 63) / 64;
+    if (elem == sizeof(float))
+        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices);
+    else
+        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices);
+    return cudaGetLastError();
+}
+
+template <typename T>
+March<T> march_args(const GroupTables& g)
+{
+    March<T> P;
+    P.nr = g.nr;
+    P.nv = g.nv;
+    P.ny = g.ny;
+    P.nsteps = g.nsteps;
+    P.B = g.B;
+    P.N = (long long)g.nr * g.nv * g.ny;
+    P.rt = (const T*)g.rt;
+    P.vt = (const T*)g.vt;
+    P.yt = (const T*)g.yt;
+    P.sc = (const T*)g.sc;
+    P.st = (const T*)g.st;
+    P.dir = (const T*)g.dir;
+    P.vf = (const T*)g.vf;
+    P.yf = (const T*)g.yf;
+    P.fl = g.fl;
+    return P;
+}
+
+template March<float> march_args<float>(const GroupTables&);
+template March<double> march_args<double>(const GroupTables&);
+
+}  // namespace hjm

@@ -1,0 +1,279 @@
+"""Thin ctypes binding of libhjm (include/hjm.h): same names, argument
+marshalling only. Every step of the pricing path runs in the library's CUDA
+kernels; there is no Python or CPU fallback, and importing this module fails
+loudly when the compiled library is missing.
+
+Structs mirror the C header field by field. Item dicts (curve, model, grid,
+inst), as produced by paper_1108_1688_gb300.workloads, convert with
+`batch_item(d)`; the field `lambda` of the model struct is spelled `lambda_`
+here because `lambda` is a Python keyword.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libhjm.so")
+
+HJM_OK, HJM_EINVAL, HJM_ENOMEM, HJM_ECUDA, HJM_ETOL, HJM_ETIMEOUT, HJM_ENUMERIC, HJM_ERANGE = range(8)
+HJM_FP64, HJM_FP32, HJM_MIXED = 0, 1, 2
+HJM_CURVE_FLAT, HJM_CURVE_NELSON_SIEGEL = 0, 1
+HJM_ZCB, HJM_CAPLET = 0, 1
+
+PRECISIONS = {"fp64": HJM_FP64, "fp32": HJM_FP32, "mixed": HJM_MIXED,
+              HJM_FP64: HJM_FP64, HJM_FP32: HJM_FP32, HJM_MIXED: HJM_MIXED}
+
+
+class hjm_curve(C.Structure):
+    _fields_ = [("kind", C.c_int), ("flat_rate", C.c_double), ("beta0", C.c_double),
+                ("beta1", C.c_double), ("beta2", C.c_double), ("tau", C.c_double)]
+
+
+class hjm_model_params(C.Structure):
+    _fields_ = [("kappa", C.c_double), ("lambda_", C.c_double), ("gamma", C.c_double),
+                ("theta", C.c_double), ("epsilon", C.c_double), ("rho", C.c_double),
+                ("v0", C.c_double)]
+
+
+class hjm_grid_spec(C.Structure):
+    _fields_ = [("n_r", C.c_int), ("n_y", C.c_int), ("n_v", C.c_int), ("n_steps", C.c_int),
+                ("r_min", C.c_double), ("r_max", C.c_double), ("y_max", C.c_double),
+                ("v_max", C.c_double), ("alpha_r", C.c_double), ("alpha_y", C.c_double),
+                ("alpha_v", C.c_double), ("k_r", C.c_double), ("k_v", C.c_double),
+                ("center_r_on_strike", C.c_int), ("theta_adi", C.c_double),
+                ("y_boundary_order", C.c_int), ("explicit_midpoint", C.c_int)]
+
+
+class hjm_instrument(C.Structure):
+    _fields_ = [("kind", C.c_int), ("expiry_T", C.c_double), ("pay_TM", C.c_double),
+                ("strike_K", C.c_double), ("strike_atm_relative", C.c_int)]
+
+
+class hjm_price_info(C.Structure):
+    _fields_ = [("precision_used", C.c_int), ("escalated", C.c_int), ("err_estimate", C.c_double),
+                ("n_steps", C.c_int), ("time_us", C.c_float), ("tile_cfg", C.c_int)]
+
+
+HJM_TRACE_KINDS = 6
+TRACE_KIND_NAMES = ("setup", "terminal", "pass1", "pass2", "pass3", "readout")
+
+
+class hjm_trace(C.Structure):
+    _fields_ = [("launches", C.c_longlong * HJM_TRACE_KINDS), ("total_ms", C.c_double * HJM_TRACE_KINDS)]
+
+
+class hjm_batch_item(C.Structure):
+    _fields_ = [("curve", hjm_curve), ("model", hjm_model_params), ("grid", hjm_grid_spec),
+                ("inst", hjm_instrument)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libhjm.so is not built (expected at %s); run "
+                          "paper_1108_1688_gb300._build.build() first" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P, vp, st = C.POINTER, C.c_void_p, C.c_int
+    sig = {
+        "hjm_grid_create": ([P(hjm_curve), P(hjm_model_params), P(hjm_grid_spec), vp, P(vp)], st),
+        "hjm_grid_destroy": ([vp], st),
+        "hjm_price": ([vp, P(hjm_instrument), st, C.c_double, P(C.c_double), P(hjm_price_info)], st),
+        "hjm_price_batch": ([P(hjm_batch_item), C.c_size_t, st, C.c_double, vp, P(hjm_price_info), vp], st),
+        "hjm_field": ([vp, P(hjm_instrument), st, C.c_int, vp], st),
+        "hjm_axis": ([vp, P(hjm_instrument), C.c_int, vp, vp, vp], st),
+        "hjm_douglas_pass": ([vp, P(hjm_instrument), st, C.c_int, C.c_int, vp, vp, vp], st),
+        "hjm_trace_enable": ([st], st),
+        "hjm_trace_read": ([P(hjm_trace), st], st),
+        "hjm_status_string": ([st], C.c_char_p),
+        "hjm_last_error": ([], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
+
+
+lib = _load()
+EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch", "hjm_field",
+            "hjm_axis", "hjm_douglas_pass", "hjm_trace_enable", "hjm_trace_read",
+            "hjm_status_string", "hjm_last_error")
+
+
+class HJMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (hjm_status_string(status), msg))
+        self.status = status
+
+
+def hjm_status_string(status):
+    return lib.hjm_status_string(int(status)).decode()
+
+
+def hjm_last_error():
+    return lib.hjm_last_error().decode()
+
+
+def _check(status):
+    if status != HJM_OK:
+        raise HJMError(status, hjm_last_error())
+
+
+# ------------------------------------------------------------- marshalling
+
+def _struct(t, d, rename=None):
+    s = t()
+    for name, _ in t._fields_:
+        key = (rename or {}).get(name, name)
+        setattr(s, name, d[key])
+    return s
+
+
+def curve_struct(d):
+    return _struct(hjm_curve, d)
+
+
+def model_struct(d):
+    return _struct(hjm_model_params, d)
+
+
+def grid_struct(d):
+    return _struct(hjm_grid_spec, d)
+
+
+def inst_struct(d):
+    return _struct(hjm_instrument, d, {"expiry_T": "T", "pay_TM": "TM", "strike_K": "K"})
+
+
+def batch_item(d):
+    return hjm_batch_item(curve_struct(d["curve"]), model_struct(d["model"]),
+                          grid_struct(d["grid"]), inst_struct(d["inst"]))
+
+
+def _ptr(x):
+    """Address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("expected a tensor, an array or an address")
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- the ABI
+
+def hjm_grid_create(curve, model, spec, stream=None):
+    h = C.c_void_p()
+    _check(lib.hjm_grid_create(C.byref(curve_struct(curve)), C.byref(model_struct(model)),
+                               C.byref(grid_struct(spec)), _stream(stream), C.byref(h)))
+    return h
+
+
+def hjm_grid_destroy(handle):
+    _check(lib.hjm_grid_destroy(handle))
+
+
+def hjm_price(handle, inst, precision=HJM_FP32, tol_rel=1e-4, with_info=False):
+    p = C.c_double()
+    info = hjm_price_info()
+    _check(lib.hjm_price(handle, C.byref(inst_struct(inst)), PRECISIONS[precision], float(tol_rel),
+                         C.byref(p), C.byref(info) if with_info else None))
+    return (p.value, info) if with_info else p.value
+
+
+def make_items(items):
+    arr = (hjm_batch_item * len(items))()
+    for i, d in enumerate(items):
+        arr[i] = batch_item(d)
+    return arr
+
+
+def hjm_price_batch(items, precision=HJM_FP32, tol_rel=1e-4, out=None, infos=False, stream=None):
+    """items: list of item dicts or a ctypes array from make_items(). out:
+    torch tensor (device or host) or numpy array of n doubles; a numpy array
+    is allocated when out is None. Returns out (and infos if asked)."""
+    arr = items if isinstance(items, C.Array) else make_items(items)
+    n = len(arr)
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    inf = (hjm_price_info * n)() if infos else None
+    _check(lib.hjm_price_batch(arr, n, PRECISIONS[precision], float(tol_rel), _ptr(out),
+                               inf, _stream(stream)))
+    return (out, inf) if infos else out
+
+
+def hjm_field(handle, inst, precision, n_run, out):
+    _check(lib.hjm_field(handle, C.byref(inst_struct(inst)), PRECISIONS[precision], int(n_run), _ptr(out)))
+    return out
+
+
+def hjm_axis(handle, inst, axis, n):
+    z, J, J2 = np.empty(n), np.empty(n), np.empty(n)
+    _check(lib.hjm_axis(handle, C.byref(inst_struct(inst)), int(axis), z.ctypes.data, J.ctypes.data,
+                        J2.ctypes.data))
+    return z, J, J2
+
+
+def hjm_douglas_pass(handle, inst, precision, pass_, step_n, inp, inp2, out):
+    _check(lib.hjm_douglas_pass(handle, C.byref(inst_struct(inst)), PRECISIONS[precision], int(pass_),
+                                int(step_n), _ptr(inp), _ptr(inp2), _ptr(out)))
+    return out
+
+
+def hjm_trace_enable(on):
+    _check(lib.hjm_trace_enable(1 if on else 0))
+
+
+def hjm_trace_read(reset=False):
+    """Per-kind launch counts and total device ms, as a dict."""
+    t = hjm_trace()
+    _check(lib.hjm_trace_read(C.byref(t), 1 if reset else 0))
+    return {name: (int(t.launches[i]), float(t.total_ms[i])) for i, name in enumerate(TRACE_KIND_NAMES)}
+
+
+class Grid:
+    """Owning wrapper of an hjm_grid handle built from an item dict."""
+
+    def __init__(self, item, stream=None):
+        self.item = item
+        self.h = hjm_grid_create(item["curve"], item["model"], item["grid"], stream)
+        g = item["grid"]
+        self.shape = (g["n_y"], g["n_v"], g["n_r"])
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            hjm_grid_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    __del__ = close
+
+    def price(self, precision=HJM_FP32, inst=None, with_info=False):
+        return hjm_price(self.h, inst or self.item["inst"], precision, with_info=with_info)
+
+    def field(self, precision, n_run, out):
+        return hjm_field(self.h, self.item["inst"], precision, n_run, out)
+
+    def axis(self, axis):
+        return hjm_axis(self.h, self.item["inst"], axis, self.shape[2 - axis])
+
+    def douglas_pass(self, precision, pass_, step_n, inp, inp2, out):
+        return hjm_douglas_pass(self.h, self.item["inst"], precision, pass_, step_n, inp, inp2, out)

@@ -1,0 +1,248 @@
+"""GPU path vs the CPU FP64 oracle, element by element, through the C ABI.
+
+Tolerances (from the arithmetic, fixed here):
+  FP64 march   fields and prices within 1e-10 relative to the field scale
+               (the oracle and the kernels differ only in rounding order)
+  FP32 march   prices within max(1e-4 |p|, 1e-6); fields within
+               FIELD32 = 16 * (n_steps + 1) * 2^-24 of the field scale (one
+               rounding per operation of a contractive step, accumulated over
+               the steps), checked together with the price criterion
+  one pass     FP64: 1e-12 of the output scale; FP32: 2e-6 of it (a single
+               pass has no accumulation)
+The cases span every chunk width of the r kernel (2, 4, 8, 16 nodes per
+lane), ragged r lengths (not multiples of 32 or of the vector width), both
+Dirichlet and degenerate r = 0 faces (gamma = 0 and gamma = 0.9), first- and
+second-order y faces, flat and Nelson-Siegel curves, bonds and caplets.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1108_1688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1688_gb300 import _build
+    _build.build()
+    from paper_1108_1688_gb300 import hjm
+    return hjm
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _caplet_case(n_r, n_y, n_v, n_steps, seed=0, **grid_kw):
+    it = W.config2_draws(1, seed=W.SEED_BASE + 100 + seed, n_r=n_r, n_y=n_y, n_v=n_v, n_steps=n_steps)[0]
+    it["grid"].update(grid_kw)
+    return it
+
+
+def _bond_gamma(n_r, n_y, n_v, n_steps):
+    return W.paper_2007_set(n_r=n_r, n_y=n_y, n_v=n_v, n_steps=n_steps)
+
+
+CASES = {
+    "config1_bond_M2": lambda: W.config1(),
+    "caplet_ragged_37x11x13": lambda: _caplet_case(37, 11, 13, 12),
+    "caplet_M4_midpoint_NS": lambda: _caplet_case(100, 9, 10, 10, seed=1, explicit_midpoint=1),
+    "caplet_M8_partial_yorder1": lambda: _caplet_case(200, 8, 7, 6, seed=2, y_boundary_order=1),
+    "caplet_M16_partial": lambda: _caplet_case(400, 6, 7, 4, seed=3),
+    "caplet_nr512": lambda: _caplet_case(512, 5, 6, 3, seed=4),
+    "bond_gamma09_nr13": lambda: _bond_gamma(13, 7, 9, 20),
+    "bond_gamma09_nr64": lambda: _bond_gamma(64, 10, 12, 15),
+    "caplet_uniform_5x5x5": lambda: _caplet_case(5, 5, 5, 7, seed=5, alpha_r=0.0, alpha_v=0.0, alpha_y=0.0),
+}
+PRECS = ["fp64", "fp32"]
+
+
+def _ptype(torch, prec):
+    return torch.float64 if prec == "fp64" else torch.float32
+
+
+def field32_tol(n_steps):
+    return 16.0 * (n_steps + 1) * 2.0 ** -24
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_axis_tables(H, orc, name):
+    it = CASES[name]()
+    with H.Grid(it) as g, orc.Ctx(it) as X:
+        for axis in range(3):
+            z, J, J2 = g.axis(axis)
+            zo, Jo, J2o = X.axis(axis)
+            for a, b_ in ((z, zo), (J, Jo), (J2, J2o)):
+                scale = np.max(np.abs(b_)) + 1e-300
+                assert np.max(np.abs(a - b_)) <= 1e-13 * scale, axis
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(CASES))
+def test_terminal_field(H, orc, torch_mod, name, prec):
+    torch = torch_mod
+    it = CASES[name]()
+    with H.Grid(it) as g, orc.Ctx(it) as X:
+        out = torch.empty(g.shape, dtype=_ptype(torch, prec), device="cuda")
+        g.field(prec, 0, out)
+        got = out.double().cpu().numpy()
+        want = X.terminal()
+        tol = 1e-13 if prec == "fp64" else 2.0 ** -23
+        assert np.max(np.abs(got - want)) <= tol * max(np.max(np.abs(want)), 1e-300)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(CASES))
+def test_douglas_passes(H, orc, torch_mod, name, prec):
+    # Each kernel pass against the oracle's corresponding stage, from the same
+    # (oracle-made) input state.
+    torch = torch_mod
+    it = CASES[name]()
+    ns = it["grid"]["n_steps"]
+    n = min(2, ns - 1)
+    with H.Grid(it) as g, orc.Ctx(it) as X:
+        U = X.terminal()
+        for s in range(n):
+            U = X.step(s, U)
+        th = X.time(n + 0.5)
+        dU0 = X.explicit(n, U)
+        dU1 = X.solve_dir(0, th, dU0)
+        dU2 = X.solve_dir(1, th, dU1)
+        U1 = U + X.solve_dir(2, th, dU2)
+        dt = _ptype(torch, prec)
+        tol = 1e-12 if prec == "fp64" else 2e-6
+        dev = lambda a: torch.tensor(a, dtype=dt, device="cuda")
+        out = torch.empty(g.shape, dtype=dt, device="cuda")
+        # pass 1 uses U in the march type: compare against the oracle fed the
+        # same rounded input, so the check isolates the pass itself.
+        Ur = dev(U).double().cpu().numpy()
+        want1 = X.solve_dir(0, th, X.explicit(n, Ur))
+        g.douglas_pass(prec, 1, n, dev(U), None, out)
+        got = out.double().cpu().numpy()
+        assert np.max(np.abs(got - want1)) <= tol * np.max(np.abs(want1)), "pass 1"
+        inp = dev(dU1)
+        want2 = X.solve_dir(1, th, inp.double().cpu().numpy())
+        g.douglas_pass(prec, 2, n, inp, None, inp)  # in place, as in the march
+        got = inp.double().cpu().numpy()
+        assert np.max(np.abs(got - want2)) <= tol * np.max(np.abs(want2)), "pass 2"
+        inp = dev(dU2)
+        Ud = dev(U)
+        want3 = Ud.double().cpu().numpy() + X.solve_dir(2, th, inp.double().cpu().numpy())
+        g.douglas_pass(prec, 3, n, inp, Ud, Ud)  # U updated in place
+        got = Ud.double().cpu().numpy()
+        assert np.max(np.abs(got - want3)) <= tol * np.max(np.abs(want3)), "pass 3"
+        del U1
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", list(CASES))
+def test_march_field_and_price(H, orc, torch_mod, name, prec):
+    torch = torch_mod
+    it = CASES[name]()
+    ns = it["grid"]["n_steps"]
+    with H.Grid(it) as g, orc.Ctx(it) as X:
+        want = X.march()
+        pref = X.readout(want)
+        out = torch.empty(g.shape, dtype=_ptype(torch, prec), device="cuda")
+        g.field(prec, ns, out)
+        got = out.double().cpu().numpy()
+        scale = np.max(np.abs(want))
+        p = g.price(prec)
+        if prec == "fp64":
+            assert np.max(np.abs(got - want)) <= 1e-10 * scale
+            assert abs(p - pref) <= 1e-10 * max(abs(pref), scale * 1e-3)
+        else:
+            assert np.max(np.abs(got - want)) <= field32_tol(ns) * scale
+            assert abs(p - pref) <= max(1e-4 * abs(pref), 1e-6)
+
+
+def test_config1_price_matches_curve(H):
+    # 5y bond, 40 x 20 x 20, 100 steps: price = exp(-0.15) within the paper's
+    # 1e-5 (the oracle's own discretisation error is ~1e-6).
+    with H.Grid(W.config1()) as g:
+        for prec in PRECS:
+            assert abs(g.price(prec) - math.exp(-0.15)) < 1e-5
+
+
+def _mixed_batch():
+    items = []
+    items += W.config2_draws(5, seed=11, n_r=48, n_y=12, n_v=10, n_steps=20)
+    items += W.config2_draws(4, seed=12, n_r=33, n_y=9, n_v=11, n_steps=15)
+    b = W.config1()
+    b["grid"].update(n_steps=30)
+    items.insert(3, b)
+    items += [_bond_gamma(24, 8, 8, 12)]
+    items += W.config3_batch(4, sizes=(64,))
+    for x in items[-4:]:
+        x["grid"].update(n_steps=16)
+    return items
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_batch_of_mixed_shapes(H, orc, torch_mod, prec):
+    torch = torch_mod
+    items = _mixed_batch()
+    want = np.array([orc.price(x) for x in items])
+    host = H.hjm_price_batch(items, prec)
+    dev = torch.full((len(items),), float("nan"), dtype=torch.float64, device="cuda")
+    H.hjm_price_batch(items, prec, out=dev, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy(), host)  # same kernels, same order
+    if prec == "fp64":
+        assert np.all(np.abs(host - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3))
+    else:
+        assert np.all(np.abs(host - want) <= np.maximum(1e-4 * np.abs(want), 1e-6))
+    # batch result equals the single-instrument path
+    with H.Grid(items[3]) as g:
+        assert g.price(prec) == host[3]
+
+
+def test_batch_repeat_is_bitwise_stable(H):
+    items = _mixed_batch()
+    a = H.hjm_price_batch(items, "fp32")
+    b = H.hjm_price_batch(items, "fp32")
+    assert np.array_equal(a, b)
+
+
+def _oracle_prices_parallel(orc, items, workers=4):
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(workers, len(items))) as pool:
+        return np.array(pool.map(orc.price, items))
+
+
+def test_full_size_config2_bench_batch(H, orc, torch_mod):
+    # The bench workload: 100 seeded caplets on 128 x 64 x 64 with 400 steps,
+    # FP32, one batch call. Sampled against the oracle (4 draws, full size)
+    # and, for all 100, against the FP64 GPU path (itself checked above).
+    torch = torch_mod
+    items = W.config2_draws(100)
+    sample = [0, 37, 64, 99]
+    want = _oracle_prices_parallel(orc, [items[i] for i in sample])
+    p32 = torch.empty(100, dtype=torch.float64, device="cuda")
+    H.hjm_price_batch(items, "fp32", out=p32, stream=torch.cuda.current_stream())
+    p64 = H.hjm_price_batch(items, "fp64")
+    torch.cuda.synchronize()
+    p32 = p32.cpu().numpy()
+    assert np.all(np.abs(p32[sample] - want) <= np.maximum(1e-4 * np.abs(want), 1e-6)), (p32[sample], want)
+    assert np.all(np.abs(p64[sample] - want) <= 1e-10 * np.abs(want)), (p64[sample], want)
+    assert np.all(np.abs(p32 - p64) <= np.maximum(1e-4 * np.abs(p64), 1e-6))
+    assert np.all(p64 > 0.0)
+
+
+def test_size_limits(H):
+    it = _caplet_case(512, 5, 5, 2)
+    with H.Grid(it) as g:
+        assert g.price("fp32") > 0.0
+    bad = _caplet_case(513, 5, 5, 2)
+    with pytest.raises(H.HJMError) as ei:
+        H.hjm_grid_create(bad["curve"], bad["model"], bad["grid"])
+    assert ei.value.status == H.HJM_ERANGE
