@@ -44,9 +44,10 @@ typedef enum {
 } hjm_status;
 
 /* Arithmetic of the time march. FP64: state, operator and solves in double.
- * FP32: state, operator and solves in float (setup and readout stay in
- * double). MIXED: FP32 march, then an FP64 re-run of the instrument when the
- * error indicator misses the tolerance. */
+ * FP32: state, operator and solves in float (set-up and read-out stay in
+ * double). MIXED: the FP32 march for every instrument, then an FP64 re-run of
+ * each instrument whose a-posteriori rounding indicator exceeds
+ * max(tol_rel |price|, 1e-6); MIXED synchronises the stream. */
 typedef enum { HJM_FP64 = 0, HJM_FP32 = 1, HJM_MIXED = 2 } hjm_precision;
 
 /* Initial forward curve f(0,t) (Section 2: p(0,T) = exp(-int_0^T f(0,s) ds)).
@@ -105,7 +106,10 @@ typedef struct {
 } hjm_instrument;
 
 /* Per-price report. err_estimate is the a-posteriori rounding indicator of
- * the march that produced the price (0 for FP64). */
+ * the march that produced the price: C u (|p| + sqrt(n_steps) max|U| +
+ * sum_n max|dU3_n|), u the unit roundoff of the march type, the maxima over
+ * the 4 x 4 read-out stencil on y = 0, C a safety factor calibrated against
+ * the FP64 oracle. */
 typedef struct {
     int precision_used;       /* hjm_precision actually used for the price */
     int escalated;            /* 1 if an FP32 result was replaced by FP64 */

@@ -182,12 +182,11 @@ struct Buffer {
     }
 };
 
-// Cached march graphs: key = (precision bytes, shape, B, buffer addresses).
-typedef std::tuple<size_t, int, int, int, int, int, int, const void*, const void*, const void*> GraphKey;
+// Cached batch graphs, keyed by precision, shapes and buffer addresses.
 
 struct Workspace {
     Buffer block;                     // fields + tables of all groups
-    std::map<GraphKey, cudaGraphExec_t> graphs;
+    std::map<std::string, cudaGraphExec_t> graphs;
     void drop_graphs()
     {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -204,6 +203,9 @@ std::mutex g_mu;
 std::map<cudaStream_t, Workspace*> g_ws;  // batch workspaces, one per stream
 bool g_init_done = false;
 cudaStream_t g_capture_stream = nullptr;
+constexpr int kBranches = 8;  // streams the shape groups of a batch graph fork onto
+cudaStream_t g_branch[kBranches];
+std::vector<cudaEvent_t> g_events;
 
 hjm_status ensure_init()
 {
@@ -213,6 +215,7 @@ hjm_status ensure_init()
         return fail(HJM_ECUDA, "no CUDA device");
     CU_TRY(init_kernels());
     CU_TRY(cudaStreamCreateWithFlags(&g_capture_stream, cudaStreamNonBlocking));
+    for (int q = 0; q < kBranches; ++q) CU_TRY(cudaStreamCreateWithFlags(&g_branch[q], cudaStreamNonBlocking));
     g_init_done = true;
     return HJM_OK;
 }
@@ -227,6 +230,7 @@ struct Group {
     void* U = nullptr;
     void* A = nullptr;
     double* prices = nullptr;
+    double* ind = nullptr;  // rounding indicators
 };
 
 // ------------------------------------------------------------ tracing
@@ -299,7 +303,7 @@ hjm_status run_steps(const Group& g, int n_from, int n_to, cudaStream_t s)
         }
         {
             TraceScope ts(4, s);
-            CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, s));
+            CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, n, s));
         }
     }
     return HJM_OK;
@@ -311,23 +315,66 @@ hjm_status run_steps_any(const Group& g, size_t elem, int n_from, int n_to, cuda
                                  : run_steps<double>(g, n_from, n_to, s);
 }
 
-// The whole march of a group as one graph launch (captured once per shape
-// and buffer set, then replayed).
-hjm_status march_graph(Workspace& ws, const Group& g, size_t elem, cudaStream_t s)
+// Set-up, terminal field, the n_steps x 3 passes and the read-out of one
+// group, in order on stream s.
+hjm_status group_sequence(const Group& g, size_t elem, cudaStream_t s)
 {
-    GraphKey key(elem, g.nr, g.nv, g.ny, g.nsteps, g.t.B, (int)g.gpos, g.U, g.A, g.t.rt);
+    {
+        TraceScope ts(0, s);
+        CU_TRY(launch_setup(g.t, elem, s));
+    }
+    {
+        TraceScope ts(1, s);
+        CU_TRY(launch_terminal(g.t, g.U, elem, s));
+    }
+    hjm_status st = run_steps_any(g, elem, 0, g.nsteps, s);
+    if (st != HJM_OK) return st;
+    TraceScope ts(5, s);
+    CU_TRY(launch_readout(g.t, g.U, elem, g.prices, g.ind, s));
+    return HJM_OK;
+}
+
+// The whole batch as one CUDA-graph launch: every shape group is a branch of
+// the graph (fork from one node, join into one), so groups of different
+// sizes run concurrently and fill the GPU together. Captured once per set of
+// shapes and buffers, then replayed.
+hjm_status batch_graph(Workspace& ws, const std::vector<Group>& groups, size_t elem, cudaStream_t s)
+{
+    std::string key = std::to_string(elem);
+    for (const auto& g : groups) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%p,%p,%p", g.nr, g.nv, g.ny, g.nsteps, g.t.B,
+                 (int)g.gpos, g.U, g.A, g.t.rt);
+        key += buf;
+    }
     auto it = ws.graphs.find(key);
     if (it == ws.graphs.end()) {
         if (ws.graphs.size() > 64) ws.drop_graphs();
-        cudaGraph_t graph = nullptr;
-        CU_TRY(cudaStreamBeginCapture(g_capture_stream, cudaStreamCaptureModeThreadLocal));
-        hjm_status st = run_steps_any(g, elem, 0, g.nsteps, g_capture_stream);
-        cudaError_t e = cudaStreamEndCapture(g_capture_stream, &graph);
-        if (st != HJM_OK) {
-            if (graph) cudaGraphDestroy(graph);
-            return st;
+        while (g_events.size() < groups.size() + 1) {
+            cudaEvent_t e;
+            CU_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            g_events.push_back(e);
         }
-        CU_TRY(e);
+        cudaGraph_t graph = nullptr;
+        cudaStream_t cs = g_capture_stream;
+        CU_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+        hjm_status st = HJM_OK;
+        cudaError_t e = cudaEventRecord(g_events[0], cs);
+        for (size_t q = 0; q < groups.size() && st == HJM_OK && e == cudaSuccess; ++q) {
+            cudaStream_t bs = g_branch[q % kBranches];
+            e = cudaStreamWaitEvent(bs, g_events[0], 0);
+            if (e != cudaSuccess) break;
+            st = group_sequence(groups[q], elem, bs);
+            if (st != HJM_OK) break;
+            e = cudaEventRecord(g_events[q + 1], bs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, g_events[q + 1], 0);
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+        if (st != HJM_OK || e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            if (st != HJM_OK) return st;
+            CU_TRY(e != cudaSuccess ? e : e2);
+        }
         cudaGraphExec_t exec = nullptr;
         e = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -357,7 +404,7 @@ bool is_device_ptr(const void* p)
 // Plan the groups of a batch and carve their buffers out of the workspace.
 hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
                 std::vector<Group>& groups, InstParams** d_params, long long** d_idx,
-                double** d_prices_all)
+                double** d_prices_all, double** d_ind_all = nullptr)
 {
     std::map<std::tuple<int, int, int, int>, size_t> where;
     for (size_t i = 0; i < n; ++i) {
@@ -378,7 +425,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         gr.gpos = gr.gpos || items[i].model.gamma > 0.0;
     }
     size_t bytes = align256(n * sizeof(InstParams)) + align256(n * sizeof(long long)) +
-                   2 * align256(n * sizeof(double));
+                   4 * align256(n * sizeof(double));
     for (auto& g : groups) {
         const size_t B = g.idx.size();
         const size_t N = (size_t)g.nr * g.nv * g.ny;
@@ -398,6 +445,10 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
     p += align256(n * sizeof(double));
     double* group_prices = (double*)p;
     p += align256(n * sizeof(double));
+    if (d_ind_all) *d_ind_all = (double*)p;
+    p += align256(n * sizeof(double));
+    double* group_ind = (double*)p;
+    p += align256(n * sizeof(double));
     size_t off = 0;
     for (auto& g : groups) {
         const size_t B = g.idx.size();
@@ -413,6 +464,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         g.t.B = (int)B;
         g.t.params = *d_params + off;
         g.prices = group_prices + off;
+        g.ind = group_ind + off;
         tables_carve(g.t, p, elem);
         p += tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
         off += B;
@@ -429,27 +481,20 @@ Workspace* stream_workspace(cudaStream_t s)
     return w;
 }
 
-// Core of hjm_price_batch (caller holds g_mu).
-hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm_precision prec,
-                       double* prices_out, hjm_price_info* infos, cudaStream_t s)
+// Enqueue set-up, march and read-out of a whole batch in one precision on
+// stream s. On return *d_prices and *d_ind (device, caller order, inside the
+// workspace) will hold the prices and rounding indicators once the stream
+// reaches them. Caller holds g_mu and has validated the items.
+hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
+                       cudaStream_t s, double** d_prices_out, double** d_ind_out)
 {
-    if (prec == HJM_MIXED)
-        return fail(HJM_EINVAL, "MIXED precision is not available in this build");
-    const size_t elem = prec == HJM_FP32 ? sizeof(float) : sizeof(double);
-    for (size_t i = 0; i < n; ++i) {
-        hjm_status st = validate(items[i].curve, items[i].model, items[i].grid, &items[i].inst, elem);
-        if (st != HJM_OK) {
-            std::string why = g_last_error;
-            return fail(st, "item %zu: %s", i, why.c_str());
-        }
-    }
     std::vector<Group> groups;
     InstParams* d_params;
     long long* d_idx;
     double* d_prices;
-    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices);
+    double* d_ind;
+    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices, &d_ind);
     if (st != HJM_OK) return st;
-
     // Parameters in group order, and the scatter map back to caller order.
     std::vector<InstParams> hp;
     std::vector<long long> order;
@@ -460,59 +505,115 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
             hp.push_back(to_params(items[i]));
             order.push_back((long long)i);
         }
+    CU_TRY(cudaMemcpyAsync(d_params, hp.data(), n * sizeof(InstParams), cudaMemcpyHostToDevice, s));
+    CU_TRY(cudaMemcpyAsync(d_idx, order.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s));
+    if (g_trace_on) {
+        for (auto& g : groups) {
+            st = group_sequence(g, elem, s);
+            if (st != HJM_OK) return st;
+        }
+    } else {
+        st = batch_graph(ws, groups, elem, s);
+        if (st != HJM_OK) return st;
+    }
+    // group order -> caller order
+    k_scatter<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].prices, d_idx, (int)n, d_prices);
+    CU_TRY(cudaGetLastError());
+    k_scatter<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].ind, d_idx, (int)n, d_ind);
+    CU_TRY(cudaGetLastError());
+    *d_prices_out = d_prices;
+    *d_ind_out = d_ind;
+    return HJM_OK;
+}
+
+// Core of hjm_price_batch (caller holds g_mu, items validated).
+//  FP32 / FP64: one march in that precision.
+//  MIXED: the FP32 march; every instrument whose rounding indicator exceeds
+//  max(tol_rel |p|, 1e-6) (or whose price is not finite) is priced again in
+//  FP64 and reported as escalated. MIXED synchronises the stream.
+hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm_precision prec,
+                       double tol_rel, double* prices_out, hjm_price_info* infos, cudaStream_t s)
+{
+    const size_t elem = prec == HJM_FP64 ? sizeof(double) : sizeof(float);
+    const bool dev_out = is_device_ptr(prices_out);
+    const bool sync = !dev_out || infos != nullptr || prec == HJM_MIXED || g_trace_on;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    const bool timing = infos != nullptr;
-    if (timing) {
+    if (infos) {
         CU_TRY(cudaEventCreate(&ev0));
         CU_TRY(cudaEventCreate(&ev1));
         CU_TRY(cudaEventRecord(ev0, s));
     }
-    CU_TRY(cudaMemcpyAsync(d_params, hp.data(), n * sizeof(InstParams), cudaMemcpyHostToDevice, s));
-    CU_TRY(cudaMemcpyAsync(d_idx, order.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s));
-    for (auto& g : groups) {
-        {
-            TraceScope ts(0, s);
-            CU_TRY(launch_setup(g.t, elem, s));
+    double *d_prices, *d_ind;
+    hjm_status st = march_batch(ws, items, n, elem, s, &d_prices, &d_ind);
+    if (st != HJM_OK) return st;
+    std::vector<double> hp, hi;
+    std::vector<int> used(n, prec == HJM_FP64 ? HJM_FP64 : HJM_FP32), esc(n, 0);
+    if (sync) {
+        hp.resize(n);
+        hi.resize(n);
+        CU_TRY(cudaMemcpyAsync(hp.data(), d_prices, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaMemcpyAsync(hi.data(), d_ind, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaStreamSynchronize(s));
+        if (g_trace_on) trace_collect();
+    }
+    if (prec == HJM_MIXED) {
+        std::vector<hjm_batch_item> redo;
+        std::vector<size_t> where;
+        for (size_t i = 0; i < n; ++i) {
+            const double lim = fmax(tol_rel * fabs(hp[i]), 1e-6);
+            if (!isfinite(hp[i]) || !(hi[i] <= lim)) {
+                redo.push_back(items[i]);
+                where.push_back(i);
+            }
         }
-        {
-            TraceScope ts(1, s);
-            CU_TRY(launch_terminal(g.t, g.U, elem, s));
-        }
-        st = g_trace_on ? run_steps_any(g, elem, 0, g.nsteps, s) : march_graph(ws, g, elem, s);
-        if (st != HJM_OK) return st;
-        {
-            TraceScope ts(5, s);
-            CU_TRY(launch_readout(g.t, g.U, elem, g.prices, s));
+        if (!redo.empty()) {
+            st = march_batch(ws, redo.data(), redo.size(), sizeof(double), s, &d_prices, &d_ind);
+            if (st != HJM_OK) return st;
+            std::vector<double> p64(redo.size()), i64(redo.size());
+            CU_TRY(cudaMemcpyAsync(p64.data(), d_prices, redo.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaMemcpyAsync(i64.data(), d_ind, redo.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            if (g_trace_on) trace_collect();
+            for (size_t q = 0; q < redo.size(); ++q) {
+                hp[where[q]] = p64[q];
+                hi[where[q]] = i64[q];
+                used[where[q]] = HJM_FP64;
+                esc[where[q]] = 1;
+            }
         }
     }
-    // group-ordered prices -> caller order
-    k_scatter<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].prices, d_idx, (int)n, d_prices);
-    CU_TRY(cudaGetLastError());
-    const bool dev_out = is_device_ptr(prices_out);
-    if (dev_out) {
-        CU_TRY(cudaMemcpyAsync(prices_out, d_prices, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (infos) CU_TRY(cudaEventRecord(ev1, s));
+    if (sync) {
+        if (dev_out)
+            CU_TRY(cudaMemcpyAsync(prices_out, hp.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+        else
+            memcpy(prices_out, hp.data(), n * sizeof(double));
     } else {
-        CU_TRY(cudaMemcpyAsync(prices_out, d_prices, n * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU_TRY(cudaMemcpyAsync(prices_out, d_prices, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
-    if (timing) CU_TRY(cudaEventRecord(ev1, s));
-    if (!dev_out || timing || g_trace_on) CU_TRY(cudaStreamSynchronize(s));
-    if (g_trace_on) trace_collect();
-    if (!dev_out)
-        for (size_t i = 0; i < n; ++i)
-            if (!isfinite(prices_out[i])) return fail(HJM_ENUMERIC, "item %zu: price is not finite", i);
-    if (timing) {
+    if (infos) {
+        CU_TRY(cudaEventSynchronize(ev1));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev0, ev1);
         cudaEventDestroy(ev0);
         cudaEventDestroy(ev1);
         for (size_t i = 0; i < n; ++i) {
-            infos[i].precision_used = prec;
-            infos[i].escalated = 0;
-            infos[i].err_estimate = 0.0;
+            infos[i].precision_used = used[i];
+            infos[i].escalated = esc[i];
+            infos[i].err_estimate = hi[i];
             infos[i].n_steps = items[i].grid.n_steps;
             infos[i].time_us = ms * 1000.f;
             infos[i].tile_cfg = pass1_chunk(items[i].grid.n_r);
         }
+    }
+    if (sync) {
+        if (dev_out) CU_TRY(cudaStreamSynchronize(s));  // hp is a local buffer
+        for (size_t i = 0; i < n; ++i)
+            if (!isfinite(hp[i])) return fail(HJM_ENUMERIC, "item %zu: price is not finite", i);
+        if (prec == HJM_MIXED)
+            for (size_t i = 0; i < n; ++i)
+                if (!(hi[i] <= fmax(tol_rel * fabs(hp[i]), 1e-6)))
+                    return fail(HJM_ETOL, "item %zu: indicator %.3g above tolerance after escalation", i, hi[i]);
     }
     return HJM_OK;
 }
@@ -572,7 +673,6 @@ static hjm_batch_item grid_item(const hjm_grid* g, const hjm_instrument* inst)
 extern "C" hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
                                 double tol_rel, double* price_out, hjm_price_info* info_out)
 {
-    (void)tol_rel;
     if (!grid || !inst || !price_out) return fail(HJM_EINVAL, "null argument");
     if (precision != HJM_FP64 && precision != HJM_FP32 && precision != HJM_MIXED)
         return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
@@ -580,8 +680,15 @@ extern "C" hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
     const hjm_batch_item it = grid_item(grid, inst);
+    st = validate(it.curve, it.model, it.grid, &it.inst,
+                  precision == HJM_FP64 ? sizeof(double) : sizeof(float));
+    if (st != HJM_OK) return st;
+    if (precision == HJM_MIXED) {
+        st = validate(it.curve, it.model, it.grid, &it.inst, sizeof(double));
+        if (st != HJM_OK) return st;
+    }
     double p = 0.0;
-    st = price_batch(grid->ws, &it, 1, precision, &p, info_out, grid->stream);
+    st = price_batch(grid->ws, &it, 1, precision, tol_rel, &p, info_out, grid->stream);
     if (st != HJM_OK) return st;
     *price_out = p;
     return HJM_OK;
@@ -591,11 +698,12 @@ extern "C" hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm
                                       double tol_rel, double* prices_out, hjm_price_info* infos_out,
                                       void* cuda_stream)
 {
-    (void)tol_rel;
     if (n == 0) return HJM_OK;
     if (!items || !prices_out) return fail(HJM_EINVAL, "null argument");
     if (precision != HJM_FP64 && precision != HJM_FP32 && precision != HJM_MIXED)
         return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    if (!(tol_rel >= 0.0)) return fail(HJM_EINVAL, "tol_rel must be >= 0");
+    // MIXED may re-run any item in FP64, so it must fit the FP64 kernels too.
     const size_t elem = precision == HJM_FP32 ? sizeof(float) : sizeof(double);
     for (size_t i = 0; i < n; ++i) {
         hjm_status st = validate(items[i].curve, items[i].model, items[i].grid, &items[i].inst, elem);
@@ -608,7 +716,7 @@ extern "C" hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    return price_batch(*stream_workspace(s), items, n, precision, prices_out, infos_out, s);
+    return price_batch(*stream_workspace(s), items, n, precision, tol_rel, prices_out, infos_out, s);
 }
 
 // ---------------------------------------------------------- stepwise access
@@ -700,13 +808,13 @@ extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* ins
         if (pass == 1) CU_TRY(launch_pass1<float>(P, (const float*)in, (float*)out, step_n, s));
         if (pass == 2) CU_TRY(launch_pass2<float>(P, (const float*)in, (float*)out, s));
         if (pass == 3)
-            CU_TRY(launch_pass3<float>(P, (const float*)in, (const float*)in2, (float*)out, g.gpos, s));
+            CU_TRY(launch_pass3<float>(P, (const float*)in, (const float*)in2, (float*)out, g.gpos, step_n, s));
     } else {
         const March<double> P = march_args<double>(g.t);
         if (pass == 1) CU_TRY(launch_pass1<double>(P, (const double*)in, (double*)out, step_n, s));
         if (pass == 2) CU_TRY(launch_pass2<double>(P, (const double*)in, (double*)out, s));
         if (pass == 3)
-            CU_TRY(launch_pass3<double>(P, (const double*)in, (const double*)in2, (double*)out, g.gpos, s));
+            CU_TRY(launch_pass3<double>(P, (const double*)in, (const double*)in2, (double*)out, g.gpos, step_n, s));
     }
     CU_TRY(cudaStreamSynchronize(s));
     return HJM_OK;

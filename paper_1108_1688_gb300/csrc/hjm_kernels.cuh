@@ -3,9 +3,9 @@
 // Data layout in device memory (one "group" = instruments of equal grid
 // shape that march together in the same launches; b indexes the group):
 //   field    U[b][j][k][i]            i on r (fastest), k on v, j on y
-//   r tables rt[b][RT_N][n_r]         per-node factors of the r operator
-//   v tables vt[b][VT_N][n_v]
-//   y tables yt[b][YT_N][n_y]
+//   r tables rt[b][RT_N][n_r]         per-node factors of the r operator,
+//   v tables vt[b][VT_N][n_v]         with the grid spacings of the centred
+//   y tables yt[b][YT_N][n_y]         differences folded in (see k_setup)
 //   scalars  sc[b][SC_N]              dt, theta*dt, 1/h per axis
 //   steps    st[b][n_steps][2]        a(t) = df(0,t)/dt + kappa f(0,t) for
 //                                     the explicit and the implicit stage
@@ -13,8 +13,10 @@
 //   v LU     vf[b][3][n_v]            Thomas factors of I - theta dt A_v
 //   y LU     yf[b][n_v][3][n_y]       Thomas factors of I - theta dt A_y
 //                                     (gamma == 0 instruments only)
-//   flags    fl[b][4]                 r_min Dirichlet, y face order, y LU
-//                                     present, unused
+//   flags    fl[b][FL_N]              r_min Dirichlet, y face order, y LU
+//                                     present, read-out stencil corner (i, k)
+//   indicator acc[b][n_steps] (float) max |dU3| of each step over the 4 x 4
+//                                     read-out stencil on y = 0
 // All tables are built in FP64 on the device and stored in the march type.
 #pragma once
 
@@ -48,11 +50,16 @@ struct InstDerived {
     double centre_r; // metric centre in r
 };
 
+// Safety factor of the a-posteriori rounding indicator, calibrated against
+// the oracle by the precision-control tests (it must bound the measured
+// FP32-march error of every tested instrument).
+constexpr double kIndicatorC = 8.0;
+
 enum { RT_R, RT_IJ, RT_C1, RT_C4V, RT_C4B, RT_C3, RT_CY, RT_N };
 enum { VT_V, VT_IJ, VT_G2, VT_G5, VT_FV, VT_N };
 enum { YT_Y, YT_IJ, YT_KY, YT_N };
 enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_N };
-enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_PAD, FL_N };
+enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_RI0, FL_RK0, FL_PAD, FL_N };
 
 template <typename T>
 struct March {
@@ -67,6 +74,7 @@ struct March {
     const T* vf;
     const T* yf;
     const int* fl;
+    float* acc;  // [B][nsteps], rounding indicator of the FP32 march
 };
 
 // Group buffers produced by setup (all device pointers).
@@ -86,6 +94,7 @@ struct GroupTables {
     void* vf;
     void* yf;
     int* fl;
+    float* acc;           // [B][nsteps]
 };
 
 // Bytes of the march-type tables of a group.
@@ -97,9 +106,10 @@ void tables_carve(GroupTables& g, void* block, size_t elem);
 cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s);
 // Terminal field U^0 (Section 7.2 cell average for caplets, 1 for bonds).
 cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStream_t s);
-// FP64 readout of every instrument's price into prices[B].
+// FP64 readout of every instrument's price into prices[B]; when indicators
+// is not null also the a-posteriori rounding indicator of the march.
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           cudaStream_t s);
+                           double* indicators, cudaStream_t s);
 
 // The three Douglas passes of step n (in/out as documented in hjm.h).
 template <typename T>
@@ -108,7 +118,7 @@ template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
-                         cudaStream_t s);
+                         int n, cudaStream_t s);
 // Raises the dynamic shared-memory limit of the strided-line kernels; call
 // once per device before launching or capturing.
 cudaError_t init_kernels();

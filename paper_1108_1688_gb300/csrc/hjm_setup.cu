@@ -97,6 +97,19 @@ __device__ double metric_z(double xi, double z0, double z1, double alpha, double
     return z;
 }
 
+// Read-out point r = f(0,0), v = v0 in node units and the first node of the
+// 4-point stencil in each direction, kept inside the grid.
+__device__ void readout_stencil(const InstParams& p, const InstDerived& D, int nr, int nv, int& i0,
+                                int& k0, double* sr = nullptr, double* sv = nullptr)
+{
+    const double r = metric_inverse(fwd(p, 0.0), p.rmin, p.rmax, p.ar, D.centre_r) * (nr - 1);
+    const double v = metric_inverse(p.v0, 0.0, p.vmax, p.av, p.kv) * (nv - 1);
+    i0 = min(max((int)floor(r) - 1, 0), nr - 4);
+    k0 = min(max((int)floor(v) - 1, 0), nv - 4);
+    if (sr) *sr = r;
+    if (sv) *sv = v;
+}
+
 // ------------------------------------------------------------------ setup
 
 template <typename T>
@@ -132,7 +145,10 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
 
     // r axis and r-operator factors: A_r = g1 d_rr + g4 d_r - r with
     // g1 = zeta_rr / J^2, g4 = mu_r / J - zeta_rr J2 / J^3 (Section 4.3),
-    // zeta_rr = lambda^2 r^{2 gamma} v / 2, mu_r = a(t) - kappa r + y.
+    // zeta_rr = lambda^2 r^{2 gamma} v / 2, mu_r = a(t) - kappa r + y. The
+    // grid spacings of the centred differences are folded in: the kernels
+    // multiply the tables by v, a(t) + y and the undivided differences.
+    const double ihr = nr - 1, ihv = nv - 1, ihy = ny - 1;
     for (int i = tid; i < nr; i += nth) {
         double z, J, J2;
         metric((double)i / (nr - 1), p.rmin, p.rmax, p.ar, D.centre_r, z, J, J2);
@@ -142,11 +158,11 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         const double rg = p.gamma == 0.0 ? 1.0 : pow(z, p.gamma);
         const double r2g = rg * rg;
         rt[RT_R * nr + i] = (T)z;
-        rt[RT_IJ * nr + i] = (T)(1.0 / J);
-        rt[RT_C1 * nr + i] = (T)(0.5 * lam2 * r2g / (J * J));
-        rt[RT_C4V * nr + i] = (T)(0.5 * lam2 * r2g * J2 / (J * J * J));
-        rt[RT_C4B * nr + i] = (T)(-p.kappa * z / J);
-        rt[RT_C3 * nr + i] = (T)(p.lambda * rg * p.eps * p.rho / J);
+        rt[RT_IJ * nr + i] = (T)(0.5 * ihr / J);
+        rt[RT_C1 * nr + i] = (T)(0.5 * lam2 * r2g / (J * J) * ihr * ihr);
+        rt[RT_C4V * nr + i] = (T)(0.5 * lam2 * r2g * J2 / (J * J * J) * 0.5 * ihr);
+        rt[RT_C4B * nr + i] = (T)(-p.kappa * z / J * 0.5 * ihr);
+        rt[RT_C3 * nr + i] = (T)(p.lambda * rg * p.eps * p.rho / J * 0.25 * ihr * ihv);
         rt[RT_CY * nr + i] = (T)(lam2 * r2g);
     }
     // v axis: A_v = g2 d_vv + g5 d_v, g2 = zeta_vv / J^2,
@@ -160,9 +176,9 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         const double zvv = 0.5 * eps2 * z, muv = p.theta * (1.0 - z);
         vt[VT_V * nv + k] = (T)z;
         vt[VT_IJ * nv + k] = (T)(1.0 / J);
-        vt[VT_G2 * nv + k] = (T)(zvv / (J * J));
-        vt[VT_G5 * nv + k] = (T)(muv / J - zvv * J2 / (J * J * J));
-        vt[VT_FV * nv + k] = (T)(muv / J);
+        vt[VT_G2 * nv + k] = (T)(zvv / (J * J) * ihv * ihv);
+        vt[VT_G5 * nv + k] = (T)((muv / J - zvv * J2 / (J * J * J)) * 0.5 * ihv);
+        vt[VT_FV * nv + k] = (T)(muv / J * 0.5 * ihv);
     }
     // y axis: A_y = g6 d_y, g6 = (lambda^2 r^{2 gamma} v - 2 kappa y) / J.
     for (int j = tid; j < ny; j += nth) {
@@ -172,7 +188,7 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         axy[ny + j] = J;
         axy[2 * ny + j] = J2;
         yt[YT_Y * ny + j] = (T)z;
-        yt[YT_IJ * ny + j] = (T)(1.0 / J);
+        yt[YT_IJ * ny + j] = (T)(0.5 * ihy / J);
         yt[YT_KY * ny + j] = (T)(-2.0 * p.kappa * z);
     }
     if (tid == 0) {
@@ -186,8 +202,13 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         fl[FL_RLO_DIR] = p.gamma == 0.0;
         fl[FL_YORDER] = p.yorder;
         fl[FL_YLU] = p.gamma == 0.0;
+        int i0, k0;
+        readout_stencil(p, D, nr, nv, i0, k0);
+        fl[FL_RI0] = i0;
+        fl[FL_RK0] = k0;
         fl[FL_PAD] = 0;
     }
+    for (int n = tid; n < ns; n += nth) g.acc[(size_t)b * ns + n] = 0.0f;
     // a(t) = df(0,t)/dt + kappa f(0,t): F at t^n (or t^{n+1/2}), implicit
     // operators at t^{n+1/2} (Section 5, delta form).
     T* st = (T*)g.st + (size_t)b * ns * 2;
@@ -354,17 +375,16 @@ __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
 // Lagrange interpolation in the computational coordinates on the 4 x 4
 // nodes nearest the point, kept inside the grid.
 template <typename T>
-__global__ void k_readout(GroupTables g, const T* U, double* prices)
+__global__ void k_readout(GroupTables g, const T* U, double* prices, double* indicators)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.B) return;
     const InstParams p = g.params[b];
     const InstDerived D = g.derived[b];
     const int nr = g.nr, nv = g.nv;
-    const double sr = metric_inverse(fwd(p, 0.0), p.rmin, p.rmax, p.ar, D.centre_r) * (nr - 1);
-    const double sv = metric_inverse(p.v0, 0.0, p.vmax, p.av, p.kv) * (nv - 1);
-    const int i0 = min(max((int)floor(sr) - 1, 0), nr - 4);
-    const int k0 = min(max((int)floor(sv) - 1, 0), nv - 4);
+    double sr, sv;
+    int i0, k0;
+    readout_stencil(p, D, nr, nv, i0, k0, &sr, &sv);
     double wr[4], wv[4];
     for (int a = 0; a < 4; ++a) {
         double pr = 1.0, pv = 1.0;
@@ -384,6 +404,18 @@ __global__ void k_readout(GroupTables g, const T* U, double* prices)
         s += wv[c] * row;
     }
     prices[b] = s;
+    if (indicators) {
+        // A-posteriori rounding indicator of the march (reading of the
+        // precision-control step): unit roundoff of the march type times the
+        // price, the random-walk growth of the per-step rounding of U over
+        // the stencil, and the summed per-step increments on the stencil.
+        double umax = 0.0, incr = 0.0;
+        for (int c = 0; c < 4; ++c)
+            for (int a = 0; a < 4; ++a) umax = fmax(umax, fabs((double)Ub[(long long)(k0 + c) * nr + i0 + a]));
+        for (int n = 0; n < g.nsteps; ++n) incr += (double)g.acc[(size_t)b * g.nsteps + n];
+        const double u = sizeof(T) == 4 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+        indicators[b] = kIndicatorC * u * (fabs(s) + sqrt((double)g.nsteps) * umax + incr);
+    }
 }
 
 // ------------------------------------------------------------- launchers
@@ -402,6 +434,7 @@ size_t tables_bytes(int nr, int nv, int ny, int nsteps, int B, size_t elem)
     s += align_up((size_t)B * 3 * nv * elem);
     s += align_up((size_t)B * nv * 3 * ny * elem);
     s += align_up((size_t)B * FL_N * sizeof(int));
+    s += align_up((size_t)B * nsteps * sizeof(float));
     s += align_up((size_t)B * 3 * (nr + nv + ny) * sizeof(double));
     s += align_up((size_t)B * sizeof(InstDerived));
     return s;
@@ -425,6 +458,7 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
     g.vf = take(B * 3 * g.nv * elem);
     g.yf = take(B * g.nv * 3 * g.ny * elem);
     g.fl = (int*)take(B * FL_N * sizeof(int));
+    g.acc = (float*)take(B * g.nsteps * sizeof(float));
     double* ax = (double*)take(B * 3 * (g.nr + g.nv + g.ny) * sizeof(double));
     g.axr = ax;
     g.axv = ax + B * 3 * g.nr;
@@ -453,13 +487,13 @@ cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStre
 }
 
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           cudaStream_t s)
+                           double* indicators, cudaStream_t s)
 {
     const int blocks = (g.B + 63) / 64;
     if (elem == sizeof(float))
-        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices);
+        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices, indicators);
     else
-        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices);
+        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators);
     return cudaGetLastError();
 }
 
@@ -482,6 +516,7 @@ March<T> march_args(const GroupTables& g)
     P.vf = (const T*)g.vf;
     P.yf = (const T*)g.yf;
     P.fl = g.fl;
+    P.acc = g.acc;
     return P;
 }
 

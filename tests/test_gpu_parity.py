@@ -7,8 +7,9 @@ Tolerances (from the arithmetic, fixed here):
                FIELD32 = 16 * (n_steps + 1) * 2^-24 of the field scale (one
                rounding per operation of a contractive step, accumulated over
                the steps), checked together with the price criterion
-  one pass     FP64: 1e-12 of the output scale; FP32: 2e-6 of it (a single
-               pass has no accumulation)
+  one pass     FP64: 1e-12, FP32: 2e-6 of the larger of the input and output
+               scales (a single pass has no accumulation; pass 1 forms dt F(U)
+               as differences of U, so its rounding scales with |U|)
 The cases span every chunk width of the r kernel (2, 4, 8, 16 nodes per
 lane), ragged r lengths (not multiples of 32 or of the vector width), both
 Dirichlet and degenerate r = 0 faces (gamma = 0 and gamma = 0.9), first- and
@@ -127,18 +128,18 @@ def test_douglas_passes(H, orc, torch_mod, name, prec):
         want1 = X.solve_dir(0, th, X.explicit(n, Ur))
         g.douglas_pass(prec, 1, n, dev(U), None, out)
         got = out.double().cpu().numpy()
-        assert np.max(np.abs(got - want1)) <= tol * np.max(np.abs(want1)), "pass 1"
+        assert np.max(np.abs(got - want1)) <= tol * max(np.max(np.abs(want1)), np.max(np.abs(U))), "pass 1"
         inp = dev(dU1)
         want2 = X.solve_dir(1, th, inp.double().cpu().numpy())
         g.douglas_pass(prec, 2, n, inp, None, inp)  # in place, as in the march
         got = inp.double().cpu().numpy()
-        assert np.max(np.abs(got - want2)) <= tol * np.max(np.abs(want2)), "pass 2"
+        assert np.max(np.abs(got - want2)) <= tol * max(np.max(np.abs(want2)), np.max(np.abs(dU1))), "pass 2"
         inp = dev(dU2)
         Ud = dev(U)
         want3 = Ud.double().cpu().numpy() + X.solve_dir(2, th, inp.double().cpu().numpy())
         g.douglas_pass(prec, 3, n, inp, Ud, Ud)  # U updated in place
         got = Ud.double().cpu().numpy()
-        assert np.max(np.abs(got - want3)) <= tol * np.max(np.abs(want3)), "pass 3"
+        assert np.max(np.abs(got - want3)) <= tol * max(np.max(np.abs(want3)), np.max(np.abs(dU2))), "pass 3"
         del U1
 
 

@@ -1,0 +1,92 @@
+"""Precision control through the C ABI: the FP32 march's a-posteriori
+rounding indicator bounds its measured error against the FP64 oracle, and
+MIXED re-runs in FP64 exactly the instruments whose indicator misses the
+tolerance max(tol_rel |p|, 1e-6)."""
+import numpy as np
+import pytest
+
+from paper_1108_1688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1688_gb300 import _build
+    _build.build()
+    from paper_1108_1688_gb300 import hjm
+    return hjm
+
+
+def _instruments():
+    items = [W.config1(), W.paper_2007_set(n_r=24, n_y=10, n_v=10, n_steps=60)]
+    items += W.config2_draws(6, seed=W.SEED_BASE + 40, n_r=64, n_y=24, n_v=24, n_steps=120)
+    items += W.config3_batch(6, sizes=(64, 96))
+    for x in items[-6:]:
+        x["grid"]["n_steps"] = 96
+    b = W.config1()
+    b["grid"].update(n_steps=600)  # many steps: rounding of U accumulates
+    items.append(b)
+    return items
+
+
+def test_indicator_bounds_fp32_error(H, orc):
+    items = _instruments()
+    want = np.array([orc.price(x) for x in items])
+    p32, inf = H.hjm_price_batch(items, "fp32", infos=True)
+    err = np.abs(p32 - want)
+    ind = np.array([inf[i].err_estimate for i in range(len(items))])
+    assert np.all(ind > 0)
+    assert np.all(err <= ind), list(zip(err, ind))
+    # FP64 indicators are at FP64 roundoff scale
+    p64, inf64 = H.hjm_price_batch(items, "fp64", infos=True)
+    ind64 = np.array([inf64[i].err_estimate for i in range(len(items))])
+    assert np.all(ind64 < 1e-9 * np.maximum(np.abs(p64), 1.0))
+    assert np.all(np.abs(p64 - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3))
+
+
+def test_mixed_keeps_fp32_when_within_tolerance(H):
+    items = W.config2_draws(4, seed=W.SEED_BASE + 41, n_r=48, n_y=16, n_v=16, n_steps=60)
+    p32 = H.hjm_price_batch(items, "fp32")
+    pm, inf = H.hjm_price_batch(items, "mixed", tol_rel=1e-4, infos=True)
+    assert np.array_equal(pm, p32)
+    assert all(inf[i].escalated == 0 and inf[i].precision_used == H.HJM_FP32 for i in range(4))
+
+
+def test_mixed_escalates_exactly_the_flagged_items(H, torch_dev):
+    torch = torch_dev
+    long_bond = W.config1()
+    long_bond["grid"].update(n_steps=600)
+    items = W.config2_draws(3, seed=W.SEED_BASE + 42, n_r=48, n_y=16, n_v=16, n_steps=60)
+    items.insert(1, long_bond)
+    p32, i32 = H.hjm_price_batch(items, "fp32", infos=True)
+    p64 = H.hjm_price_batch(items, "fp64")
+    tol = 1e-7
+    flagged = [i32[i].err_estimate > max(tol * abs(p32[i]), 1e-6) for i in range(len(items))]
+    assert flagged[1] and not any(flagged[:1] + flagged[2:])
+    out = torch.empty(len(items), dtype=torch.float64, device="cuda")
+    _, inf = H.hjm_price_batch(items, "mixed", tol_rel=tol, out=out, infos=True)
+    got = out.cpu().numpy()
+    for i in range(len(items)):
+        if flagged[i]:
+            assert got[i] == p64[i] and inf[i].escalated == 1 and inf[i].precision_used == H.HJM_FP64
+        else:
+            assert got[i] == p32[i] and inf[i].escalated == 0 and inf[i].precision_used == H.HJM_FP32
+
+
+def test_single_price_mixed(H):
+    long_bond = W.config1()
+    long_bond["grid"].update(n_steps=600)
+    with H.Grid(long_bond) as g:
+        p64 = g.price("fp64")
+        pm, info = H.hjm_price(g.h, long_bond["inst"], "mixed", tol_rel=1e-9, with_info=True)
+        assert pm == p64 and info.escalated == 1
+
+
+@pytest.fixture(scope="module")
+def torch_dev():
+    import torch
+    return torch
