@@ -190,6 +190,36 @@ typedef struct {
 hjm_status hjm_trace_enable(int on);
 hjm_status hjm_trace_read(hjm_trace* out, int reset);
 
+/* Allocation-free pricing of one instrument (the paper has no counterpart;
+ * this is a deployment aid). For callers that cannot allocate device memory:
+ * code that runs while a CUDA stream capture is open (cudaMalloc is not a
+ * legal call then), processes whose device memory belongs to another
+ * allocator (a framework's caching allocator, or a fixed pool sized at
+ * start-up), and latency-critical loops that cannot take cudaMalloc's
+ * implicit device-wide synchronisation.
+ *
+ * Instead of a workspace, the march uses one file-scope device array of
+ * HJM_STATIC_SCRATCH_BYTES bytes that every GPU loading the library holds
+ * until the process exits. The call allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine): it copies the item's parameters
+ * into the array, runs set-up, terminal field, the n_steps Douglas steps and
+ * the read-out on cuda_stream, and writes the price to price_out, which must
+ * be device memory (one double). precision: HJM_FP32 or HJM_FP64.
+ *
+ * Limits and caveats:
+ *  - an item whose fields and tables do not fit in the array is rejected with
+ *    HJM_ERANGE (FP64 fields of up to about 2^19 points per field fit; the
+ *    message states the bytes needed);
+ *  - the first call on each device sets up the array's device address and the
+ *    kernels' shared-memory limit; make that first call before any stream
+ *    capture;
+ *  - every call shares the one array and leaves the last call's contents in
+ *    it: calls that overlap on the GPU (different streams without ordering,
+ *    or several host threads) race and give wrong prices; order them. */
+#define HJM_STATIC_SCRATCH_BYTES (8u << 20)
+hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision precision, double* price_out,
+                            void* cuda_stream);
+
 const char* hjm_status_string(hjm_status status);
 const char* hjm_last_error(void);
 

@@ -835,3 +835,96 @@ extern "C" hjm_status hjm_trace_read(hjm_trace* out, int reset)
     if (reset) memset(&g_trace, 0, sizeof g_trace);
     return HJM_OK;
 }
+
+// ------------------------------------------------- allocation-free pricing
+//
+// hjm_price_static (declared in hjm.h): the whole march of one instrument in
+// a file-scope device array, for callers that cannot allocate device memory
+// (open stream captures, externally owned device memory, latency-critical
+// loops). Nothing here allocates; the array is reserved when the library's
+// module is loaded on a device and lives until the process exits.
+
+static __device__ __align__(256) unsigned char g_static_scratch[HJM_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kStaticMaxDevices = 64;
+void* g_static_addr[kStaticMaxDevices];  // device address of g_static_scratch, per device
+std::mutex g_static_mu;
+
+template <typename T>
+hjm_status static_march(const GroupTables& t, void* U, void* A, int nsteps, bool gpos, cudaStream_t s)
+{
+    const March<T> P = march_args<T>(t);
+    for (int n = 0; n < nsteps; ++n) {
+        CU_TRY(launch_pass1<T>(P, (const T*)U, (T*)A, n, s));
+        CU_TRY(launch_pass2<T>(P, (const T*)A, (T*)A, s));
+        CU_TRY(launch_pass3<T>(P, (const T*)A, (const T*)U, (T*)U, gpos, n, s));
+    }
+    return HJM_OK;
+}
+}  // namespace
+
+extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision precision,
+                                       double* price_out, void* cuda_stream)
+{
+    if (!item || !price_out) return fail(HJM_EINVAL, "null argument");
+    if (precision != HJM_FP32 && precision != HJM_FP64)
+        return fail(HJM_EINVAL, "hjm_price_static takes HJM_FP32 or HJM_FP64");
+    const size_t elem = precision == HJM_FP32 ? sizeof(float) : sizeof(double);
+    hjm_status st = validate(item->curve, item->model, item->grid, &item->inst, elem);
+    if (st != HJM_OK) return st;
+    const hjm_grid_spec& g = item->grid;
+    const size_t N = (size_t)g.n_r * g.n_v * g.n_y;
+    const size_t need = align256(sizeof(InstParams)) + 2 * align256(N * elem) +
+                        tables_bytes(g.n_r, g.n_v, g.n_y, g.n_steps, 1, elem) + align256(sizeof(double));
+    if (need > HJM_STATIC_SCRATCH_BYTES)
+        return fail(HJM_ERANGE, "item needs %zu bytes of scratch, the static array holds %u", need,
+                    (unsigned)HJM_STATIC_SCRATCH_BYTES);
+    if (!is_device_ptr(price_out)) return fail(HJM_EINVAL, "price_out must be device memory");
+    int dev = 0;
+    CU_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(HJM_ERANGE, "device ordinal %d not supported", dev);
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_addr[dev]) {
+            // Once per device, with that device current: the host-side name
+            // of the array is not a device address, so look the address up.
+            void* addr = nullptr;
+            CU_TRY(cudaGetSymbolAddress(&addr, g_static_scratch));
+            CU_TRY(init_kernels());
+            g_static_addr[dev] = addr;
+        }
+        base = g_static_addr[dev];
+    }
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    char* p = (char*)base;
+    GroupTables t{};
+    t.nr = g.n_r;
+    t.nv = g.n_v;
+    t.ny = g.n_y;
+    t.nsteps = g.n_steps;
+    t.B = 1;
+    t.params = (InstParams*)p;
+    p += align256(sizeof(InstParams));
+    void* U = p;
+    p += align256(N * elem);
+    void* A = p;
+    p += align256(N * elem);
+    tables_carve(t, p, elem);
+    p += tables_bytes(g.n_r, g.n_v, g.n_y, g.n_steps, 1, elem);
+    double* ind = (double*)p;
+    // Every region above is fully rewritten by the kernels below before it
+    // is read (the set-up kernel also zeroes the rounding indicator), so no
+    // clearing is needed between calls.
+    const InstParams hp = to_params(*item);
+    CU_TRY(cudaMemcpyAsync(t.params, &hp, sizeof hp, cudaMemcpyHostToDevice, s));
+    CU_TRY(launch_setup(t, elem, s));
+    CU_TRY(launch_terminal(t, U, elem, s));
+    const bool gpos = item->model.gamma > 0.0;
+    st = elem == sizeof(float) ? static_march<float>(t, U, A, g.n_steps, gpos, s)
+                               : static_march<double>(t, U, A, g.n_steps, gpos, s);
+    if (st != HJM_OK) return st;
+    CU_TRY(launch_readout(t, U, elem, price_out, ind, s));
+    return HJM_OK;
+}

@@ -84,6 +84,7 @@ def _load():
         "hjm_field": ([vp, P(hjm_instrument), st, C.c_int, vp], st),
         "hjm_axis": ([vp, P(hjm_instrument), C.c_int, vp, vp, vp], st),
         "hjm_douglas_pass": ([vp, P(hjm_instrument), st, C.c_int, C.c_int, vp, vp, vp], st),
+        "hjm_price_static": ([P(hjm_batch_item), st, vp, vp], st),
         "hjm_trace_enable": ([st], st),
         "hjm_trace_read": ([P(hjm_trace), st], st),
         "hjm_status_string": ([st], C.c_char_p),
@@ -98,7 +99,7 @@ def _load():
 
 lib = _load()
 EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch", "hjm_field",
-            "hjm_axis", "hjm_douglas_pass", "hjm_trace_enable", "hjm_trace_read",
+            "hjm_axis", "hjm_douglas_pass", "hjm_price_static", "hjm_trace_enable", "hjm_trace_read",
             "hjm_status_string", "hjm_last_error")
 
 
@@ -230,6 +231,14 @@ def hjm_axis(handle, inst, axis, n):
 def hjm_douglas_pass(handle, inst, precision, pass_, step_n, inp, inp2, out):
     _check(lib.hjm_douglas_pass(handle, C.byref(inst_struct(inst)), PRECISIONS[precision], int(pass_),
                                 int(step_n), _ptr(inp), _ptr(inp2), _ptr(out)))
+    return out
+
+
+def hjm_price_static(item, precision, out, stream=None):
+    """Allocation-free price of one item into out (a device tensor of one
+    double); see hjm.h for the limits and the ordering rule."""
+    it = item if isinstance(item, hjm_batch_item) else batch_item(item)
+    _check(lib.hjm_price_static(C.byref(it), PRECISIONS[precision], _ptr(out), _stream(stream)))
     return out
 
 
