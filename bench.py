@@ -45,10 +45,15 @@ KERNEL_KINDS = ("setup", "terminal", "pass1", "pass2", "pass3", "readout")
 WORDS_PER_POINT = {"pass1": 2, "pass2": 2, "pass3": 3}
 
 
-def workload_items(name):
+def workload_items(name, instruments=None, march_steps=None):
+    """Items of a workload. instruments / march_steps shrink config2 for
+    profiling captures (they change the workload named in the JSON line)."""
     from paper_1108_1688_gb300 import workloads as W
     if name == "config2":
-        return W.config2_draws(100), "100 caplets 5y-into-6m ATM, NS curves, 128x64x64, 400 steps"
+        n = instruments or 100
+        ns = march_steps or 400
+        return (W.config2_draws(n, n_steps=ns),
+                "%d caplets 5y-into-6m ATM, NS curves, 128x64x64, %d steps" % (n, ns))
     if name == "config4":
         return [W.config4()], "1 caplet 10y-into-6m ATM, flat 3%, 512x256x256, 1000 steps"
     if name == "config3":
@@ -153,10 +158,15 @@ def barrier(world):
 
 # ---------------------------------------------------------------- helpers
 
+MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu")
+
+
 def source_digest():
+    """Digest of the three Douglas pass kernels' sources (recorded with the ncu
+    counters, so a stale counter is detected and reported as null)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1108_1688_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in MARCH_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -214,7 +224,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    items, desc = workload_items(args.workload)
+    items, desc = workload_items(args.workload, args.instruments, args.march_steps)
     it = items[0]
     g = it["grid"]
     pts = g["n_r"] * g["n_v"] * g["n_y"]
@@ -259,7 +269,7 @@ def run_ours(args):
     barrier(world)
     from paper_1108_1688_gb300 import hjm
 
-    items, desc = workload_items(args.workload)
+    items, desc = workload_items(args.workload, args.instruments, args.march_steps)
     prec = args.precision
     arr = hjm.make_items(items)
     import ctypes
@@ -386,6 +396,8 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--instruments", type=int, default=None, help="config2 only: fewer caplets (profiling)")
+    ap.add_argument("--march-steps", type=int, default=None, help="config2 only: fewer Douglas steps (profiling)")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)

@@ -190,6 +190,79 @@ typedef struct {
 hjm_status hjm_trace_enable(int on);
 hjm_status hjm_trace_read(hjm_trace* out, int reset);
 
+/* Pricing surrogate (the paper has no counterpart: it is a learned stand-in
+ * for the march, for repeated pricing in calibration loops). A multilayer
+ * perceptron 9 -> 256 -> 256 -> 256 -> 256 -> 1 with SiLU activations; its
+ * three 256 x 256 layers run on the tensor cores with bfloat16 operands and
+ * FP32 accumulation (forward and backward), AdamW on FP32 master weights.
+ *
+ * Inputs, per row (float, device, [n][9]): x = (kappa, lambda, theta,
+ * epsilon, rho, T, delta, K, F) with gamma = 0 and v0 = 1: model parameters,
+ * expiry T, accrual delta = T_M - T, strike K and the simple forward rate F
+ * of the curve over [T, T + delta]. Output: the forward premium C / P(0,T)
+ * of the caplet paying max(1 - (1 + delta K) p(T, T_M), 0) at T (multiply by
+ * the caller's P(0,T) for the price). With gamma = 0 this quantity depends on
+ * the curve only through F.
+ *
+ * Training data are the library's own FP32 march prices (labels on a flat
+ * curve with that forward), drawn uniformly over the box of features
+ * (kappa, lambda, theta, epsilon, rho, T, delta, K - F, F); 1/16 of the draws
+ * are held out and give, per (T, K - F) bin (9 x 8), the largest PDE-judged
+ * error. Inference answers from the network inside the box in bins whose
+ * held-out error is at most 0.5e-4 (half the 1e-4 price tolerance, a margin
+ * for unseen rows), and prices every other row with the march (the
+ * fallback); used_pde marks those rows.
+ *
+ * label_grid: node counts, steps and scheme options of each label's march;
+ * its domain fields are ignored (set per draw from the model's scales).
+ * checkpoint_path: NULL, or a file written after every epoch; an existing
+ * file resumes training from it. hidden must be 256 and depth 4. */
+typedef struct {
+    size_t n_train;
+    int hidden, depth;
+    int epochs, batch;
+    float lr;
+    uint64_t seed;
+    double box_lo[9], box_hi[9];
+    hjm_grid_spec label_grid;
+    const char* checkpoint_path;
+} hjm_surrogate_cfg;
+typedef struct hjm_surrogate hjm_surrogate;
+#define HJM_SURROGATE_PARAMS 200193
+#define HJM_SURROGATE_BINS 72
+
+/* Untrained network (seeded Glorot-uniform weights); every row falls back. */
+hjm_status hjm_surrogate_create(const hjm_surrogate_cfg* cfg, void* cuda_stream, hjm_surrogate** out);
+/* Draw, label with the march, train, build the error table. Synchronous. */
+hjm_status hjm_surrogate_train(const hjm_surrogate_cfg* cfg, void* cuda_stream, hjm_surrogate** out);
+/* epochs of AdamW on given data: x [n][9] raw inputs and t [n] scaled
+ * targets C / (P(0,T) delta 0.01), both device. */
+hjm_status hjm_surrogate_fit(hjm_surrogate* s, const float* x, const float* t, size_t n, int epochs,
+                             void* cuda_stream, float* final_loss);
+/* Gated prices (device x [n][9], device price_out [n], device used_pde [n]
+ * or NULL). Synchronises when rows fall back. */
+hjm_status hjm_surrogate_infer(hjm_surrogate* s, const float* x, size_t n, double* price_out,
+                               uint8_t* used_pde, void* cuda_stream);
+/* The network alone: y_out [n] = scaled output (device). */
+hjm_status hjm_surrogate_forward(hjm_surrogate* s, const float* x, size_t n, float* y_out, void* cuda_stream);
+/* Mean squared error of the scaled targets t and its gradient (device,
+ * HJM_SURROGATE_PARAMS floats, layout W0 [256x9], b0, W1 [256x256], b1, W2,
+ * b2, W3, b3, W4 [256], b4). loss_out: host float or NULL. */
+hjm_status hjm_surrogate_loss_grad(hjm_surrogate* s, const float* x, const float* t, size_t n,
+                                   float* loss_out, float* grad_out, void* cuda_stream);
+hjm_status hjm_surrogate_get_params(const hjm_surrogate* s, float* out);
+hjm_status hjm_surrogate_set_params(hjm_surrogate* s, const float* in);
+/* Held-out error per bin (host, HJM_SURROGATE_BINS floats, +inf = no data). */
+hjm_status hjm_surrogate_error_table(const hjm_surrogate* s, float* out);
+hjm_status hjm_surrogate_save(const hjm_surrogate* s, const char* path);
+hjm_status hjm_surrogate_load(const char* path, hjm_surrogate** out);
+hjm_status hjm_surrogate_destroy(hjm_surrogate* s);
+/* The surrogate's tensor-core product, exposed for testing: C[M x N] (FP32,
+ * device) = op(A) op(B) with bfloat16 A, B (device); op(A)(m,k) = A[m lda+k]
+ * or A[k lda+m] when trans_a, op(B)(k,n) = B[k ldb+n] or B[n ldb+k]. */
+hjm_status hjm_mlp_gemm(int M, int N, int K, const void* A, int lda, int trans_a, const void* B, int ldb,
+                        int trans_b, float* C, int ldc, void* cuda_stream);
+
 /* Allocation-free pricing of one instrument (the paper has no counterpart;
  * this is a deployment aid). For callers that cannot allocate device memory:
  * code that runs while a CUDA stream capture is open (cudaMalloc is not a

@@ -60,6 +60,9 @@ extern "C" const char* hjm_status_string(hjm_status s)
 
 extern "C" const char* hjm_last_error(void) { return g_last_error.c_str(); }
 
+// Error reporting for the other translation units of the library.
+hjm_status hjm_internal_fail(hjm_status s, const char* msg) { return fail(s, "%s", msg); }
+
 // ------------------------------------------------------------- validation
 
 static bool finite_all(std::initializer_list<double> xs)
@@ -406,11 +409,18 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
                 std::vector<Group>& groups, InstParams** d_params, long long** d_idx,
                 double** d_prices_all, double** d_ind_all = nullptr)
 {
+    // Groups hold at most kMaxGroup instruments (the set-up kernels index
+    // instruments with the grid's y dimension).
+    constexpr size_t kMaxGroup = 65535;
     std::map<std::tuple<int, int, int, int>, size_t> where;
     for (size_t i = 0; i < n; ++i) {
         const hjm_grid_spec& g = items[i].grid;
         auto key = std::make_tuple(g.n_r, g.n_v, g.n_y, g.n_steps);
         auto f = where.find(key);
+        if (f != where.end() && groups[f->second].idx.size() >= kMaxGroup) {
+            where.erase(f);
+            f = where.end();
+        }
         if (f == where.end()) {
             Group gr;
             gr.nr = g.n_r;

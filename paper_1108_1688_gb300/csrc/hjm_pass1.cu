@@ -361,14 +361,16 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
                 c[0] = -w * frI;
             }
         }
+        if (e0 + M > nr - 1) {  // only lanes holding r_max or padding
 #pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const int e = e0 + m;
-            if (e >= nr - 1) {
-                d[m] = e == nr - 1 ? gHi - uc[m] : T(0);
-                a[m] = T(0);
-                bb[m] = T(1);
-                c[m] = T(0);
+            for (int m = 0; m < M; ++m) {
+                const int e = e0 + m;
+                if (e >= nr - 1) {
+                    d[m] = e == nr - 1 ? gHi - uc[m] : T(0);
+                    a[m] = T(0);
+                    bb[m] = T(1);
+                    c[m] = T(0);
+                }
             }
         }
         seg_partition_solve<T, S, M>(a, bb, c, d, sl);

@@ -43,23 +43,6 @@ __device__ double Gfun(double kappa, double s)
     return kappa == 0.0 ? s : -expm1(-kappa * s) / kappa;
 }
 
-// Affine bond price p(t,S) at state (r, y), Section 3.1 (x = r - f(0,t)).
-__device__ double bond(const InstParams& p, double t, double S, double r, double y)
-{
-    const double G = Gfun(p.kappa, S - t);
-    return discount(p, S) / discount(p, t) * exp(-G * (r - fwd(p, t)) - 0.5 * G * G * y);
-}
-
-// Dirichlet data on the r faces: the exact bond, or the caplet's intrinsic
-// forward value max(P(t,T) - Delta_M P(t,T_M), 0).
-__device__ double face_value(const InstParams& p, const InstDerived& D, double t, double r, double y)
-{
-    const double pT = bond(p, t, p.T, r, y);
-    if (p.kind == HJM_ZCB) return pT;
-    const double v = pT - D.DM * bond(p, t, p.TM, r, y);
-    return v > 0.0 ? v : 0.0;
-}
-
 // --------------------------------------------------------------- metric
 
 // z(xi) = K + alpha sinh(c2 xi + c1 (1 - xi)) with c1, c2 fixing the end
@@ -220,14 +203,6 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
     }
     __syncthreads();  // y nodes above are read below by other threads
 
-    // Dirichlet data at t^{n+1} on r = r_min (face 0) and r = r_max (face 1).
-    T* dir = (T*)g.dir + (size_t)b * ns * 2 * ny;
-    for (int idx = tid; idx < ns * 2 * ny; idx += nth) {
-        const int j = idx % ny, face = (idx / ny) & 1, n = idx / (2 * ny);
-        const double t = p.T - (n + 1) * D.dt;
-        dir[idx] = (T)face_value(p, D, t, face ? p.rmax : p.rmin, axy[j]);
-    }
-
     // Thomas factors (sub, c', 1/m) of I - theta dt A_v: the same for every
     // v line (A_v depends on v only).
     if (tid == 0) {
@@ -290,6 +265,44 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
     }
 }
 
+// Dirichlet data at t^{n+1} on r = r_min (face 0) and r = r_max (face 1):
+// the exact bond p(t,S) = P(0,S)/P(0,t) exp(-G(S-t) x - G(S-t)^2 y / 2),
+// x = r - f(0,t) (Section 3.1), for a bond, and the caplet's intrinsic
+// forward value max(p(t,T) - Delta_M p(t,T_M), 0). One block per (step,
+// instrument): the curve factors depend on t only and are formed once.
+template <typename T>
+__global__ void __launch_bounds__(128) k_faces(GroupTables g)
+{
+    const int n = blockIdx.x, b = blockIdx.y, ny = g.ny, ns = g.nsteps;
+    const InstParams& p = g.params[b];
+    __shared__ double sc[6];
+    if (threadIdx.x == 0) {
+        const InstDerived D = g.derived[b];
+        const double t = p.T - (n + 1) * D.dt;
+        const double Pt = discount(p, t);
+        sc[0] = discount(p, p.T) / Pt;
+        sc[1] = discount(p, p.TM) / Pt;
+        sc[2] = fwd(p, t);
+        sc[3] = Gfun(p.kappa, p.T - t);
+        sc[4] = Gfun(p.kappa, p.TM - t);
+        sc[5] = D.DM;
+    }
+    __syncthreads();
+    const double* axy = g.axy + (size_t)b * 3 * ny;
+    T* dir = (T*)g.dir + ((size_t)b * ns + n) * 2 * ny;
+    for (int idx = threadIdx.x; idx < 2 * ny; idx += blockDim.x) {
+        const int j = idx % ny, face = idx / ny;
+        const double r = face ? p.rmax : p.rmin, y = axy[j], x = r - sc[2];
+        const double pT = sc[0] * exp(-sc[3] * x - 0.5 * sc[3] * sc[3] * y);
+        double v = pT;
+        if (p.kind == HJM_CAPLET) {
+            const double pM = sc[1] * exp(-sc[4] * x - 0.5 * sc[4] * sc[4] * y);
+            v = fmax(pT - sc[5] * pM, 0.0);
+        }
+        dir[idx] = (T)v;
+    }
+}
+
 // ------------------------------------------------------- terminal field
 
 // Gauss-Legendre rule of order 8 on [-1, 1] by Newton on the Legendre
@@ -314,15 +327,11 @@ __device__ void gauss_legendre8(double* x, double* wt, int q)
     wt[q] = 2.0 / ((1.0 - z * z) * dp * dp);
 }
 
-// Mean over r in [ra, rb] of max(1 - Delta_M p(T,T_M; r, y), 0): p is
-// A e^{-G r}, the payoff is positive above r* = ln(Delta_M A) / G and its
-// integral there is closed form.
-__device__ double caplet_r_mean(const InstParams& p, const InstDerived& D, double ra, double rb,
-                                double y)
+// Mean over r in [ra, rb] of max(1 - Delta_M p(T,T_M; r, y), 0) where
+// Delta_M p = e^{lnDA - G r}: the payoff is positive above r* = lnDA / G and
+// its integral there is closed form.
+__device__ double caplet_r_mean(double G, double lnDA, double ra, double rb)
 {
-    const double G = Gfun(p.kappa, p.TM - p.T);
-    const double lnA = log(discount(p, p.TM) / discount(p, p.T)) + G * fwd(p, p.T) - 0.5 * G * G * y;
-    const double lnDA = log(D.DM) + lnA;
     if (!(rb > ra)) {
         const double v = 1.0 - exp(lnDA - G * ra);
         return v > 0.0 ? v : 0.0;
@@ -334,33 +343,42 @@ __device__ double caplet_r_mean(const InstParams& p, const InstDerived& D, doubl
     return ((rb - lo) - tail) / (rb - ra);
 }
 
+// U^0 at t = T: 1 for a bond; for a caplet the payoff averaged over each
+// node's control volume in r and y (Section 7.2; closed form in r, 8-point
+// Gauss-Legendre in y), the same for every v. One block per (y node,
+// instrument); the y cell and the curve factors are formed once per block.
 template <typename T>
 __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
 {
-    __shared__ double gx[8], gw[8];
-    if (threadIdx.x < 8) gauss_legendre8(gx, gw, threadIdx.x);
-    __syncthreads();
+    const int j = blockIdx.x, b = blockIdx.y;
     const int nr = g.nr, nv = g.nv, ny = g.ny;
+    const InstParams& p = g.params[b];
+    __shared__ double gx[8], gw[8], sc[4];
+    if (threadIdx.x < 8) gauss_legendre8(gx, gw, threadIdx.x);
+    if (p.kind == HJM_CAPLET && threadIdx.x == 32) {
+        const InstDerived D = g.derived[b];
+        const double hy = 1.0 / (ny - 1);
+        const double G = Gfun(p.kappa, p.TM - p.T);
+        sc[0] = G;
+        // ln(Delta_M p(T,T_M; r=0, y=0))
+        sc[1] = log(D.DM) + log(discount(p, p.TM) / discount(p, p.T)) + G * fwd(p, p.T);
+        sc[2] = metric_z(fmax(0.0, (j - 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
+        sc[3] = metric_z(fmin(1.0, (j + 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
+    }
+    __syncthreads();
     const long long N = (long long)nr * nv * ny;
-    const long long total = (long long)g.B * ny * nr;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(idx % nr);
-        const int j = (int)((idx / nr) % ny);
-        const int b = (int)(idx / ((long long)nr * ny));
-        const InstParams& p = g.params[b];
+    const double hr = 1.0 / (nr - 1);
+    const double centre = g.derived[b].centre_r;
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         double val = 1.0;
         if (p.kind == HJM_CAPLET) {
-            const InstDerived D = g.derived[b];
-            const double hr = 1.0 / (nr - 1), hy = 1.0 / (ny - 1);
-            const double ra = metric_z(fmax(0.0, (i - 0.5) * hr), p.rmin, p.rmax, p.ar, D.centre_r);
-            const double rb = metric_z(fmin(1.0, (i + 0.5) * hr), p.rmin, p.rmax, p.ar, D.centre_r);
-            const double ya = metric_z(fmax(0.0, (j - 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
-            const double yb = metric_z(fmin(1.0, (j + 0.5) * hy), 0.0, p.ymax, p.ay, 0.0);
+            const double ra = metric_z(fmax(0.0, (i - 0.5) * hr), p.rmin, p.rmax, p.ar, centre);
+            const double rb = metric_z(fmin(1.0, (i + 0.5) * hr), p.rmin, p.rmax, p.ar, centre);
+            const double G = sc[0], ya = sc[2], yb = sc[3];
             double s = 0.0;
             for (int q = 0; q < 8; ++q) {
                 const double yq = 0.5 * (ya + yb) + 0.5 * (yb - ya) * gx[q];
-                s += 0.5 * gw[q] * caplet_r_mean(p, D, ra, rb, yq);
+                s += 0.5 * gw[q] * caplet_r_mean(G, sc[1] - 0.5 * G * G * yq, ra, rb);
             }
             val = s;
         }
@@ -468,21 +486,24 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
 
 cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s)
 {
-    if (elem == sizeof(float))
+    const dim3 faces(g.nsteps, g.B);
+    if (elem == sizeof(float)) {
         k_setup<float><<<g.B, 256, 0, s>>>(g);
-    else
+        k_faces<float><<<faces, 128, 0, s>>>(g);
+    } else {
         k_setup<double><<<g.B, 256, 0, s>>>(g);
+        k_faces<double><<<faces, 128, 0, s>>>(g);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStream_t s)
 {
-    const long long total = (long long)g.B * g.ny * g.nr;
-    const int blocks = (int)((total + 127) / 128 < 152 * 16 ? (total + 127) / 128 : 152 * 16);
+    const dim3 grid(g.ny, g.B);
     if (elem == sizeof(float))
-        k_terminal<float><<<blocks, 128, 0, s>>>(g, (float*)U);
+        k_terminal<float><<<grid, 128, 0, s>>>(g, (float*)U);
     else
-        k_terminal<double><<<blocks, 128, 0, s>>>(g, (double*)U);
+        k_terminal<double><<<grid, 128, 0, s>>>(g, (double*)U);
     return cudaGetLastError();
 }
 

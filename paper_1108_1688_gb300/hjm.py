@@ -65,6 +65,16 @@ class hjm_trace(C.Structure):
     _fields_ = [("launches", C.c_longlong * HJM_TRACE_KINDS), ("total_ms", C.c_double * HJM_TRACE_KINDS)]
 
 
+class hjm_surrogate_cfg(C.Structure):
+    _fields_ = [("n_train", C.c_size_t), ("hidden", C.c_int), ("depth", C.c_int), ("epochs", C.c_int),
+                ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64), ("box_lo", C.c_double * 9),
+                ("box_hi", C.c_double * 9), ("label_grid", hjm_grid_spec), ("checkpoint_path", C.c_char_p)]
+
+
+HJM_SURROGATE_PARAMS = 200193
+HJM_SURROGATE_BINS = 72
+
+
 class hjm_batch_item(C.Structure):
     _fields_ = [("curve", hjm_curve), ("model", hjm_model_params), ("grid", hjm_grid_spec),
                 ("inst", hjm_instrument)]
@@ -85,6 +95,19 @@ def _load():
         "hjm_axis": ([vp, P(hjm_instrument), C.c_int, vp, vp, vp], st),
         "hjm_douglas_pass": ([vp, P(hjm_instrument), st, C.c_int, C.c_int, vp, vp, vp], st),
         "hjm_price_static": ([P(hjm_batch_item), st, vp, vp], st),
+        "hjm_surrogate_create": ([P(hjm_surrogate_cfg), vp, P(vp)], st),
+        "hjm_surrogate_train": ([P(hjm_surrogate_cfg), vp, P(vp)], st),
+        "hjm_surrogate_fit": ([vp, vp, vp, C.c_size_t, C.c_int, vp, P(C.c_float)], st),
+        "hjm_surrogate_infer": ([vp, vp, C.c_size_t, vp, vp, vp], st),
+        "hjm_surrogate_forward": ([vp, vp, C.c_size_t, vp, vp], st),
+        "hjm_surrogate_loss_grad": ([vp, vp, vp, C.c_size_t, P(C.c_float), vp, vp], st),
+        "hjm_surrogate_get_params": ([vp, vp], st),
+        "hjm_surrogate_set_params": ([vp, vp], st),
+        "hjm_surrogate_error_table": ([vp, vp], st),
+        "hjm_surrogate_save": ([vp, C.c_char_p], st),
+        "hjm_surrogate_load": ([C.c_char_p, P(vp)], st),
+        "hjm_surrogate_destroy": ([vp], st),
+        "hjm_mlp_gemm": ([C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, vp], st),
         "hjm_trace_enable": ([st], st),
         "hjm_trace_read": ([P(hjm_trace), st], st),
         "hjm_status_string": ([st], C.c_char_p),
@@ -99,7 +122,11 @@ def _load():
 
 lib = _load()
 EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch", "hjm_field",
-            "hjm_axis", "hjm_douglas_pass", "hjm_price_static", "hjm_trace_enable", "hjm_trace_read",
+            "hjm_axis", "hjm_douglas_pass", "hjm_price_static", "hjm_surrogate_create", "hjm_surrogate_train",
+            "hjm_surrogate_fit", "hjm_surrogate_infer", "hjm_surrogate_forward", "hjm_surrogate_loss_grad",
+            "hjm_surrogate_get_params", "hjm_surrogate_set_params", "hjm_surrogate_error_table",
+            "hjm_surrogate_save", "hjm_surrogate_load", "hjm_surrogate_destroy", "hjm_mlp_gemm",
+            "hjm_trace_enable", "hjm_trace_read",
             "hjm_status_string", "hjm_last_error")
 
 
@@ -251,6 +278,97 @@ def hjm_trace_read(reset=False):
     t = hjm_trace()
     _check(lib.hjm_trace_read(C.byref(t), 1 if reset else 0))
     return {name: (int(t.launches[i]), float(t.total_ms[i])) for i, name in enumerate(TRACE_KIND_NAMES)}
+
+
+# ---------------------------------------------------------------- surrogate
+
+def surrogate_cfg(n_train, epochs, batch, lr, seed, box_lo, box_hi, label_grid, checkpoint_path=None):
+    c = hjm_surrogate_cfg()
+    c.n_train = int(n_train)
+    c.hidden, c.depth = 256, 4
+    c.epochs, c.batch, c.lr, c.seed = int(epochs), int(batch), float(lr), int(seed)
+    for k in range(9):
+        c.box_lo[k] = float(box_lo[k])
+        c.box_hi[k] = float(box_hi[k])
+    c.label_grid = grid_struct(label_grid)
+    c.checkpoint_path = checkpoint_path.encode() if checkpoint_path else None
+    return c
+
+
+def hjm_surrogate_create(cfg, stream=None):
+    h = C.c_void_p()
+    _check(lib.hjm_surrogate_create(C.byref(cfg), _stream(stream), C.byref(h)))
+    return h
+
+
+def hjm_surrogate_train(cfg, stream=None):
+    h = C.c_void_p()
+    _check(lib.hjm_surrogate_train(C.byref(cfg), _stream(stream), C.byref(h)))
+    return h
+
+
+def hjm_surrogate_fit(h, x, t, epochs, stream=None):
+    loss = C.c_float()
+    n = int(t.numel() if hasattr(t, "numel") else len(t))
+    _check(lib.hjm_surrogate_fit(h, _ptr(x), _ptr(t), n, int(epochs), _stream(stream), C.byref(loss)))
+    return loss.value
+
+
+def hjm_surrogate_infer(h, x, price_out, used_pde=None, stream=None):
+    n = int(price_out.numel() if hasattr(price_out, "numel") else len(price_out))
+    _check(lib.hjm_surrogate_infer(h, _ptr(x), n, _ptr(price_out), _ptr(used_pde), _stream(stream)))
+    return price_out
+
+
+def hjm_surrogate_forward(h, x, y_out, stream=None):
+    n = int(y_out.numel() if hasattr(y_out, "numel") else len(y_out))
+    _check(lib.hjm_surrogate_forward(h, _ptr(x), n, _ptr(y_out), _stream(stream)))
+    return y_out
+
+
+def hjm_surrogate_loss_grad(h, x, t, grad_out, stream=None):
+    loss = C.c_float()
+    n = int(t.numel() if hasattr(t, "numel") else len(t))
+    _check(lib.hjm_surrogate_loss_grad(h, _ptr(x), _ptr(t), n, C.byref(loss), _ptr(grad_out), _stream(stream)))
+    return loss.value
+
+
+def hjm_surrogate_get_params(h):
+    out = np.empty(HJM_SURROGATE_PARAMS, dtype=np.float32)
+    _check(lib.hjm_surrogate_get_params(h, out.ctypes.data))
+    return out
+
+
+def hjm_surrogate_set_params(h, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == HJM_SURROGATE_PARAMS
+    _check(lib.hjm_surrogate_set_params(h, p.ctypes.data))
+
+
+def hjm_surrogate_error_table(h):
+    out = np.empty(HJM_SURROGATE_BINS, dtype=np.float32)
+    _check(lib.hjm_surrogate_error_table(h, out.ctypes.data))
+    return out
+
+
+def hjm_surrogate_save(h, path):
+    _check(lib.hjm_surrogate_save(h, path.encode()))
+
+
+def hjm_surrogate_load(path):
+    h = C.c_void_p()
+    _check(lib.hjm_surrogate_load(path.encode(), C.byref(h)))
+    return h
+
+
+def hjm_surrogate_destroy(h):
+    _check(lib.hjm_surrogate_destroy(h))
+
+
+def hjm_mlp_gemm(M, N, K, A, lda, trans_a, B, ldb, trans_b, C_out, ldc, stream=None):
+    _check(lib.hjm_mlp_gemm(int(M), int(N), int(K), _ptr(A), int(lda), int(bool(trans_a)), _ptr(B), int(ldb),
+                            int(bool(trans_b)), _ptr(C_out), int(ldc), _stream(stream)))
+    return C_out
 
 
 class Grid:

@@ -190,3 +190,45 @@ def with_grid(it, **kw):
 def point_steps(it):
     g = it["grid"]
     return g["n_r"] * g["n_y"] * g["n_v"] * g["n_steps"]
+
+
+# Surrogate input box (features kappa, lambda, theta, epsilon, rho, T, delta,
+# K - F, F): epsilon and rho as in config2/3, kappa, lambda, theta 50-100%
+# around config1, expiries 1..10y, accruals 3m..1y, strikes ATM +- 200bp.
+SURROGATE_BOX_LO = (0.05, 0.005, 0.5, 0.1, -0.7, 1.0, 0.25, -0.02, 0.01)
+SURROGATE_BOX_HI = (0.2, 0.015, 2.0, 0.6, 0.3, 10.0, 1.0, 0.02, 0.07)
+
+
+def surrogate_label_grid(n_r=96, n_y=48, n_v=48, n_steps=192):
+    """Counts and scheme of the surrogate's label march (the library sets the
+    domain of each label from its draw)."""
+    return dict(n_r=n_r, n_y=n_y, n_v=n_v, n_steps=n_steps, r_min=0.0, r_max=0.0, y_max=0.0, v_max=0.0,
+                alpha_r=0.0, alpha_y=0.0, alpha_v=0.0, k_r=0.0, k_v=1.0, center_r_on_strike=1,
+                theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0)
+
+
+def surrogate_draws(n, seed, box_lo=SURROGATE_BOX_LO, box_hi=SURROGATE_BOX_HI, out_of_box=0.0):
+    """Raw surrogate inputs (kappa, lambda, theta, epsilon, rho, T, delta, K, F)
+    uniform over the box; a fraction out_of_box has one feature pushed 20%
+    of its range outside the box."""
+    rng = np.random.default_rng(seed)
+    lo, hi = np.array(box_lo), np.array(box_hi)
+    f = lo + (hi - lo) * rng.random((n, 9))
+    m = int(round(out_of_box * n))
+    for r in range(m):
+        k = int(rng.integers(0, 9))
+        f[r, k] = hi[k] + 0.2 * (hi[k] - lo[k]) if k != 4 else hi[k] + 0.1
+    x = f.copy()
+    x[:, 7] = f[:, 7] + f[:, 8]
+    return x.astype(np.float32)
+
+
+def surrogate_item(x, label_grid):
+    """The march's item for one raw surrogate input row (flat curve with the
+    row's forward F over [T, T + delta]: continuous rate ln(1 + F delta)/delta)."""
+    kap, lam, th, eps, rho, T, dl, K, F = [float(v) for v in x]
+    c = math.log1p(F * dl) / dl
+    curve = flat_curve(c)
+    m = model(kap, lam, 0.0, th, eps, rho, 1.0)
+    g = default_grid(curve, m, T, label_grid["n_r"], label_grid["n_y"], label_grid["n_v"], label_grid["n_steps"])
+    return item(curve, m, g, caplet(T, T + dl, K, atm_relative=False))

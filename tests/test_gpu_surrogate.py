@@ -1,0 +1,225 @@
+"""The pricing surrogate through the C ABI: its tensor-core GEMM against an
+exact product, its loss gradient against the CPU FP64 reference network
+(oracle/mlp_oracle.py, itself pinned by finite differences), training,
+gating with the march as fallback, checkpointing, the PDE-judged error of a
+trained network and what it gains over pricing with the march alone."""
+import math
+import os
+import time
+
+import numpy as np
+import pytest
+
+from paper_1108_1688_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1108_1688_gb300 import _build
+    _build.build()
+    from paper_1108_1688_gb300 import hjm
+    return torch, hjm
+
+
+def _cfg(H, n_train=256, epochs=2, batch=64, lr=1e-3, seed=7, label=None, ckpt=None):
+    return H.surrogate_cfg(n_train, epochs, batch, lr, seed, W.SURROGATE_BOX_LO, W.SURROGATE_BOX_HI,
+                           label or W.surrogate_label_grid(24, 10, 10, 24), ckpt)
+
+
+def _bf16_tensor(torch, a):
+    return torch.tensor(a, dtype=torch.float32).to(torch.bfloat16).cuda()
+
+
+@pytest.mark.parametrize("ta,tb", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_tensor_core_gemm(env, ta, tb):
+    torch, H = env
+    rng = np.random.default_rng(ta * 2 + tb)
+    M, N, K = 100, 70, 48
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    Ad, Bd = _bf16_tensor(torch, A), _bf16_tensor(torch, B)
+    Ar = Ad.float().cpu().numpy().astype(np.float64)
+    Br = Bd.float().cpu().numpy().astype(np.float64)
+    want = (Ar.T if ta else Ar) @ (Br.T if tb else Br)
+    C = torch.full((M, N), float("nan"), dtype=torch.float32, device="cuda")
+    H.hjm_mlp_gemm(M, N, K, Ad, A.shape[1], ta, Bd, B.shape[1], tb, C, N)
+    torch.cuda.synchronize()
+    got = C.cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-5, atol=1e-5 * np.abs(want).max())
+
+
+def _features(x):
+    f = x.astype(np.float64).copy()
+    f[:, 7] = f[:, 7] - f[:, 8]
+    return f
+
+
+def test_loss_gradient_matches_fp64_reference(env):
+    torch, H = env
+    from oracle import mlp_oracle as M
+    h = H.hjm_surrogate_create(_cfg(H))
+    try:
+        p = H.hjm_surrogate_get_params(h).astype(np.float64)
+        rng = np.random.default_rng(11)
+        x = W.surrogate_draws(192, seed=5)
+        t = rng.standard_normal(192).astype(np.float32)
+        g = torch.empty(H.HJM_SURROGATE_PARAMS, dtype=torch.float32, device="cuda")
+        loss = H.hjm_surrogate_loss_grad(h, torch.tensor(x).cuda(), torch.tensor(t).cuda(), g)
+        torch.cuda.synchronize()
+        lo, hi = np.array(W.SURROGATE_BOX_LO), np.array(W.SURROGATE_BOX_HI)
+        lref, gref = M.loss_and_grad(p, _features(x), t.astype(np.float64), lo, hi, bf16_round=True)
+        assert abs(loss - lref) <= 1e-4 * abs(lref)
+        gg = g.cpu().numpy().astype(np.float64)
+        for name, shape, off in M.LAYOUT:
+            n = int(np.prod(shape))
+            a, b = gg[off:off + n], gref[off:off + n]
+            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+            assert rel < 5e-3, (name, rel)
+        # forward agrees as well
+        y = torch.empty(192, dtype=torch.float32, device="cuda")
+        H.hjm_surrogate_forward(h, torch.tensor(x).cuda(), y)
+        torch.cuda.synchronize()
+        yref = M.forward(p, _features(x), lo, hi, bf16_round=True)
+        assert np.max(np.abs(y.cpu().numpy() - yref)) <= 2e-3 * max(1.0, np.max(np.abs(yref)))
+    finally:
+        H.hjm_surrogate_destroy(h)
+
+
+def test_fit_reduces_loss(env):
+    torch, H = env
+    h = H.hjm_surrogate_create(_cfg(H, batch=256, lr=2e-3))
+    try:
+        x = W.surrogate_draws(4096, seed=6)
+        f = _features(x)
+        lo, hi = np.array(W.SURROGATE_BOX_LO), np.array(W.SURROGATE_BOX_HI)
+        z = 2 * (f - lo) / (hi - lo) - 1
+        t = (np.sin(2 * z[:, 5]) + 0.5 * z[:, 7] ** 2 - 0.3 * z[:, 3] * z[:, 4]).astype(np.float32)
+        xd, td = torch.tensor(x).cuda(), torch.tensor(t).cuda()
+        g = torch.empty(H.HJM_SURROGATE_PARAMS, dtype=torch.float32, device="cuda")
+        l0 = H.hjm_surrogate_loss_grad(h, xd, td, g)
+        H.hjm_surrogate_fit(h, xd, td, 20)
+        l1 = H.hjm_surrogate_loss_grad(h, xd, td, g)
+        assert l1 < 0.05 * l0, (l0, l1)
+    finally:
+        H.hjm_surrogate_destroy(h)
+
+
+def _pde_forward_premium(H, x, label):
+    items = [W.surrogate_item(r, label) for r in x]
+    C = H.hjm_price_batch(items, "fp32")
+    out = []
+    for r, c in zip(x, C):
+        T, dl, F = float(r[5]), float(r[6]), float(r[8])
+        out.append(c * math.exp(math.log1p(F * dl) / dl * T))
+    return np.array(out)
+
+
+def test_untrained_surrogate_falls_back_everywhere(env):
+    torch, H = env
+    label = W.surrogate_label_grid(24, 10, 10, 24)
+    h = H.hjm_surrogate_create(_cfg(H, label=label))
+    try:
+        x = W.surrogate_draws(40, seed=8, out_of_box=0.25)
+        out = torch.empty(40, dtype=torch.float64, device="cuda")
+        used = torch.zeros(40, dtype=torch.uint8, device="cuda")
+        H.hjm_surrogate_infer(h, torch.tensor(x).cuda(), out, used)
+        torch.cuda.synchronize()
+        assert bool(used.all())
+        want = _pde_forward_premium(H, x, label)
+        assert np.allclose(out.cpu().numpy(), want, rtol=1e-12, atol=1e-15)
+    finally:
+        H.hjm_surrogate_destroy(h)
+
+
+def test_train_gate_checkpoint_and_resume(env, tmp_path):
+    torch, H = env
+    label = W.surrogate_label_grid(24, 10, 10, 24)
+    path = str(tmp_path / "s.ckpt")
+    h = H.hjm_surrogate_train(_cfg(H, n_train=1024, epochs=2, batch=128, label=label, ckpt=path))
+    try:
+        assert os.path.exists(path)
+        table = H.hjm_surrogate_error_table(h)
+        assert table.shape == (72,) and np.all(table >= 0)
+        # out-of-box rows always fall back; in-box rows follow their bin
+        x = W.surrogate_draws(64, seed=9, out_of_box=0.25)
+        out = torch.empty(64, dtype=torch.float64, device="cuda")
+        used = torch.zeros(64, dtype=torch.uint8, device="cuda")
+        H.hjm_surrogate_infer(h, torch.tensor(x).cuda(), out, used)
+        torch.cuda.synchronize()
+        u = used.cpu().numpy().astype(bool)
+        assert u[:16].all()
+        want = _pde_forward_premium(H, x[u], label)
+        assert np.allclose(out.cpu().numpy()[u], want, rtol=1e-12, atol=1e-15)
+        # save / load round trip gives the same network
+        p1 = H.hjm_surrogate_get_params(h)
+        h2 = H.hjm_surrogate_load(path)
+        try:
+            assert np.array_equal(H.hjm_surrogate_get_params(h2), p1)
+            assert np.array_equal(H.hjm_surrogate_error_table(h2), table)
+        finally:
+            H.hjm_surrogate_destroy(h2)
+        # resuming with more epochs continues from the checkpoint
+        h3 = H.hjm_surrogate_train(_cfg(H, n_train=1024, epochs=3, batch=128, label=label, ckpt=path))
+        try:
+            assert not np.array_equal(H.hjm_surrogate_get_params(h3), p1)
+        finally:
+            H.hjm_surrogate_destroy(h3)
+    finally:
+        H.hjm_surrogate_destroy(h)
+
+
+def test_trained_surrogate_error_coverage_and_gain(env):
+    # A network trained on 2^16 PDE labels (64 x 32 x 32, 128 steps), judged
+    # by the PDE on fresh draws (5% out of the box): every answered row within
+    # 1e-4 of the PDE forward premium, the rest priced by the PDE; then the
+    # speed-up of surrogate pricing over the march alone on 65,536 rows.
+    torch, H = env
+    label = W.surrogate_label_grid(64, 32, 32, 128)
+    t0 = time.time()
+    h = H.hjm_surrogate_train(H.surrogate_cfg(1 << 16, 120, 1024, 3e-3, 2024, W.SURROGATE_BOX_LO,
+                                              W.SURROGATE_BOX_HI, label, None))
+    train_s = time.time() - t0
+    table = H.hjm_surrogate_error_table(h)
+    print("surrogate: held-out bin errors min %.2e median %.2e max %.2e, bins under 5e-5: %d/72"
+          % (table.min(), np.median(table), table.max(), int((table <= 5e-5).sum())))
+    try:
+        x = W.surrogate_draws(2048, seed=31, out_of_box=0.05)
+        out = torch.empty(2048, dtype=torch.float64, device="cuda")
+        used = torch.zeros(2048, dtype=torch.uint8, device="cuda")
+        H.hjm_surrogate_infer(h, torch.tensor(x).cuda(), out, used)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        u = used.cpu().numpy().astype(bool)
+        want = _pde_forward_premium(H, x, label)
+        err = np.abs(got - want)
+        coverage = 1.0 - u.mean()
+        print("surrogate: train %.1fs coverage %.3f max err answered %.2e median %.2e"
+              % (train_s, coverage, err[~u].max() if (~u).any() else 0, np.median(err[~u]) if (~u).any() else 0))
+        assert np.all(err[u] <= 1e-12 + 1e-12 * np.abs(want[u]))  # fallback rows are the PDE
+        assert np.all(err[~u] <= 1e-4)
+        assert coverage > 0.5
+        # gain: 65,536 rows through the network vs the march on a 256-row sample
+        xb = torch.tensor(W.surrogate_draws(65536, seed=32)).cuda()
+        yb = torch.empty(65536, dtype=torch.float32, device="cuda")
+        H.hjm_surrogate_forward(h, xb, yb)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(5):
+            H.hjm_surrogate_forward(h, xb, yb)
+        torch.cuda.synchronize()
+        net_per_row = (time.perf_counter() - t0) / 5 / 65536
+        xs = W.surrogate_draws(256, seed=33)
+        items = [W.surrogate_item(r, label) for r in xs]
+        H.hjm_price_batch(items, "fp32")
+        t0 = time.perf_counter()
+        H.hjm_price_batch(items, "fp32")
+        pde_per_row = (time.perf_counter() - t0) / 256
+        print("surrogate: %.3g s/row vs march %.3g s/row: %.0fx" % (net_per_row, pde_per_row, pde_per_row / net_per_row))
+        assert pde_per_row / net_per_row > 100
+    finally:
+        H.hjm_surrogate_destroy(h)
