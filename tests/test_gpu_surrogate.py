@@ -119,6 +119,36 @@ def _pde_forward_premium(H, x, label):
     return np.array(out)
 
 
+def test_forward_premium_depends_on_the_curve_only_through_the_forward(env):
+    # The reduction behind the surrogate's ninth input: with gamma = 0 the
+    # forward premium C / P(0,T) of a caplet depends on the initial curve only
+    # through the simple forward F over [T, T_M] (the bond formula of Section
+    # 3.2 gives p(T,T_M) through P(0,T_M)/P(0,T); the law of (x, y, v) does
+    # not involve the curve). The FP64 march on a Nelson-Siegel curve and on
+    # the flat curve with the same F must agree up to the discretisation
+    # error, which shrinks under refinement (F at t^{n+1/2}, so the time error
+    # of the curve-dependent drift is second order).
+    torch, H = env
+    from oracle import curve_P
+    gaps = []
+    for n in ((48, 24, 24, 96), (96, 48, 48, 192), (192, 96, 96, 384)):
+        worst = 0.0
+        for x in W.config2_draws(3, n_r=n[0], n_y=n[1], n_v=n[2], n_steps=n[3]):
+            x["grid"]["explicit_midpoint"] = 1
+            c, m, inst = x["curve"], x["model"], x["inst"]
+            T, TM = inst["T"], inst["TM"]
+            dl = TM - T
+            P0 = curve_P(c, T)
+            F = (P0 / curve_P(c, TM) - 1.0) / dl
+            fc = W.flat_curve(math.log1p(F * dl) / dl)
+            y = W.item(fc, m, W.default_grid(fc, m, T, *n, explicit_midpoint=1),
+                       W.caplet(T, TM, F, atm_relative=False))
+            C_ns, C_flat = H.hjm_price_batch([x, y], "fp64")
+            worst = max(worst, abs(C_ns / P0 - C_flat / curve_P(fc, T)))
+        gaps.append(worst)
+    assert gaps[2] < gaps[0] and gaps[2] < 5e-6, gaps
+
+
 def test_untrained_surrogate_falls_back_everywhere(env):
     torch, H = env
     label = W.surrogate_label_grid(24, 10, 10, 24)

@@ -62,3 +62,58 @@ def test_rounded_network_close_to_exact():
     y1 = M.forward(p, x, lo, hi, bf16_round=True)
     y0 = M.forward(p, x, lo, hi, bf16_round=False)
     assert np.max(np.abs(y1 - y0)) < 1e-2 * max(1.0, np.max(np.abs(y0)))
+
+
+def _fd_mismatch(loss_and_grad, p, x, t, lo, hi):
+    """Largest gap between a gradient routine and central differences of the
+    (unmutated) loss on a sample of coordinates from every block."""
+    _, g = loss_and_grad(p, x, t, lo, hi, bf16_round=False)
+    rng = np.random.default_rng(19)
+    worst = 0.0
+    for name, shape, off in M.LAYOUT:
+        n = int(np.prod(shape))
+        fd, gi = [], []
+        for i in off + rng.choice(n, size=min(4, n), replace=False):
+            e = np.zeros_like(p)
+            e[i] = 1e-6
+            lp = float(np.mean((M.forward(p + e, x, lo, hi, False) - t) ** 2))
+            lm = float(np.mean((M.forward(p - e, x, lo, hi, False) - t) ** 2))
+            fd.append((lp - lm) / 2e-6)
+            gi.append(g[i])
+        fd, gi = np.array(fd), np.array(gi)
+        worst = max(worst, np.max(np.abs(fd - gi)) / max(np.max(np.abs(fd)), 1e-12))
+    return worst
+
+
+@pytest.mark.parametrize("mutation", ["silu_grad_sign", "transposed_weight", "bias_grad_dropped"])
+def test_planted_backward_mistakes_fail_the_pin(monkeypatch, mutation):
+    # Each plausible mistake in the backward pass, planted in the reference,
+    # must break the finite-difference pin above.
+    p, x, t, lo, hi = _setup()
+    assert _fd_mismatch(M.loss_and_grad, p, x, t, lo, hi) < 1e-5
+    if mutation == "silu_grad_sign":
+        monkeypatch.setattr(M, "silu_grad", lambda u: M.sigmoid(u) * (1.0 - u * (1.0 - M.sigmoid(u))))
+    elif mutation == "transposed_weight":
+        orig = M.unpack
+
+        def unpack_t(q):
+            P = orig(q)
+            if unpack_t.calls == 1:  # the backward pass's own unpack
+                for l in (1, 2, 3):
+                    P["W%d" % l] = P["W%d" % l].T
+            unpack_t.calls += 1
+            return P
+        unpack_t.calls = 0
+        monkeypatch.setattr(M, "unpack", unpack_t)
+    else:
+        orig_lg = M.loss_and_grad
+
+        def lg(q, *a, **k):
+            l, g = orig_lg(q, *a, **k)
+            g = g.copy()
+            for name, shape, off in M.LAYOUT:
+                if name.startswith("b"):
+                    g[off:off + int(np.prod(shape))] = 0.0
+            return l, g
+        monkeypatch.setattr(M, "loss_and_grad", lg)
+    assert _fd_mismatch(M.loss_and_grad, p, x, t, lo, hi) > 1e-2, mutation
