@@ -283,6 +283,16 @@ def run_ours(args):
     def step_dev():
         hjm.hjm_price_batch(arr, prec, out=out, stream=stream)
 
+    # Launch shapes: the library's autotuner times the candidate shapes of
+    # every grid shape of the workload once (untimed, before the warm-up).
+    tiles = {}
+    if not args.no_autotune:
+        hjm.hjm_autotune(arr, prec, steps=8, stream=stream)
+    for x in items:
+        g = x["grid"]
+        key = "%dx%dx%d" % (g["n_r"], g["n_y"], g["n_v"])
+        tiles[key] = list(hjm.hjm_tile_get(g["n_r"], g["n_v"], g["n_y"], prec))
+
     for _ in range(args.warmup):
         step_dev()
     torch.cuda.synchronize()
@@ -366,7 +376,8 @@ def run_ours(args):
                    "caplets_per_s": world * n * args.steps / (ms_max * 1e-3),
                    "precision": prec, "l2": "working set %.0f MB > L2 (no flush)" % (2 * total_points * elem / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "param_upload_bytes_per_step": n * item_bytes},
+                   "param_upload_bytes_per_step": n * item_bytes,
+                   "tiles": {"autotuned": not args.no_autotune, "r_x_y_x_v": tiles}},
         "e2e": {"value": world * ps * args.steps / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": n * item_bytes, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches_per_step * args.steps,
@@ -396,6 +407,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="use the default launch shapes")
     ap.add_argument("--instruments", type=int, default=None, help="config2 only: fewer caplets (profiling)")
     ap.add_argument("--march-steps", type=int, default=None, help="config2 only: fewer Douglas steps (profiling)")
     args = ap.parse_args(argv)

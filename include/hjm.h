@@ -116,7 +116,7 @@ typedef struct {
     double err_estimate;
     int n_steps;
     float time_us;            /* device time of the whole call, microseconds */
-    int tile_cfg;             /* r-line chunk size of the r-direction kernel */
+    int tile_cfg;             /* launch shape used, packed as described at hjm_tile */
 } hjm_price_info;
 
 typedef struct hjm_grid hjm_grid;
@@ -189,6 +189,47 @@ typedef struct {
 } hjm_trace;
 hjm_status hjm_trace_enable(int on);
 hjm_status hjm_trace_read(hjm_trace* out, int reset);
+
+/* Launch shapes of the march kernels for one grid shape and precision (the
+ * Douglas passes of Section 5.1). Pass 1 gives each r line p1_lanes lanes
+ * of a warp holding p1_nodes consecutive nodes each (p1_lanes * p1_nodes >=
+ * n_r; compiled: FP32 (8: 8, 16), (16: 4, 8, 16), (32: 2, 4, 8, 16); FP64
+ * (16: 2, 4, 8), (32: 2, 4, 8, 16)) and processes p1_lines lines per lane
+ * segment per CTA (1..64). p2_warps / p3_warps: warps sharing each v / y
+ * line of passes 2 and 3: 1 (one thread per line), or 2, 4, 8 when the line
+ * has at least 2 nodes per warp and at most 32 (pass 3 splits y lines only
+ * in groups where every instrument has gamma = 0). p1_staged = 1 makes
+ * pass 1 copy the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v
+ * nodes into shared memory and march over p1_planes (1..4096) y nodes per
+ * CTA (needs n_r * element size a multiple of 16 and the ring within the
+ * shared memory of a CTA); p1_staged = 0 reads the rows from global memory
+ * (p1_planes = 0). A shape changes speed and the rounding of the line
+ * solves, nothing else.
+ * tile_cfg in hjm_price_info packs p1_lanes | p1_nodes << 8 | p1_lines << 14
+ * | p2_warps << 21 | p3_warps << 25 | p1_staged << 29. */
+typedef struct {
+    int p1_lanes;
+    int p1_nodes;
+    int p1_lines;
+    int p2_warps;
+    int p3_warps;
+    int p1_staged;
+    int p1_planes;
+} hjm_tile;
+/* The shape in use for (n_r, n_v, n_y, precision): set, tuned or default.
+ * HJM_MIXED reads the FP32 entry. */
+hjm_status hjm_tile_get(int n_r, int n_v, int n_y, hjm_precision precision, hjm_tile* out);
+/* Use *tile for this grid shape from now on (process-wide); NULL restores
+ * the default. HJM_EINVAL when the shape is not compiled or does not cover
+ * n_r. */
+hjm_status hjm_tile_set(int n_r, int n_v, int n_y, hjm_precision precision, const hjm_tile* tile);
+/* Autotuner: for every grid shape among the items, march the items of that
+ * shape for `steps` Douglas steps (1..1000) with each candidate launch shape
+ * (timed with CUDA events on cuda_stream, best of two), and keep the fastest
+ * for later calls. Prices are not computed; synchronous; the items are
+ * validated as in hjm_price_batch. */
+hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_precision precision, int steps,
+                        void* cuda_stream);
 
 /* Pricing surrogate (the paper has no counterpart: it is a learned stand-in
  * for the march, for repeated pricing in calibration loops). A multilayer

@@ -10,6 +10,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <map>
 #include <mutex>
 #include <string>
@@ -210,6 +211,16 @@ constexpr int kBranches = 8;  // streams the shape groups of a batch graph fork 
 cudaStream_t g_branch[kBranches];
 std::vector<cudaEvent_t> g_events;
 
+// Launch shapes per grid shape (n_r, n_v, n_y, element size), set by
+// hjm_tile_set or hjm_autotune; shapes without an entry use default_tile.
+std::map<std::tuple<int, int, int, size_t>, Tile> g_tiles;
+
+Tile tile_for(int nr, int nv, int ny, size_t elem)
+{
+    auto it = g_tiles.find(std::make_tuple(nr, nv, ny, elem));
+    return it != g_tiles.end() ? it->second : default_tile(nr, nv, ny, elem);
+}
+
 hjm_status ensure_init()
 {
     if (g_init_done) return HJM_OK;
@@ -229,6 +240,7 @@ struct Group {
     int nr, nv, ny, nsteps;
     std::vector<size_t> idx;  // positions in the caller's item array
     bool gpos = false;
+    Tile tile{};
     GroupTables t{};
     void* U = nullptr;
     void* A = nullptr;
@@ -298,7 +310,7 @@ hjm_status run_steps(const Group& g, int n_from, int n_to, cudaStream_t s)
     for (int n = n_from; n < n_to; ++n) {
         {
             TraceScope ts(2, s);
-            CU_TRY(launch_pass1<T>(P, U, A, n, s));
+            CU_TRY(launch_pass1<T>(P, U, A, n, g.tile, s));
         }
         {
             TraceScope ts(3, s);
@@ -345,9 +357,10 @@ hjm_status batch_graph(Workspace& ws, const std::vector<Group>& groups, size_t e
 {
     std::string key = std::to_string(elem);
     for (const auto& g : groups) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%p,%p,%p", g.nr, g.nv, g.ny, g.nsteps, g.t.B,
-                 (int)g.gpos, g.U, g.A, g.t.rt);
+        char buf[200];
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%p,%p,%p,%d.%d.%d.%d.%d.%d.%d", g.nr, g.nv, g.ny,
+                 g.nsteps, g.t.B, (int)g.gpos, g.U, g.A, g.t.rt, g.tile.p1_S, g.tile.p1_M, g.tile.p1_R, g.tile.p2_P,
+                 g.tile.p3_P, g.tile.p1_stage, g.tile.p1_J);
         key += buf;
     }
     auto it = ws.graphs.find(key);
@@ -431,6 +444,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
             groups.push_back(gr);
         }
         Group& gr = groups[f->second];
+        if (gr.idx.empty()) gr.tile = tile_for(gr.nr, gr.nv, gr.ny, elem);
         gr.idx.push_back(i);
         gr.gpos = gr.gpos || items[i].model.gamma > 0.0;
     }
@@ -472,6 +486,8 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         g.t.ny = g.ny;
         g.t.nsteps = g.nsteps;
         g.t.B = (int)B;
+        g.t.p2P = g.tile.p2_P;
+        g.t.p3P = g.tile.p3_P;
         g.t.params = *d_params + off;
         g.prices = group_prices + off;
         g.ind = group_ind + off;
@@ -613,7 +629,12 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
             infos[i].err_estimate = hi[i];
             infos[i].n_steps = items[i].grid.n_steps;
             infos[i].time_us = ms * 1000.f;
-            infos[i].tile_cfg = pass1_chunk(items[i].grid.n_r);
+            {
+                const hjm_grid_spec& gs = items[i].grid;
+                const Tile t = tile_for(gs.n_r, gs.n_v, gs.n_y, used[i] == HJM_FP64 ? sizeof(double) : sizeof(float));
+                infos[i].tile_cfg =
+                    t.p1_S | t.p1_M << 8 | t.p1_R << 14 | t.p2_P << 21 | t.p3_P << 25 | t.p1_stage << 29;
+            }
         }
     }
     if (sync) {
@@ -729,6 +750,226 @@ extern "C" hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm
     return price_batch(*stream_workspace(s), items, n, precision, tol_rel, prices_out, infos_out, s);
 }
 
+// ---------------------------------------------------------- launch shapes
+
+static bool tile_precision(hjm_precision precision, size_t& elem)
+{
+    if (precision != HJM_FP64 && precision != HJM_FP32 && precision != HJM_MIXED) return false;
+    elem = precision == HJM_FP64 ? sizeof(double) : sizeof(float);
+    return true;
+}
+
+static Tile from_abi(const hjm_tile& t)
+{
+    return Tile{t.p1_lanes, t.p1_nodes, t.p1_lines, t.p2_warps, t.p3_warps, t.p1_staged, t.p1_planes};
+}
+
+extern "C" hjm_status hjm_tile_get(int n_r, int n_v, int n_y, hjm_precision precision, hjm_tile* out)
+{
+    size_t elem;
+    if (!out) return fail(HJM_EINVAL, "null argument");
+    if (!tile_precision(precision, elem)) return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    if (n_r < 4 || n_v < 4 || n_y < 4) return fail(HJM_EINVAL, "node counts must be >= 4");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const Tile t = tile_for(n_r, n_v, n_y, elem);
+    *out = hjm_tile{t.p1_S, t.p1_M, t.p1_R, t.p2_P, t.p3_P, t.p1_stage, t.p1_J};
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_tile_set(int n_r, int n_v, int n_y, hjm_precision precision, const hjm_tile* tile)
+{
+    size_t elem;
+    if (!tile_precision(precision, elem)) return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    if (n_r < 4 || n_v < 4 || n_y < 4) return fail(HJM_EINVAL, "node counts must be >= 4");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const auto key = std::make_tuple(n_r, n_v, n_y, elem);
+    if (!tile) {
+        g_tiles.erase(key);
+        return HJM_OK;
+    }
+    const Tile t = from_abi(*tile);
+    if (!tile_valid(t, n_r, n_v, n_y, elem))
+        return fail(HJM_EINVAL, "tile (%d, %d, %d, %d, %d, %d, %d) is not available for %d x %d x %d", t.p1_S,
+                    t.p1_M, t.p1_R, t.p2_P, t.p3_P, t.p1_stage, t.p1_J, n_r, n_v, n_y);
+    g_tiles[key] = t;
+    return HJM_OK;
+}
+
+// Pass-1 shapes to try: every compiled shape that covers the r line without
+// more than doubling it (padding rows are identity rows, wasted work).
+static std::vector<Tile> pass1_candidates(int nr, int nv, int ny, size_t elem, const Tile& base)
+{
+    std::vector<Tile> out;
+    int cover = 1 << 30;  // fewest nodes of a compiled shape that covers n_r
+    for (int S : {8, 16, 32})
+        for (int M : {2, 4, 8, 16}) {
+            Tile t = base;
+            t.p1_S = S;
+            t.p1_M = M;
+            if (tile_valid(t, nr, nv, ny, elem)) cover = std::min(cover, S * M);
+        }
+    for (int S : {8, 16, 32})
+        for (int M : {2, 4, 8, 16}) {
+            if (S * M > std::max(2 * nr + 32, cover)) continue;
+            for (int R : {2, 4, 8}) {  // rows from global memory
+                Tile t = base;
+                t.p1_S = S;
+                t.p1_M = M;
+                t.p1_R = R;
+                t.p1_stage = 0;
+                t.p1_J = 0;
+                if (tile_valid(t, nr, nv, ny, elem)) out.push_back(t);
+            }
+            for (int R : {1, 2})  // staged y planes
+                for (int J : {8, 16, 32}) {
+                    Tile t = base;
+                    t.p1_S = S;
+                    t.p1_M = M;
+                    t.p1_R = R;
+                    t.p1_stage = 1;
+                    t.p1_J = J;
+                    if (tile_valid(t, nr, nv, ny, elem)) out.push_back(t);
+                }
+        }
+    return out;
+}
+
+// Device time of each pass over `ns` Douglas steps of group g with its
+// current tile (set-up and terminal field re-run first: the split factors
+// depend on the tile).
+template <typename T>
+static hjm_status time_passes(Group& g, int ns, cudaStream_t s, cudaEvent_t* ev, float ms[3])
+{
+    const size_t elem = sizeof(T);
+    g.t.p2P = g.tile.p2_P;
+    g.t.p3P = g.tile.p3_P;
+    CU_TRY(launch_setup(g.t, elem, s));
+    CU_TRY(launch_terminal(g.t, g.U, elem, s));
+    const March<T> P = march_args<T>(g.t);
+    T* U = (T*)g.U;
+    T* A = (T*)g.A;
+    ms[0] = ms[1] = ms[2] = 0.f;
+    for (int n = -1; n < ns; ++n) {  // n = -1: untimed warm-up step
+        const int sn = n < 0 ? 0 : n;
+        CU_TRY(cudaEventRecord(ev[0], s));
+        CU_TRY(launch_pass1<T>(P, U, A, sn, g.tile, s));
+        CU_TRY(cudaEventRecord(ev[1], s));
+        CU_TRY(launch_pass2<T>(P, A, A, s));
+        CU_TRY(cudaEventRecord(ev[2], s));
+        CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, sn, s));
+        CU_TRY(cudaEventRecord(ev[3], s));
+        CU_TRY(cudaEventSynchronize(ev[3]));
+        if (n < 0) continue;
+        for (int q = 0; q < 3; ++q) {
+            float t = 0.f;
+            CU_TRY(cudaEventElapsedTime(&t, ev[q], ev[q + 1]));
+            ms[q] += t;
+        }
+    }
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_precision precision, int steps,
+                                   void* cuda_stream)
+{
+    size_t elem;
+    if (n == 0) return HJM_OK;
+    if (!items) return fail(HJM_EINVAL, "null argument");
+    if (!tile_precision(precision, elem)) return fail(HJM_EINVAL, "unknown precision %d", (int)precision);
+    if (steps < 1 || steps > 1000) return fail(HJM_EINVAL, "steps must be in [1, 1000]");
+    for (size_t i = 0; i < n; ++i) {
+        hjm_status st = validate(items[i].curve, items[i].model, items[i].grid, &items[i].inst, elem);
+        if (st != HJM_OK) {
+            std::string why = g_last_error;
+            return fail(st, "item %zu: %s", i, why.c_str());
+        }
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    Workspace& ws = *stream_workspace(s);
+    // The batch's instruments by grid shape; each shape is timed on its own
+    // instruments, all marching with the first one's step count.
+    std::map<std::tuple<int, int, int>, std::vector<hjm_batch_item>> shapes;
+    for (size_t i = 0; i < n; ++i)
+        shapes[std::make_tuple(items[i].grid.n_r, items[i].grid.n_v, items[i].grid.n_y)].push_back(items[i]);
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evs;
+    for (auto& e : evs.e) CU_TRY(cudaEventCreate(&e));
+    for (auto& kv : shapes) {
+        std::vector<hjm_batch_item>& v = kv.second;
+        for (auto& it : v) it.grid.n_steps = v[0].grid.n_steps;
+        const int ns = std::min(steps, v[0].grid.n_steps);
+        const int nr = std::get<0>(kv.first), nv = std::get<1>(kv.first), ny = std::get<2>(kv.first);
+        std::vector<Group> groups;
+        InstParams* d_params;
+        long long* d_idx;
+        double* d_prices;
+        st = plan(ws, v.data(), v.size(), elem, groups, &d_params, &d_idx, &d_prices);
+        if (st != HJM_OK) return st;
+        std::vector<InstParams> hp;
+        for (auto& g : groups)
+            for (size_t i : g.idx) hp.push_back(to_params(v[i]));
+        CU_TRY(cudaMemcpyAsync(d_params, hp.data(), hp.size() * sizeof(InstParams), cudaMemcpyHostToDevice, s));
+        Group& g = groups[0];
+        Tile best = default_tile(nr, nv, ny, elem);
+        // Pass 1 shapes (passes 2 and 3 at their defaults), then the line
+        // splits of passes 2 and 3 (pass 1 at its best): each pass keeps the
+        // fastest of its own options, best of two timings.
+        std::vector<Tile> cands = pass1_candidates(nr, nv, ny, elem, best);
+        float best_ms[3] = {3.0e38f, 3.0e38f, 3.0e38f};
+        for (int phase = 0; phase < 2; ++phase) {
+            if (phase == 1) {
+                cands.clear();
+                for (int Pw : {1, 2, 4, 8}) {
+                    Tile t = best;
+                    t.p2_P = split_valid(nv, Pw) ? Pw : 1;
+                    t.p3_P = split_valid(ny, Pw) && !g.gpos ? Pw : 1;
+                    cands.push_back(t);
+                }
+                best_ms[1] = best_ms[2] = 3.0e38f;
+            }
+            for (const Tile& cand : cands) {
+                g.tile = cand;
+                float ms[3], mn[3] = {3.0e38f, 3.0e38f, 3.0e38f};
+                for (int rep = 0; rep < 2; ++rep) {
+                    st = elem == sizeof(float) ? time_passes<float>(g, ns, s, evs.e, ms)
+                                               : time_passes<double>(g, ns, s, evs.e, ms);
+                    if (st != HJM_OK) return st;
+                    for (int q = 0; q < 3; ++q) mn[q] = std::min(mn[q], ms[q]);
+                }
+                if (phase == 0 && mn[0] < best_ms[0]) {
+                    best_ms[0] = mn[0];
+                    best.p1_S = cand.p1_S;
+                    best.p1_M = cand.p1_M;
+                    best.p1_R = cand.p1_R;
+                    best.p1_stage = cand.p1_stage;
+                    best.p1_J = cand.p1_J;
+                }
+                if (phase == 1) {
+                    if (mn[1] < best_ms[1]) {
+                        best_ms[1] = mn[1];
+                        best.p2_P = cand.p2_P;
+                    }
+                    if (mn[2] < best_ms[2]) {
+                        best_ms[2] = mn[2];
+                        best.p3_P = cand.p3_P;
+                    }
+                }
+            }
+        }
+        g_tiles[std::make_tuple(nr, nv, ny, elem)] = best;
+    }
+    return HJM_OK;
+}
+
 // ---------------------------------------------------------- stepwise access
 
 // Set up one instrument on the grid's workspace (tables + terminal field).
@@ -815,13 +1056,13 @@ extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* ins
     cudaStream_t s = grid->stream;
     if (elem == sizeof(float)) {
         const March<float> P = march_args<float>(g.t);
-        if (pass == 1) CU_TRY(launch_pass1<float>(P, (const float*)in, (float*)out, step_n, s));
+        if (pass == 1) CU_TRY(launch_pass1<float>(P, (const float*)in, (float*)out, step_n, g.tile, s));
         if (pass == 2) CU_TRY(launch_pass2<float>(P, (const float*)in, (float*)out, s));
         if (pass == 3)
             CU_TRY(launch_pass3<float>(P, (const float*)in, (const float*)in2, (float*)out, g.gpos, step_n, s));
     } else {
         const March<double> P = march_args<double>(g.t);
-        if (pass == 1) CU_TRY(launch_pass1<double>(P, (const double*)in, (double*)out, step_n, s));
+        if (pass == 1) CU_TRY(launch_pass1<double>(P, (const double*)in, (double*)out, step_n, g.tile, s));
         if (pass == 2) CU_TRY(launch_pass2<double>(P, (const double*)in, (double*)out, s));
         if (pass == 3)
             CU_TRY(launch_pass3<double>(P, (const double*)in, (const double*)in2, (double*)out, g.gpos, step_n, s));
@@ -862,11 +1103,12 @@ void* g_static_addr[kStaticMaxDevices];  // device address of g_static_scratch, 
 std::mutex g_static_mu;
 
 template <typename T>
-hjm_status static_march(const GroupTables& t, void* U, void* A, int nsteps, bool gpos, cudaStream_t s)
+hjm_status static_march(const GroupTables& t, void* U, void* A, int nsteps, bool gpos, const Tile& tile,
+                        cudaStream_t s)
 {
     const March<T> P = march_args<T>(t);
     for (int n = 0; n < nsteps; ++n) {
-        CU_TRY(launch_pass1<T>(P, (const T*)U, (T*)A, n, s));
+        CU_TRY(launch_pass1<T>(P, (const T*)U, (T*)A, n, tile, s));
         CU_TRY(launch_pass2<T>(P, (const T*)A, (T*)A, s));
         CU_TRY(launch_pass3<T>(P, (const T*)A, (const T*)U, (T*)U, gpos, n, s));
     }
@@ -924,6 +1166,13 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     tables_carve(t, p, elem);
     p += tables_bytes(g.n_r, g.n_v, g.n_y, g.n_steps, 1, elem);
     double* ind = (double*)p;
+    Tile tile;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        tile = tile_for(g.n_r, g.n_v, g.n_y, elem);
+    }
+    t.p2P = tile.p2_P;
+    t.p3P = tile.p3_P;
     // Every region above is fully rewritten by the kernels below before it
     // is read (the set-up kernel also zeroes the rounding indicator), so no
     // clearing is needed between calls.
@@ -932,8 +1181,8 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     CU_TRY(launch_setup(t, elem, s));
     CU_TRY(launch_terminal(t, U, elem, s));
     const bool gpos = item->model.gamma > 0.0;
-    st = elem == sizeof(float) ? static_march<float>(t, U, A, g.n_steps, gpos, s)
-                               : static_march<double>(t, U, A, g.n_steps, gpos, s);
+    st = elem == sizeof(float) ? static_march<float>(t, U, A, g.n_steps, gpos, tile, s)
+                               : static_march<double>(t, U, A, g.n_steps, gpos, tile, s);
     if (st != HJM_OK) return st;
     CU_TRY(launch_readout(t, U, elem, price_out, ind, s));
     return HJM_OK;

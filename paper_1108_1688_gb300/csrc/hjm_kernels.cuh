@@ -13,6 +13,9 @@
 //   v LU     vf[b][3][n_v]            Thomas factors of I - theta dt A_v
 //   y LU     yf[b][n_v][3][n_y]       Thomas factors of I - theta dt A_y
 //                                     (gamma == 0 instruments only)
+//   v split  vp[b][sys]               factors of the v system split into
+//   y split  yp[b][n_v][sys]          p2P (p3P) chunks, one warp per chunk
+//                                     (see part_sys_size; y: gamma == 0)
 //   flags    fl[b][FL_N]              r_min Dirichlet, y face order, y LU
 //                                     present, read-out stencil corner (i, k)
 //   indicator acc[b][n_steps] (float) max |dU3| of each step over the 4 x 4
@@ -75,7 +78,37 @@ struct March {
     const T* yf;
     const int* fl;
     float* acc;  // [B][nsteps], rounding indicator of the FP32 march
+    const T* vp;
+    const T* yp;
+    int p2P, p3P;  // chunks per v line / y line (1: one thread per line)
 };
+
+// Largest number of chunks a strided line is split into, and the largest
+// chunk a thread holds in registers.
+constexpr int kMaxSplit = 8;
+constexpr int kMaxChunk = 32;
+
+// Elements of one split system of n rows in P chunks (layout, all offsets
+// even so pairs are aligned):
+//   [0, 2n)        (sub-diagonal, 1 / pivot) of each row, chunk-local LU
+//   [2n, 4n)       (V, W): the chunk's solution for a unit value of the
+//                  unknown before (V) and after (W) the chunk
+//   [4n, 4n+2PK)   per chunk p and reduced row q (K = 2 (P - 1)): the
+//                  coefficients of the reduced right-hand side q in the
+//                  unknowns just before and just after chunk p
+//   [4n+2PK, 5n+2PK)  c' of each row (chunk-local LU)
+__host__ __device__ inline size_t part_sys_size(int n, int P)
+{
+    const size_t K = 2 * (size_t)(P - 1);
+    return ((5 * (size_t)n + 2 * (size_t)P * K) + 3) & ~(size_t)3;
+}
+// Rows [s, s + L) of chunk p of a line of n nodes split in P chunks.
+__host__ __device__ inline void part_chunk(int n, int P, int p, int& s, int& L)
+{
+    const int q = n / P, r = n % P;
+    L = q + (p < r ? 1 : 0);
+    s = p * q + (p < r ? p : r);
+}
 
 // Group buffers produced by setup (all device pointers).
 struct GroupTables {
@@ -95,6 +128,9 @@ struct GroupTables {
     void* yf;
     int* fl;
     float* acc;           // [B][nsteps]
+    void* vp;             // split factors (sized for kMaxSplit chunks)
+    void* yp;
+    int p2P, p3P;         // chunks per v / y line used by set-up and march
 };
 
 // Bytes of the march-type tables of a group.
@@ -111,9 +147,26 @@ cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStre
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
                            double* indicators, cudaStream_t s);
 
+// Launch shapes of the three passes for one grid shape (heuristic default or
+// picked by the autotuner).
+struct Tile {
+    int p1_S;  // pass 1: lanes per r line (8, 16, 32)
+    int p1_M;  // pass 1: r nodes per lane; p1_S * p1_M >= n_r
+    int p1_R;  // pass 1: lines per lane segment per CTA
+    int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8)
+    int p3_P;  // pass 3: warps sharing each y line (1, 2, 4, 8)
+    int p1_stage;  // pass 1: 0 rows from global memory, 1 staged y planes
+    int p1_J;      // pass 1 staged: y planes marched per CTA (0 when not staged)
+};
+Tile default_tile(int nr, int nv, int ny, size_t elem);
+// Whether the kernels are compiled for t and it covers the grid shape.
+bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem);
+// Whether a line of n nodes can be split into Pw chunks (Pw = 1: unsplit).
+bool split_valid(int n, int Pw);
+
 // The three Douglas passes of step n (in/out as documented in hjm.h).
 template <typename T>
-cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, cudaStream_t s);
+cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>
@@ -122,6 +175,8 @@ cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bo
 // Raises the dynamic shared-memory limit of the strided-line kernels; call
 // once per device before launching or capturing.
 cudaError_t init_kernels();
+// The same for the staged pass-1 kernels (called by init_kernels).
+cudaError_t init_pass1();
 // Chunk size per lane used by pass 1 for this n_r (0 if unsupported).
 int pass1_chunk(int nr);
 // Largest line length pass 2 / pass 3 accept for this element size.

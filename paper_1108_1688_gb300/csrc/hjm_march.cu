@@ -209,6 +209,166 @@ __global__ void __launch_bounds__(32) k_pass3(const March<T> P, const T* in, con
     note_increment(P, fl, b, i, k, n, x);
 }
 
+// ---------------------------------------------------- split line solves
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+// Passes 2 (AXIS 0: v lines) and 3 (AXIS 1: y lines, fused with the update
+// U^{n+1} = U^n + dU3) with each line split into P chunks, one warp per
+// chunk and one lane per line (32 consecutive r nodes per CTA, so every
+// access is a 128-byte row):
+//   1. gather the chunk of the right-hand side (and of U^n in pass 3) into
+//      shared memory with asynchronous copies, all in flight at once;
+//   2. y = A_p^{-1} d in registers with the chunk's precomputed LU;
+//   3. publish the chunk's end values of y, barrier, and form the unknowns
+//      just before and after the chunk as weighted sums of the published
+//      values (weights: the inverse of the reduced system, precomputed);
+//   4. x = y - x_before V - x_after W, store.
+// Lines whose r node is a Dirichlet face keep the identity system.
+template <typename T, int MC, int AXIS>
+__global__ void __launch_bounds__(256) k_split_lines(const March<T> P, const T* in, const T* Un, T* out,
+                                                     const int step_n)
+{
+    using T2 = typename Pair<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int Pw = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+    const int nr = P.nr, nv = P.nv, ny = P.ny;
+    const int n = AXIS == 0 ? nv : ny;
+    const int other = AXIS == 0 ? ny : nv;
+    const int K = 2 * (Pw - 1);
+    T* red = reinterpret_cast<T*>(smem_raw);  // [K][32] reduced right-hand sides
+    T* col = red + K * 32;                    // [n][32] right-hand side
+    T* ucol = col + n * 32;                   // [n][32] U^n (pass 3)
+    const int tiles = (nr + 31) / 32;
+    const long long blk = blockIdx.x;
+    const int it = (int)(blk % tiles);
+    const int o = (int)((blk / tiles) % other);
+    const int b = (int)(blk / ((long long)tiles * other));
+    const int i = it * 32 + lane;
+    const bool live = i < nr;  // lanes past n_r only join the barrier
+    const int ic = live ? i : nr - 1;
+    const long long stride = AXIS == 0 ? (long long)nr : (long long)nr * nv;
+    const long long base = (long long)b * P.N + (AXIS == 0 ? (long long)o * nv * nr : (long long)o * nr) + ic;
+    int s, L;
+    part_chunk(n, Pw, c, s, L);
+    const T* F = AXIS == 0 ? P.vp + (size_t)b * part_sys_size(nv, kMaxSplit)
+                           : P.yp + ((size_t)b * nv + o) * part_sys_size(ny, kMaxSplit);
+    const T2* AB = reinterpret_cast<const T2*>(F) + s;          // (sub, 1/pivot)
+    const T2* VW = reinterpret_cast<const T2*>(F + 2 * n) + s;  // (V, W)
+    const T2* CF = reinterpret_cast<const T2*>(F + 4 * n) + c * K;
+    const T* CP = F + 4 * n + 2 * Pw * K + s;
+
+    // 1. gather.
+    const T* src = in + base + s * stride;
+    for (int m = 0; m < L; ++m) cp_async_elem(&col[(s + m) * 32 + lane], src + m * stride);
+    if constexpr (AXIS == 1) {
+        const T* usrc = Un + base + s * stride;
+        for (int m = 0; m < L; ++m) cp_async_elem(&ucol[(s + m) * 32 + lane], usrc + m * stride);
+    }
+    cp_async_commit();
+    cp_async_wait_pending(0);
+    T d[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+        if (m < L) d[m] = col[(s + m) * 32 + lane];
+    // 2. chunk solve with the local LU.
+    {
+        const T2 f = __ldg(AB);
+        d[0] *= f.y;
+    }
+#pragma unroll
+    for (int m = 1; m < MC; ++m)
+        if (m < L) {
+            const T2 f = __ldg(AB + m);
+            d[m] = (d[m] - f.x * d[m - 1]) * f.y;
+        }
+    T nxt = T(0), ylast = T(0);
+#pragma unroll
+    for (int m = MC - 1; m >= 0; --m)
+        if (m < L) {
+            const T cpm = m < L - 1 ? __ldg(CP + m) : T(0);
+            d[m] -= cpm * nxt;
+            nxt = d[m];
+            if (m == L - 1) ylast = nxt;
+        }
+    // 3. reduced system across the chunks of each line.
+    if (Pw > 1) {
+        if (c >= 1) red[(2 * c - 1) * 32 + lane] = d[0];
+        if (c + 1 < Pw) red[(2 * c) * 32 + lane] = ylast;
+        __syncthreads();
+        T xb = T(0), xa = T(0);
+        for (int q = 0; q < K; ++q) {
+            const T r = red[q * 32 + lane];
+            const T2 w = __ldg(CF + q);
+            xb += w.x * r;
+            xa += w.y * r;
+        }
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+            if (m < L) {
+                const T2 f = __ldg(VW + m);
+                d[m] -= f.x * xb + f.y * xa;
+            }
+    }
+    if (!live) return;
+    const int* fl = P.fl + (size_t)b * FL_N;
+    if (i == nr - 1 || (i == 0 && fl[FL_RLO_DIR])) {  // Dirichlet line: identity system
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+            if (m < L) d[m] = col[(s + m) * 32 + lane];
+    }
+    if constexpr (AXIS == 1)
+        if (c == 0) note_increment(P, fl, b, i, o, step_n, d[0]);  // dU3 at j = 0
+    T* dst = out + base + s * stride;
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+        if (m < L) {
+            if constexpr (AXIS == 1)
+                dst[m * stride] = ucol[(s + m) * 32 + lane] + d[m];
+            else
+                dst[m * stride] = d[m];
+        }
+}
+
+static size_t split_smem(int n, int Pw, int axis, size_t elem)
+{
+    return (size_t)(2 * (Pw - 1) + n * (axis == 1 ? 2 : 1)) * 32 * elem;
+}
+
+template <typename T, int AXIS>
+static cudaError_t split_launch(const March<T>& P, const T* in, const T* Un, T* out, int Pw, int step_n,
+                                cudaStream_t s)
+{
+    const int n = AXIS == 0 ? P.nv : P.ny;
+    const int other = AXIS == 0 ? P.ny : P.nv;
+    const int chunk = (n + Pw - 1) / Pw;
+    const long long blocks = (long long)P.B * other * ((P.nr + 31) / 32);
+    const size_t smem = split_smem(n, Pw, AXIS, sizeof(T));
+    const dim3 grid((unsigned)blocks), block(32 * Pw);
+    if (chunk <= 4) k_split_lines<T, 4, AXIS><<<grid, block, smem, s>>>(P, in, Un, out, step_n);
+    else if (chunk <= 8) k_split_lines<T, 8, AXIS><<<grid, block, smem, s>>>(P, in, Un, out, step_n);
+    else if (chunk <= 16) k_split_lines<T, 16, AXIS><<<grid, block, smem, s>>>(P, in, Un, out, step_n);
+    else if (chunk <= 32) k_split_lines<T, 32, AXIS><<<grid, block, smem, s>>>(P, in, Un, out, step_n);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+bool split_valid(int n, int Pw)
+{
+    return Pw == 1 || ((Pw == 2 || Pw == 4 || Pw == 8) && n >= 2 * Pw && (n + Pw - 1) / Pw <= kMaxChunk &&
+                       split_smem(n, Pw, 1, sizeof(double)) <= 227 * 1024);
+}
+
 // ------------------------------------------------------------- launchers
 
 static const size_t kSmemLimit = 227 * 1024;
@@ -224,6 +384,16 @@ int max_strided_len(size_t elem, bool gamma_pos)
 cudaError_t init_kernels()
 {
     cudaError_t e;
+    if ((e = init_pass1())) return e;
+#define SPLIT_ATTR(T_, MC_, AX_)                                                                             \
+    if ((e = cudaFuncSetAttribute(k_split_lines<T_, MC_, AX_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  (int)kSmemLimit)))                                                        \
+        return e;
+    SPLIT_ATTR(float, 4, 0) SPLIT_ATTR(float, 8, 0) SPLIT_ATTR(float, 16, 0) SPLIT_ATTR(float, 32, 0)
+    SPLIT_ATTR(float, 4, 1) SPLIT_ATTR(float, 8, 1) SPLIT_ATTR(float, 16, 1) SPLIT_ATTR(float, 32, 1)
+    SPLIT_ATTR(double, 4, 0) SPLIT_ATTR(double, 8, 0) SPLIT_ATTR(double, 16, 0) SPLIT_ATTR(double, 32, 0)
+    SPLIT_ATTR(double, 4, 1) SPLIT_ATTR(double, 8, 1) SPLIT_ATTR(double, 16, 1) SPLIT_ATTR(double, 32, 1)
+#undef SPLIT_ATTR
     if ((e = cudaFuncSetAttribute(k_pass2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
         return e;
     if ((e = cudaFuncSetAttribute(k_pass2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
@@ -236,6 +406,10 @@ cudaError_t init_kernels()
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s)
 {
+    if (P.p2P > 1) {
+        if (!split_valid(P.nv, P.p2P)) return cudaErrorInvalidValue;
+        return split_launch<T, 0>(P, in, nullptr, out, P.p2P, 0, s);
+    }
     const size_t smem = (size_t)P.nv * 32 * sizeof(T);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     const long long tiles = (long long)P.B * P.ny * ((P.nr + 31) / 32);
@@ -247,6 +421,11 @@ template <typename T>
 cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
                          int n, cudaStream_t s)
 {
+    // Split y lines need line-invariant y systems (gamma = 0 in the group).
+    if (P.p3P > 1 && !any_gamma_pos) {
+        if (!split_valid(P.ny, P.p3P)) return cudaErrorInvalidValue;
+        return split_launch<T, 1>(P, in, Un, out, P.p3P, n, s);
+    }
     const size_t smem = (size_t)P.ny * 32 * sizeof(T) * (any_gamma_pos ? 3 : 2);
     if (smem > kSmemLimit) return cudaErrorInvalidValue;
     const long long tiles = (long long)P.B * P.nv * ((P.nr + 31) / 32);

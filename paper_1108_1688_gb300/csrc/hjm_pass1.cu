@@ -35,6 +35,19 @@ __device__ __forceinline__ float fast_rcp<float>(float x)
     return __fdividef(1.0f, x);
 }
 
+// 16-byte asynchronous global -> shared copies (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit16() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait16()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <typename T, int M>
 __device__ __forceinline__ void p1_load(const T* __restrict__ row, int e0, int nr, T (&u)[M])
 {
@@ -163,14 +176,255 @@ __device__ __forceinline__ void seg_partition_solve(T (&a)[M], T (&b)[M], T (&c)
     d[M - 1] = xE;
 }
 
-// One CTA = 4 warps = 4 * (32/S) segments; each segment processes R lines of
-// one instrument (line index k + n_v j), all segments of a warp advancing
-// together so the width-S shuffles always see full warps.
-template <typename T, int S, int M, bool TS, bool PF>
+// Shared-memory layout of the r tables: tsm[q][sl][MP], lane sl's M nodes
+// contiguous, padded to MP so that 16-byte vector reads by consecutive lanes
+// fall in distinct banks (MP * sizeof(T) / 16 odd).
+template <typename T, int M>
+struct P1Layout {
+    static constexpr int W = (M * sizeof(T) >= 16) ? int(16 / sizeof(T)) : M;  // nodes per vector read
+    static constexpr int MP = (M * sizeof(T) < 16 || ((M * sizeof(T) / 16) & 1)) ? M : M + int(16 / sizeof(T));
+};
+
+template <typename T, int W>
+struct VecOf;
+template <>
+struct VecOf<float, 4> {
+    using type = float4;
+};
+template <>
+struct VecOf<float, 2> {
+    using type = float2;
+};
+template <>
+struct VecOf<double, 2> {
+    using type = double2;
+};
+
+template <typename T, int W>
+__device__ __forceinline__ void lds_vec(const T* p, T (&o)[W])
+{
+    const typename VecOf<T, W>::type x = *reinterpret_cast<const typename VecOf<T, W>::type*>(p);
+    if constexpr (W == 4) {
+        o[0] = x.x;
+        o[1] = x.y;
+        o[2] = x.z;
+        o[3] = x.w;
+    } else {
+        o[0] = x.x;
+        o[1] = x.y;
+    }
+}
+
+// Per-instrument scalars of one pass-1 launch.
+template <typename T>
+struct P1Inst {
+    int nr, nv, ny, rlo, yord;
+    T dt, w, aF, aI, dA;
+    const T* vt;
+    const T* yt;
+    const T* dir;  // Dirichlet data of this step: [2][n_y]
+};
+
+template <typename T>
+__device__ __forceinline__ P1Inst<T> p1_inst(const March<T>& P, int b, int n)
+{
+    P1Inst<T> I;
+    I.nr = P.nr;
+    I.nv = P.nv;
+    I.ny = P.ny;
+    const T* sc = P.sc + (size_t)b * SC_N;
+    const int* fl = P.fl + (size_t)b * FL_N;
+    I.dt = sc[SC_DT];
+    I.w = sc[SC_W];
+    I.aF = P.st[((size_t)b * P.nsteps + n) * 2];
+    I.aI = P.st[((size_t)b * P.nsteps + n) * 2 + 1];
+    I.dA = I.aF - I.aI;
+    I.rlo = fl[FL_RLO_DIR];
+    I.yord = fl[FL_YORDER];
+    I.vt = P.vt + (size_t)b * VT_N * P.nv;
+    I.yt = P.yt + (size_t)b * YT_N * P.ny;
+    I.dir = P.dir + (((size_t)b * P.nsteps + n) * 2) * P.ny;
+    return I;
+}
+
+// One r line (v node k, y node j) on an S-lane segment, lane sl holding nodes
+// e0 = sl M .. e0 + M - 1 (tables of this lane at tl, layout P1Layout):
+//   1. the right-hand side dU0 = dt F(U^n) from the five rows (centre, v-a,
+//      v-b, y-a, y-b; a, b the neighbours, one-sided on faces), face rows
+//      patched;
+//   2. the rows of I - theta dt A_r(t^{n+1/2}) from the r tables and the
+//      line's (v, y) (the input rows are dead by then, which bounds the
+//      registers at about 6 M + scalars);
+//   3. the partition solve. d returns dU1 on the lane's nodes.
+template <typename T, int S, int M>
+__device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl, int k, int j, const T (&uc)[M],
+                                        const T (&ua)[M], const T (&ub)[M], const T (&ya)[M], const T (&yb)[M],
+                                        T (&d)[M])
+{
+    constexpr int W = P1Layout<T, M>::W, MP = P1Layout<T, M>::MP;
+    const int nr = I.nr, nv = I.nv, ny = I.ny, e0 = sl * M;
+    const T* vt = I.vt;
+    const T* yt = I.yt;
+    const T v = vt[VT_V * nv + k];
+    const T g2 = vt[VT_G2 * nv + k], g5 = vt[VT_G5 * nv + k], fv = vt[VT_FV * nv + k];
+    const bool vin = k > 0 && k < nv - 1;
+    const bool yin = j > 0 && j < ny - 1;
+    const T vq = vin ? v * vt[VT_IJ * nv + k] : T(0);  // mixed term off on v faces
+    const T y = yt[YT_Y * ny + j], iJy = yt[YT_IJ * ny + j], ky = yt[YT_KY * ny + j];
+    const T aIy = I.aI + y, aFy = I.aF + y;
+    const T vy = v * iJy, kyy = ky * iJy;  // g6 = cy * vy + kyy
+    // v part A_v U = cA (U_{v,a} - U) + cB (U_{v,b} - U); centred inside,
+    // one-sided on the v faces (Section 7.3).
+    const T cA = vin ? g2 - g5 : (k == 0 ? T(4) * fv : T(-4) * fv);
+    const T cB = vin ? g2 + g5 : (k == 0 ? -fv : fv);
+    // y part A_y U = g6 (yA (U_{y,a} - U) + yB (U_{y,b} - U)).
+    const int yord = I.yord;
+    const T yA = yin ? T(-1) : (yord == 1 ? (j == 0 ? T(2) : T(-2)) : (j == 0 ? T(4) : T(-4)));
+    const T yB = yin ? T(1) : (yord == 1 ? T(0) : (j == 0 ? T(-1) : T(1)));
+    const T dt = I.dt, w = I.w;
+
+    // Neighbours across lanes by shuffles: U at the chunk's ends and, for the
+    // mixed term, wd = U_{v,b} - U_{v,a}.
+    const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
+    const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
+    const T wd_prev = __shfl_up_sync(0xffffffffu, ub[M - 1] - ua[M - 1], 1, S);
+    const T wd_next = __shfl_down_sync(0xffffffffu, ub[0] - ua[0], 1, S);
+
+#define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
+    // 1. right-hand side, every node as if interior in r.
+#pragma unroll
+    for (int m0 = 0; m0 < M; m0 += W) {
+        T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W], tC3[W], tCY[W];
+        TABV(RT_R, m0, tR);
+        TABV(RT_IJ, m0, tIJ);
+        TABV(RT_C1, m0, tC1);
+        TABV(RT_C4V, m0, tC4V);
+        TABV(RT_C4B, m0, tC4B);
+        TABV(RT_C3, m0, tC3);
+        TABV(RT_CY, m0, tCY);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int m = m0 + q;
+            const T u = uc[m];
+            const T um = m > 0 ? uc[m - 1] : uc_prev;
+            const T up = m < M - 1 ? uc[m + 1] : uc_next;
+            const T wp = m < M - 1 ? ub[m + 1] - ua[m + 1] : wd_next;
+            const T wm = m > 0 ? ub[m - 1] - ua[m - 1] : wd_prev;
+            const T g1 = tC1[q] * v;                               // zeta_rr / (J^2 h^2)
+            const T g4F = aFy * tIJ[q] + (tC4B[q] - v * tC4V[q]);  // g4 / (2h) at t^n
+            T f = g1 * ((up - u) - (u - um)) + g4F * (up - um) - tR[q] * u;
+            f += tC3[q] * vq * (wp - wm);
+            f += cA * (ua[m] - u) + cB * (ub[m] - u);
+            const T g6 = tCY[q] * vy + kyy;
+            f += g6 * (yA * (ya[m] - u) + yB * (yb[m] - u));
+            d[m] = dt * f;
+        }
+    }
+    const T gLo = I.dir[j], gHi = I.dir[ny + j];
+    if (sl == 0) {
+        if (I.rlo) {
+            d[0] = gLo - uc[0];
+        } else {
+            // gamma > 0: r = 0 face, one-sided first derivative, zeta_rr = 0
+            // and no mixed term (Section 7.3).
+            const T u = uc[0], u1 = uc[1], u2 = M >= 3 ? uc[M >= 3 ? 2 : 1] : uc_next;
+            const T fr = aFy * tl[RT_IJ * S * MP] + tl[RT_C4B * S * MP];  // mu_r / (2 h J) at t^n
+            T f = fr * (T(-3) * u + T(4) * u1 - u2) - tl[RT_R * S * MP] * u;
+            f += cA * (ua[0] - u) + cB * (ub[0] - u);
+            const T g6 = tl[RT_CY * S * MP] * vy + kyy;
+            f += g6 * (yA * (ya[0] - u) + yB * (yb[0] - u));
+            d[0] = dt * f;
+        }
+    }
+    if (e0 + M > nr - 1) {  // only lanes holding r_max or padding
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            const int e = e0 + m;
+            if (e >= nr - 1) d[m] = e == nr - 1 ? gHi - uc[m] : T(0);
+        }
+    }
+
+    // 2. rows of I - theta dt A_r(t^{n+1/2}).
+    T a[M], bb[M], c[M];
+#pragma unroll
+    for (int m0 = 0; m0 < M; m0 += W) {
+        T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W];
+        TABV(RT_R, m0, tR);
+        TABV(RT_IJ, m0, tIJ);
+        TABV(RT_C1, m0, tC1);
+        TABV(RT_C4V, m0, tC4V);
+        TABV(RT_C4B, m0, tC4B);
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            const int m = m0 + q;
+            const T g1 = tC1[q] * v;
+            const T g4I = aIy * tIJ[q] + (tC4B[q] - v * tC4V[q]);
+            a[m] = -w * (g1 - g4I);
+            bb[m] = T(1) + w * (T(2) * g1 + tR[q]);
+            c[m] = -w * (g1 + g4I);
+        }
+    }
+#undef TABV
+    if (sl == 0) {
+        if (I.rlo) {
+            a[0] = T(0);
+            bb[0] = T(1);
+            c[0] = T(0);
+        } else {
+            const T frI = T(2) * (aIy * tl[RT_IJ * S * MP] + tl[RT_C4B * S * MP]);  // mu_r / (h J) at t^{n+1/2}
+            a[0] = T(0);
+            bb[0] = T(1) + w * (frI + tl[RT_R * S * MP]);
+            c[0] = -w * frI;
+        }
+    }
+    if (e0 + M > nr - 1) {
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (e0 + m >= nr - 1) {
+                a[m] = T(0);
+                bb[m] = T(1);
+                c[m] = T(0);
+            }
+        }
+    }
+    // 3. solve.
+    seg_partition_solve<T, S, M>(a, bb, c, d, sl);
+}
+
+// Loads the r tables of instrument b into shared memory (layout P1Layout).
+template <typename T, int S, int M>
+__device__ __forceinline__ void p1_tables(const March<T>& P, int b, T* tsm)
+{
+    constexpr int MP = P1Layout<T, M>::MP;
+    const int nr = P.nr;
+    const T* __restrict__ rt = P.rt + (size_t)b * RT_N * nr;
+    for (int idx = threadIdx.x; idx < RT_N * S * M; idx += blockDim.x) {
+        const int q = idx / (S * M), e = idx % (S * M);
+        tsm[(q * S + e / M) * MP + e % M] = e < nr ? rt[q * nr + e] : T(0);
+    }
+}
+
+// Neighbour rows of line (k, j): v-a, v-b, y-a, y-b (one-sided on faces).
+__device__ __forceinline__ void p1_neighbours(int k, int j, int nv, int ny, int& ka, int& kb, int& ja, int& jb)
+{
+    const bool vin = k > 0 && k < nv - 1;
+    ka = vin ? k - 1 : (k == 0 ? 1 : nv - 2);
+    kb = vin ? k + 1 : (k == 0 ? 2 : nv - 3);
+    const bool yin = j > 0 && j < ny - 1;
+    ja = yin ? j - 1 : (j == 0 ? 1 : ny - 2);
+    jb = yin ? j + 1 : (j == 0 ? 2 : ny - 3);
+}
+
+// Pass 1, rows from global memory: one CTA = 4 warps = 4 * (32/S) segments;
+// each segment processes R lines of one instrument (line index k + n_v j),
+// all segments of a warp advancing together so the width-S shuffles always
+// see full warps.
+template <typename T, int S, int M>
 __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __restrict__ U,
                                                T* __restrict__ out, const int n, const int R)
 {
     constexpr int G = 32 / S;
+    constexpr int MP = P1Layout<T, M>::MP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int seg = lane / S, sl = lane % S;
     const int nr = P.nr, nv = P.nv, ny = P.ny;
@@ -178,310 +432,273 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
     const int lpc = 4 * G * R;
     const int bpi = (L + lpc - 1) / lpc;
     const int b = blockIdx.x / bpi, cb = blockIdx.x % bpi;
-
     const T* __restrict__ Ub = U + (long long)b * P.N;
     T* __restrict__ Ob = out + (long long)b * P.N;
-    const T* __restrict__ rt = P.rt + (size_t)b * RT_N * nr;
-    const T* __restrict__ vt = P.vt + (size_t)b * VT_N * nv;
-    const T* __restrict__ yt = P.yt + (size_t)b * YT_N * ny;
-    const T* __restrict__ sc = P.sc + (size_t)b * SC_N;
-    const int* __restrict__ fl = P.fl + (size_t)b * FL_N;
-    const T dt = sc[SC_DT], w = sc[SC_W];
-    const T aF = P.st[((size_t)b * P.nsteps + n) * 2];
-    const T aI = P.st[((size_t)b * P.nsteps + n) * 2 + 1];
-    const T dA = aF - aI;
-    const int rlo = fl[FL_RLO_DIR], yord = fl[FL_YORDER];
-    const T* __restrict__ dir = P.dir + (((size_t)b * P.nsteps + n) * 2) * ny;
-
-    // r-factor chunks of this lane, loaded once for all lines of the CTA:
-    // in registers, or (TS) in shared memory laid out [table][m][lane in
-    // segment] so each read is conflict-free.
+    const P1Inst<T> I = p1_inst(P, b, n);
     const int e0 = sl * M;
-    __shared__ T tsm[TS ? RT_N * M * S : 1];
-    T tR[TS ? 1 : M], tIJ[TS ? 1 : M], tC1[TS ? 1 : M], tC4V[TS ? 1 : M], tC4B[TS ? 1 : M],
-        tC3[TS ? 1 : M], tCY[TS ? 1 : M];
-    if constexpr (TS) {
-        for (int idx = threadIdx.x; idx < RT_N * M * S; idx += blockDim.x) {
-            const int q = idx / (M * S), e = idx % (M * S);
-            tsm[(q * M + e % M) * S + e / M] = e < nr ? rt[q * nr + e] : T(0);
-        }
-        __syncthreads();
-    } else {
-        p1_load<T, M>(rt + RT_R * nr, e0, nr, tR);
-        p1_load<T, M>(rt + RT_IJ * nr, e0, nr, tIJ);
-        p1_load<T, M>(rt + RT_C1 * nr, e0, nr, tC1);
-        p1_load<T, M>(rt + RT_C4V * nr, e0, nr, tC4V);
-        p1_load<T, M>(rt + RT_C4B * nr, e0, nr, tC4B);
-        p1_load<T, M>(rt + RT_C3 * nr, e0, nr, tC3);
-        p1_load<T, M>(rt + RT_CY * nr, e0, nr, tCY);
-    }
-#define TAB(arr, q, m) (TS ? tsm[((q) * M + (m)) * S + sl] : arr[TS ? 0 : (m)])
-
-    // Rows of the current line (and, with PF, of the next one, loaded while
-    // the current line is computed).
-    auto line_rows = [&](int it, int& k, int& j, bool& valid, int& ka, int& kb, int& ja, int& jb) {
-        const int line = cb * lpc + (warp * R + it) * G + seg;
-        valid = line < L;
-        const int lc = valid ? line : L - 1;  // keep addresses in bounds
-        k = lc % nv;
-        j = lc / nv;
-        const bool vin_ = k > 0 && k < nv - 1;
-        ka = vin_ ? k - 1 : (k == 0 ? 1 : nv - 2);
-        kb = vin_ ? k + 1 : (k == 0 ? 2 : nv - 3);
-        const bool yin_ = j > 0 && j < ny - 1;
-        ja = yin_ ? j - 1 : (j == 0 ? 1 : ny - 2);
-        jb = yin_ ? j + 1 : (j == 0 ? 2 : ny - 3);
-    };
-    T uc[M], ua[M], ub[M], ya[M], yb[M];
-    T nuc[PF ? M : 1], nua[PF ? M : 1], nub[PF ? M : 1], nya[PF ? M : 1], nyb[PF ? M : 1];
-    int k, j, ka, kb, ja, jb;
-    bool valid;
-    line_rows(0, k, j, valid, ka, kb, ja, jb);
-    auto load5 = [&](int k_, int j_, int ka_, int kb_, int ja_, int jb_, T (&c_)[M], T (&a_)[M],
-                     T (&b_)[M], T (&ya_)[M], T (&yb_)[M]) {
-        p1_load<T, M>(Ub + ((long long)j_ * nv + k_) * nr, e0, nr, c_);
-        p1_load<T, M>(Ub + ((long long)j_ * nv + ka_) * nr, e0, nr, a_);
-        p1_load<T, M>(Ub + ((long long)j_ * nv + kb_) * nr, e0, nr, b_);
-        p1_load<T, M>(Ub + ((long long)ja_ * nv + k_) * nr, e0, nr, ya_);
-        p1_load<T, M>(Ub + ((long long)jb_ * nv + k_) * nr, e0, nr, yb_);
-    };
-    load5(k, j, ka, kb, ja, jb, uc, ua, ub, ya, yb);
-
+    __shared__ __align__(16) T tsm[RT_N * S * MP];
+    p1_tables<T, S, M>(P, b, tsm);
+    __syncthreads();
+    const T* tl = tsm + sl * MP;
     for (int it = 0; it < R; ++it) {
-        int nk = 0, nj = 0, nka = 0, nkb = 0, nja = 0, njb = 0;
-        bool nvalid = false;
-        if constexpr (PF) {
-            if (it + 1 < R) {
-                line_rows(it + 1, nk, nj, nvalid, nka, nkb, nja, njb);
-                load5(nk, nj, nka, nkb, nja, njb, nuc, nua, nub, nya, nyb);
-            }
-        }
-
-        const T v = vt[VT_V * nv + k];
-        const T g2 = vt[VT_G2 * nv + k], g5 = vt[VT_G5 * nv + k], fv = vt[VT_FV * nv + k];
-        const T vq = v * vt[VT_IJ * nv + k];
-        const T y = yt[YT_Y * ny + j], iJy = yt[YT_IJ * ny + j], ky = yt[YT_KY * ny + j];
-        const T aIy = aI + y, aFy = aF + y;
-        const T vy = v * iJy, kyy = ky * iJy;  // g6 = cy * vy + kyy
-        const T gLo = dir[j], gHi = dir[ny + j];
-
-        const bool vin = k > 0 && k < nv - 1;
-        const bool yin = j > 0 && j < ny - 1;
-        T d[M];
-        const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
-        const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
-        const T ua_prev = __shfl_up_sync(0xffffffffu, ua[M - 1], 1, S);
-        const T ua_next = __shfl_down_sync(0xffffffffu, ua[0], 1, S);
-        const T ub_prev = __shfl_up_sync(0xffffffffu, ub[M - 1], 1, S);
-        const T ub_next = __shfl_down_sync(0xffffffffu, ub[0], 1, S);
-
-        T a[M], bb[M], c[M];
-        // r part, the r-v mixed term and the rows of I - theta dt A_r(t^{n+1/2}),
-        // for every node as if interior in r (the r faces are patched below).
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            const T u = uc[m];
-            const T um = m > 0 ? uc[m - 1] : uc_prev;
-            const T up = m < M - 1 ? uc[m + 1] : uc_next;
-            const T g1 = TAB(tC1, RT_C1, m) * v;                                  // zeta_rr/(J^2 h^2)
-            const T g4I = aIy * TAB(tIJ, RT_IJ, m) + (TAB(tC4B, RT_C4B, m) - v * TAB(tC4V, RT_C4V, m));     // g4/(2h) at t^{n+1/2}
-            const T g4F = g4I + dA * TAB(tIJ, RT_IJ, m);                          // g4/(2h) at t^n
-            T f = g1 * ((up - u) - (u - um)) + g4F * (up - um) - TAB(tR, RT_R, m) * u;
-            const T bp = m < M - 1 ? ub[m + 1] : ub_next, bm = m > 0 ? ub[m - 1] : ub_prev;
-            const T ap = m < M - 1 ? ua[m + 1] : ua_next, am = m > 0 ? ua[m - 1] : ua_prev;
-            if (vin) f += TAB(tC3, RT_C3, m) * vq * ((bp - bm) - (ap - am));
-            d[m] = f;
-            a[m] = -w * (g1 - g4I);
-            bb[m] = T(1) + w * (T(2) * g1 + TAB(tR, RT_R, m));
-            c[m] = -w * (g1 + g4I);
-        }
-        // v and y parts (face lines use one-sided differences, Section 7.3).
-        if (vin && yin) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const T u = uc[m];
-                const T g6 = TAB(tCY, RT_CY, m) * vy + kyy;
-                d[m] = dt * (d[m] + g2 * ((ub[m] - u) - (u - ua[m])) + g5 * (ub[m] - ua[m]) +
-                             g6 * (yb[m] - ya[m]));
-            }
-        } else {
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const T u = uc[m];
-                T Av;
-                if (vin)
-                    Av = g2 * ((ub[m] - u) - (u - ua[m])) + g5 * (ub[m] - ua[m]);
-                else if (k == 0)
-                    Av = fv * (T(-3) * u + T(4) * ua[m] - ub[m]);
-                else
-                    Av = fv * (T(3) * u - T(4) * ua[m] + ub[m]);
-                const T g6 = TAB(tCY, RT_CY, m) * vy + kyy;
-                T Ay;
-                if (yin)
-                    Ay = g6 * (yb[m] - ya[m]);
-                else if (j == 0)
-                    Ay = yord == 1 ? T(2) * g6 * (ya[m] - u) : g6 * (T(-3) * u + T(4) * ya[m] - yb[m]);
-                else
-                    Ay = yord == 1 ? T(2) * g6 * (u - ya[m]) : g6 * (T(3) * u - T(4) * ya[m] + yb[m]);
-                d[m] = dt * (d[m] + Av + Ay);
-            }
-        }
-        // r faces: Dirichlet rows at r_max (and r_min when gamma = 0), the
-        // degenerate r = 0 face when gamma > 0, identity padding rows.
-        if (sl == 0) {
-            if (rlo) {
-                d[0] = gLo - uc[0];
-                a[0] = T(0);
-                bb[0] = T(1);
-                c[0] = T(0);
-            } else {
-                // one-sided first derivative, zeta_rr = 0 and no mixed term at r = 0;
-                // recompute the node's F without the centred r and mixed parts.
-                const T u = uc[0], u1 = uc[1], u2 = M >= 3 ? uc[M >= 3 ? 2 : 1] : uc_next;
-                const T fr = aFy * TAB(tIJ, RT_IJ, 0) + TAB(tC4B, RT_C4B, 0);  // mu_r / (2 h J) at t^n
-                T Av;
-                if (vin)
-                    Av = g2 * ((ub[0] - u) - (u - ua[0])) + g5 * (ub[0] - ua[0]);
-                else if (k == 0)
-                    Av = fv * (T(-3) * u + T(4) * ua[0] - ub[0]);
-                else
-                    Av = fv * (T(3) * u - T(4) * ua[0] + ub[0]);
-                const T g6 = TAB(tCY, RT_CY, 0) * vy + kyy;
-                T Ay;
-                if (yin)
-                    Ay = g6 * (yb[0] - ya[0]);
-                else if (j == 0)
-                    Ay = yord == 1 ? T(2) * g6 * (ya[0] - u) : g6 * (T(-3) * u + T(4) * ya[0] - yb[0]);
-                else
-                    Ay = yord == 1 ? T(2) * g6 * (u - ya[0]) : g6 * (T(3) * u - T(4) * ya[0] + yb[0]);
-                d[0] = dt * (fr * (T(-3) * u + T(4) * u1 - u2) - TAB(tR, RT_R, 0) * u + Av + Ay);
-                const T frI = T(2) * (aIy * TAB(tIJ, RT_IJ, 0) + TAB(tC4B, RT_C4B, 0));  // mu_r / (h J) at t^{n+1/2}
-                a[0] = T(0);
-                bb[0] = T(1) + w * (frI + TAB(tR, RT_R, 0));
-                c[0] = -w * frI;
-            }
-        }
-        if (e0 + M > nr - 1) {  // only lanes holding r_max or padding
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                const int e = e0 + m;
-                if (e >= nr - 1) {
-                    d[m] = e == nr - 1 ? gHi - uc[m] : T(0);
-                    a[m] = T(0);
-                    bb[m] = T(1);
-                    c[m] = T(0);
-                }
-            }
-        }
-        seg_partition_solve<T, S, M>(a, bb, c, d, sl);
+        const int line = cb * lpc + (warp * R + it) * G + seg;
+        const bool valid = line < L;
+        const int lc = valid ? line : L - 1;  // keep addresses in bounds
+        const int k = lc % nv, j = lc / nv;
+        int ka, kb, ja, jb;
+        p1_neighbours(k, j, nv, ny, ka, kb, ja, jb);
+        T uc[M], ua[M], ub[M], ya[M], yb[M], d[M];
+        p1_load<T, M>(Ub + ((long long)j * nv + k) * nr, e0, nr, uc);
+        p1_load<T, M>(Ub + ((long long)j * nv + ka) * nr, e0, nr, ua);
+        p1_load<T, M>(Ub + ((long long)j * nv + kb) * nr, e0, nr, ub);
+        p1_load<T, M>(Ub + ((long long)ja * nv + k) * nr, e0, nr, ya);
+        p1_load<T, M>(Ub + ((long long)jb * nv + k) * nr, e0, nr, yb);
+        p1_line<T, S, M>(I, tl, sl, k, j, uc, ua, ub, ya, yb, d);
         if (valid) p1_store<T, M>(Ob + ((long long)j * nv + k) * nr, e0, nr, d);
-        if (it + 1 < R) {
-            if constexpr (PF) {
+    }
+}
+
+// Pass 1 with staged planes: a CTA owns a strip of KB = 4 (32/S) RK
+// consecutive v nodes and marches over a run of JC y nodes. The rows of the
+// strip (plus two v neighbours each side) of y planes j-1, j, j+1 sit in a
+// ring of four shared-memory slots; plane j+2 is copied in asynchronously
+// (cp.async, 16 bytes per copy) while plane j is computed, so every row of
+// U^n crosses L2 about once instead of five times. Rows are stored with the
+// 16-byte chunk index XOR-swizzled so that the lanes' vector reads of their
+// M-node chunks hit distinct banks. The y-face lines read their second y
+// neighbour (a plane outside the ring) from global memory.
+template <typename T, int M>
+__device__ __forceinline__ int p1s_swz(int c)
+{
+    constexpr int CPL = (M * (int)sizeof(T)) / 16;  // 16-byte chunks per lane
+    if constexpr (CPL >= 2)
+        return c ^ ((c >> 3) & (CPL - 1));
+    else
+        return c;
+}
+
+template <typename T, int M>
+__device__ __forceinline__ void p1s_row(const T* row, int e0, T (&u)[M])
+{
+    constexpr int V = 16 / sizeof(T);
+    if constexpr (M * sizeof(T) >= 16) {
 #pragma unroll
-                for (int m = 0; m < M; ++m) {
-                    uc[m] = nuc[m];
-                    ua[m] = nua[m];
-                    ub[m] = nub[m];
-                    ya[m] = nya[m];
-                    yb[m] = nyb[m];
-                }
-                k = nk;
-                j = nj;
-                valid = nvalid;
-            } else {
-                line_rows(it + 1, k, j, valid, ka, kb, ja, jb);
-                load5(k, j, ka, kb, ja, jb, uc, ua, ub, ya, yb);
+        for (int q = 0; q < M / V; ++q) {
+            T x[V];
+            lds_vec<T, V>(row + p1s_swz<T, M>(e0 / V + q) * V, x);
+#pragma unroll
+            for (int t = 0; t < V; ++t) u[q * V + t] = x[t];
+        }
+    } else {
+        lds_vec<T, M>(row + e0, u);
+    }
+}
+
+// Padded row stride of the ring (elements): whole groups of 8 chunks (the
+// swizzle permutes within them) covering both the row and the lanes' reads.
+__host__ __device__ inline int p1s_row_stride(int nr, int SM, int V)
+{
+    const int ch = (nr > SM ? nr : SM) / V + ((nr > SM ? nr : SM) % V != 0);
+    return ((ch + 7) & ~7) * V;
+}
+
+template <typename T, int S, int M>
+__global__ void __launch_bounds__(128, 4) k_pass1s(const March<T> P, const T* __restrict__ U,
+                                                T* __restrict__ out, const int n, const int RK, const int JC)
+{
+    constexpr int G = 32 / S;
+    constexpr int MP = P1Layout<T, M>::MP;
+    constexpr int V = 16 / sizeof(T);
+    extern __shared__ __align__(16) unsigned char p1s_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int seg = lane / S, sl = lane % S;
+    const int sg = warp * G + seg;  // segment index in the CTA
+    const int nr = P.nr, nv = P.nv, ny = P.ny;
+    const int KB = 4 * G * RK;
+    const int strips = (nv + KB - 1) / KB, runs = (ny + JC - 1) / JC;
+    const int b = blockIdx.x / (strips * runs);
+    const int st = (blockIdx.x / runs) % strips, rn = blockIdx.x % runs;
+    const int k0 = st * KB, k1 = min(k0 + KB, nv);
+    const int klo = max(k0 - 2, 0), khi = min(k1 + 1, nv - 1);
+    const int nrows = khi - klo + 1;
+    const int j0 = rn * JC, j1 = min(j0 + JC, ny);
+    const int CPR = nr / V;  // 16-byte chunks per row
+    const int RS = p1s_row_stride(nr, S * M, V);
+    const int SLOT = (KB + 4) * RS;              // elements per ring slot
+    const T* __restrict__ Ub = U + (long long)b * P.N;
+    T* __restrict__ Ob = out + (long long)b * P.N;
+    const P1Inst<T> I = p1_inst(P, b, n);
+    const int e0 = sl * M;
+
+    T* tsm = reinterpret_cast<T*>(p1s_raw);          // r tables
+    T* ring = tsm + ((RT_N * S * MP + V - 1) / V) * V;  // 4 slots
+    p1_tables<T, S, M>(P, b, tsm);
+    for (int idx = threadIdx.x; idx < 4 * SLOT; idx += blockDim.x) ring[idx] = T(0);  // padding stays 0
+    __syncthreads();
+    const T* tl = tsm + sl * MP;
+
+    auto load_plane = [&](int jp) {
+        if (jp >= 0 && jp < ny && jp <= j1) {
+            T* dst = ring + (jp & 3) * SLOT;
+            const T* src = Ub + ((long long)jp * nv + klo) * nr;
+            for (int c = threadIdx.x; c < nrows * CPR; c += blockDim.x) {
+                const int r = c / CPR, ch = c % CPR;
+                cp_async16(dst + r * RS + p1s_swz<T, M>(ch) * V, src + (long long)r * nr + ch * V);
             }
         }
+        cp_async_commit16();
+    };
+    load_plane(j0 - 1);
+    load_plane(j0);
+    load_plane(j0 + 1);
+    for (int j = j0; j < j1; ++j) {
+        __syncthreads();  // every thread is done with plane j-2's slot
+        load_plane(j + 2);
+        cp_async_wait16<1>();  // this thread's copies of planes <= j+1 landed
+        __syncthreads();       // and everyone's
+        const T* pc = ring + (j & 3) * SLOT;
+        for (int r = 0; r < RK; ++r) {
+            const int kk = k0 + sg + 4 * G * r;
+            const bool valid = kk < k1;
+            const int k = valid ? kk : k1 - 1;
+            int ka, kb, ja, jb;
+            p1_neighbours(k, j, nv, ny, ka, kb, ja, jb);
+            T uc[M], ua[M], ub[M], ya[M], yb[M], d[M];
+            p1s_row<T, M>(pc + (k - klo) * RS, e0, uc);
+            p1s_row<T, M>(pc + (ka - klo) * RS, e0, ua);
+            p1s_row<T, M>(pc + (kb - klo) * RS, e0, ub);
+            // y neighbours: in the ring unless two planes away (y faces)
+            if (ja >= j - 1 && ja <= j + 1)
+                p1s_row<T, M>(ring + (ja & 3) * SLOT + (k - klo) * RS, e0, ya);
+            else
+                p1_load<T, M>(Ub + ((long long)ja * nv + k) * nr, e0, nr, ya);
+            if (jb >= j - 1 && jb <= j + 1)
+                p1s_row<T, M>(ring + (jb & 3) * SLOT + (k - klo) * RS, e0, yb);
+            else
+                p1_load<T, M>(Ub + ((long long)jb * nv + k) * nr, e0, nr, yb);
+            p1_line<T, S, M>(I, tl, sl, k, j, uc, ua, ub, ya, yb, d);
+            if (valid) p1_store<T, M>(Ob + ((long long)j * nv + k) * nr, e0, nr, d);
+        }
     }
-#undef TAB
+    cp_async_wait16<0>();
 }
 
-// (S, M, R) per r-line length: M nodes per lane, S lanes per line, R lines
-// per segment per CTA.
-struct P1Shape {
-    int S, M, R, TS, PF;
-};
-
-// HJM_PASS1_SHAPE="S,M,R,TS,PF" overrides the table below (tuning experiments).
-static bool p1_override(P1Shape& sh)
+// Pass-1 shapes compiled for each element type: (S, M) with S lanes per r
+// line and M nodes per lane.
+static bool p1_compiled(size_t elem, int S, int M)
 {
-    static int state = -1;
-    static P1Shape ov{0, 0, 0};
-    if (state < 0) {
-        const char* e = getenv("HJM_PASS1_SHAPE");
-        state = e && sscanf(e, "%d,%d,%d,%d,%d", &ov.S, &ov.M, &ov.R, &ov.TS, &ov.PF) == 5 ? 1 : 0;
-    }
-    if (state) sh = ov;
-    return state == 1;
+    if (elem == 4)
+        return (S == 8 && (M == 8 || M == 16)) || (S == 16 && (M == 4 || M == 8 || M == 16)) ||
+               (S == 32 && (M == 2 || M == 4 || M == 8 || M == 16));
+    return (S == 16 && (M == 2 || M == 4 || M == 8)) || (S == 32 && (M == 2 || M == 4 || M == 8 || M == 16));
 }
 
-static P1Shape p1_shape(int nr, size_t elem)
+static constexpr size_t kP1SmemLimit = 227 * 1024;
+
+// Dynamic shared memory of the staged kernel (tables + four ring slots).
+static size_t p1s_smem(int nr, int S, int M, int RK, size_t elem)
 {
-    P1Shape ov;
-    if (p1_override(ov) && ov.S * ov.M >= nr) return ov;
-    // Measured on GB300 (config-2-shaped batches): tables in shared memory
-    // (128 registers, 16 warps per SM) beat tables in registers (173
-    // registers) by 1.3-1.4x; prefetching the next line's rows costs more in
-    // occupancy than it hides.
+    const int V = (int)(16 / elem);
+    const int Wt = (M * (int)elem >= 16) ? V : M;
+    (void)Wt;
+    const int MP = (M * (int)elem < 16 || (((M * (int)elem) / 16) & 1)) ? M : M + V;
+    const size_t tab = (size_t)((RT_N * S * MP + V - 1) / V) * V;
+    const int KB = 4 * (32 / S) * RK;
+    const size_t slot = (size_t)(KB + 4) * p1s_row_stride(nr, S * M, V);
+    return (tab + 4 * slot) * elem;
+}
+
+Tile default_tile(int nr, int nv, int ny, size_t elem)
+{
+    (void)nv;
+    (void)ny;
+    Tile t{32, 16, 4, 1, 1, 0, 0};
+    // Heuristic table (the autotuner may replace it per grid shape).
     if (elem == 4) {
-        if (nr <= 64) return {8, 8, 4, 1, 0};
-        if (nr <= 128) return {16, 8, 4, 1, 0};
-        if (nr <= 256) return {32, 8, 4, 1, 0};
-        return {32, 16, 4, 1, 0};
+        if (nr <= 64) t = {8, 8, 4, 1, 1, 0, 0};
+        else if (nr <= 128) t = {16, 8, 4, 1, 1, 0, 0};
+        else if (nr <= 256) t = {32, 8, 4, 1, 1, 0, 0};
+    } else {
+        if (nr <= 32) t = {16, 2, 4, 1, 1, 0, 0};
+        else if (nr <= 64) t = {16, 4, 4, 1, 1, 0, 0};
+        else if (nr <= 128) t = {32, 4, 4, 1, 1, 0, 0};
+        else if (nr <= 256) t = {32, 8, 4, 1, 1, 0, 0};
     }
-    if (nr <= 32) return {16, 2, 4, 1, 0};
-    if (nr <= 64) return {16, 4, 4, 1, 0};
-    if (nr <= 128) return {32, 4, 4, 1, 0};
-    if (nr <= 256) return {32, 8, 4, 1, 0};
-    return {32, 16, 4, 1, 0};
+    return t;
+}
+
+bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
+{
+    if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
+    if (!split_valid(nv, t.p2_P) || !split_valid(ny, t.p3_P)) return false;
+    if (t.p1_stage == 0) return t.p1_J == 0;
+    if (t.p1_stage != 1 || t.p1_J < 1 || t.p1_J > 4096) return false;
+    // staged rows are copied in 16-byte pieces
+    if ((nr * (int)elem) % 16 != 0) return false;
+    return p1s_smem(nr, t.p1_S, t.p1_M, t.p1_R, elem) <= kP1SmemLimit;
 }
 
 int pass1_chunk(int nr)
 {
-    return nr <= 512 ? p1_shape(nr, 4).M : 0;
-}
-
-template <typename T, int S, int M, bool TS, bool PF>
-static cudaError_t p1_launch(const March<T>& P, const T* U, T* out, int n, int R, cudaStream_t s)
-{
-    const int lpc = 4 * (32 / S) * R;
-    const int bpi = (P.nv * P.ny + lpc - 1) / lpc;
-    k_pass1<T, S, M, TS, PF><<<(unsigned)(bpi * P.B), 128, 0, s>>>(P, U, out, n, R);
-    return cudaGetLastError();
+    return nr <= 512 ? default_tile(nr, 0, 0, 4).p1_M : 0;
 }
 
 template <typename T, int S, int M>
-static cudaError_t p1_launch_v(const March<T>& P, const T* U, T* out, int n, const P1Shape& sh,
-                               cudaStream_t s)
+static cudaError_t p1_launch(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s)
 {
-    if (sh.TS && sh.PF) return p1_launch<T, S, M, true, true>(P, U, out, n, sh.R, s);
-    if (sh.TS) return p1_launch<T, S, M, true, false>(P, U, out, n, sh.R, s);
-    if (sh.PF) return p1_launch<T, S, M, false, true>(P, U, out, n, sh.R, s);
-    return p1_launch<T, S, M, false, false>(P, U, out, n, sh.R, s);
+    if (t.p1_stage == 1 && (reinterpret_cast<uintptr_t>(U) & 15) == 0) {
+        const int KB = 4 * (32 / S) * t.p1_R;
+        const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
+        const size_t smem = p1s_smem(P.nr, S, M, t.p1_R, sizeof(T));
+        k_pass1s<T, S, M><<<(unsigned)((long long)P.B * strips * runs), 128, smem, s>>>(P, U, out, n, t.p1_R,
+                                                                                       t.p1_J);
+        return cudaGetLastError();
+    }
+    const int lpc = 4 * (32 / S) * t.p1_R;
+    const int bpi = (P.nv * P.ny + lpc - 1) / lpc;
+    k_pass1<T, S, M><<<(unsigned)(bpi * P.B), 128, 0, s>>>(P, U, out, n, t.p1_R);
+    return cudaGetLastError();
+}
+
+#define P1_SHAPES_F32(X) X(float, 8, 8) X(float, 8, 16) X(float, 16, 4) X(float, 16, 8) X(float, 16, 16) \
+    X(float, 32, 2) X(float, 32, 4) X(float, 32, 8) X(float, 32, 16)
+#define P1_SHAPES_F64(X) X(double, 16, 2) X(double, 16, 4) X(double, 16, 8) X(double, 32, 2) X(double, 32, 4) \
+    X(double, 32, 8) X(double, 32, 16)
+
+// Lets the staged kernels use up to kP1SmemLimit bytes of dynamic shared
+// memory (once per device, before launches or captures).
+cudaError_t init_pass1()
+{
+    cudaError_t e = cudaSuccess;
+#define P1_ATTR(T_, S_, M_)                                                                                  \
+    if (e == cudaSuccess)                                                                                    \
+        e = cudaFuncSetAttribute(k_pass1s<T_, S_, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
+                                 (int)kP1SmemLimit);
+    P1_SHAPES_F32(P1_ATTR)
+    P1_SHAPES_F64(P1_ATTR)
+#undef P1_ATTR
+    return e;
 }
 
 template <typename T>
-cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, cudaStream_t s)
+cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s)
 {
-    const P1Shape sh = p1_shape(P.nr, sizeof(T));
-    if (P.nr > 512) return cudaErrorInvalidValue;
+    if (!tile_valid(t, P.nr, P.nv, P.ny, sizeof(T))) return cudaErrorInvalidValue;
+    const int S = t.p1_S, M = t.p1_M;
+#define P1_CASE(T_, S_, M_) \
+    if (S == S_ && M == M_) return p1_launch<T, S_, M_>(P, U, out, n, t, s);
     if constexpr (sizeof(T) == 4) {
-        if (sh.S == 8 && sh.M == 8) return p1_launch_v<T, 8, 8>(P, U, out, n, sh, s);
-        if (sh.S == 16 && sh.M == 8) return p1_launch_v<T, 16, 8>(P, U, out, n, sh, s);
-        if (sh.S == 32 && sh.M == 8) return p1_launch_v<T, 32, 8>(P, U, out, n, sh, s);
-        if (sh.S == 32 && sh.M == 4) return p1_launch_v<T, 32, 4>(P, U, out, n, sh, s);
-        return p1_launch<T, 32, 16, true, false>(P, U, out, n, sh.R, s);
+        P1_SHAPES_F32(P1_CASE)
     } else {
-        if (sh.S == 16 && sh.M == 2) return p1_launch<T, 16, 2, true, false>(P, U, out, n, sh.R, s);
-        if (sh.S == 16 && sh.M == 4) return p1_launch<T, 16, 4, true, false>(P, U, out, n, sh.R, s);
-        if (sh.S == 32 && sh.M == 4) return p1_launch<T, 32, 4, true, false>(P, U, out, n, sh.R, s);
-        if (sh.S == 32 && sh.M == 8) return p1_launch<T, 32, 8, true, false>(P, U, out, n, sh.R, s);
-        return p1_launch<T, 32, 16, true, false>(P, U, out, n, sh.R, s);
+        P1_SHAPES_F64(P1_CASE)
     }
+#undef P1_CASE
+    return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_pass1<float>(const March<float>&, const float*, float*, int, cudaStream_t);
-template cudaError_t launch_pass1<double>(const March<double>&, const double*, double*, int, cudaStream_t);
+template cudaError_t launch_pass1<float>(const March<float>&, const float*, float*, int, const Tile&,
+                                         cudaStream_t);
+template cudaError_t launch_pass1<double>(const March<double>&, const double*, double*, int, const Tile&,
+                                          cudaStream_t);
 
 }  // namespace hjm

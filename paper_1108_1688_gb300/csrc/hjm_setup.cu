@@ -265,6 +265,175 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
     }
 }
 
+// Rows (sub, main, super) of I - theta dt A_v at v node k (Section 5.1, the
+// one-sided first-order face rows of Section 7.3) and of I - theta dt A_y at
+// y node j for the v node v (gamma = 0).
+__device__ void v_row(const InstParams& p, const double* axv, int nv, double w, int k, double& sub,
+                      double& mainv, double& sup)
+{
+    const double ih = nv - 1, ih2 = ih * ih;
+    const double v = axv[k], J = axv[nv + k], J2 = axv[2 * nv + k];
+    const double zvv = 0.5 * p.eps * p.eps * v, muv = p.theta * (1.0 - v);
+    double lo = 0.0, di = 0.0, up = 0.0;
+    if (k > 0 && k < nv - 1) {
+        const double g2 = zvv / (J * J), g5 = muv / J - zvv * J2 / (J * J * J);
+        lo = g2 * ih2 - 0.5 * g5 * ih;
+        di = -2.0 * g2 * ih2;
+        up = g2 * ih2 + 0.5 * g5 * ih;
+    } else if (k == 0) {
+        di = -muv / J * ih;
+        up = muv / J * ih;
+    } else {
+        lo = -muv / J * ih;
+        di = muv / J * ih;
+    }
+    sub = -w * lo;
+    mainv = 1.0 - w * di;
+    sup = -w * up;
+}
+
+__device__ void y_row(const InstParams& p, const double* axy, int ny, double w, double v, int j, double& sub,
+                      double& mainv, double& sup)
+{
+    const double ih = ny - 1;
+    const double g6 = (p.lambda * p.lambda * v - 2.0 * p.kappa * axy[j]) / axy[ny + j];
+    double lo = 0.0, di = 0.0, up = 0.0;
+    if (j > 0 && j < ny - 1) {
+        lo = -0.5 * g6 * ih;
+        up = 0.5 * g6 * ih;
+    } else if (j == 0) {
+        di = -g6 * ih;
+        up = g6 * ih;
+    } else {
+        lo = -g6 * ih;
+        di = g6 * ih;
+    }
+    sub = -w * lo;
+    mainv = 1.0 - w * di;
+    sup = -w * up;
+}
+
+// Factors of the v systems (axis 0: one per instrument) or y systems (axis 1:
+// one per instrument and v node, gamma = 0 only) split into P chunks solved
+// independently, one warp each, and joined through a small reduced system
+// (layout in part_sys_size). For chunk p with rows [s, s + L):
+//   the LU of the chunk's rows without their outside couplings;
+//   V = A_p^{-1} (sub_s e_0) and W = A_p^{-1} (sup_{s+L-1} e_{L-1}), so
+//   that x = A_p^{-1} d - x_{s-1} V - x_{s+L} W on the chunk;
+//   evaluated at the chunks' end rows this gives the reduced system in
+//   z = (last of chunk 0, first of chunk 1, last of chunk 1, ..., first of
+//   chunk P-1), whose inverse yields, per chunk, the weights of the reduced
+//   right-hand sides (the chunks' end values of A_p^{-1} d) in x_{s-1} and
+//   x_{s+L}.
+// One warp per system: lanes p < P factor the chunks, then the lanes run
+// Gauss-Jordan with partial pivoting on [M | I] in shared memory. FP64
+// throughout, stored in the march type.
+template <typename T>
+__global__ void __launch_bounds__(32) k_split(GroupTables g, int axis, int P)
+{
+    const int lane = threadIdx.x;
+    const int nv = g.nv, ny = g.ny;
+    const int b = axis == 0 ? blockIdx.x : blockIdx.x / nv;
+    const int k = axis == 0 ? 0 : blockIdx.x % nv;
+    const InstParams p = g.params[b];
+    if (axis == 1 && p.gamma != 0.0) return;
+    const double w = p.theta_adi * g.derived[b].dt;
+    const double* axv = g.axv + (size_t)b * 3 * nv;
+    const double* axy = g.axy + (size_t)b * 3 * ny;
+    const int n = axis == 0 ? nv : ny;
+    T* out = axis == 0 ? (T*)g.vp + (size_t)b * part_sys_size(nv, kMaxSplit)
+                       : (T*)g.yp + ((size_t)b * nv + k) * part_sys_size(ny, kMaxSplit);
+    const int K = 2 * (P - 1);
+    __shared__ double im[kMaxSplit][kMaxChunk], cp[kMaxSplit][kMaxChunk], lo[kMaxSplit][kMaxChunk],
+        vv[kMaxSplit][kMaxChunk];
+    __shared__ double Vend[2 * kMaxSplit], Wend[2 * kMaxSplit];
+    __shared__ double A[2 * (kMaxSplit - 1)][4 * (kMaxSplit - 1)];
+    __shared__ int piv_row;
+    if (lane < P) {
+        const int c = lane;
+        int s, L;
+        part_chunk(n, P, c, s, L);
+        for (int m = 0; m < L; ++m) {
+            double l, d, u;
+            if (axis == 0)
+                v_row(p, axv, nv, w, s + m, l, d, u);
+            else
+                y_row(p, axy, ny, w, axv[k], s + m, l, d, u);
+            lo[c][m] = l;
+            const double pv = m > 0 ? d - l * cp[c][m - 1] : d;
+            im[c][m] = 1.0 / pv;
+            cp[c][m] = u * im[c][m];
+            out[2 * (s + m)] = (T)(m > 0 ? l : 0.0);
+            out[2 * (s + m) + 1] = (T)im[c][m];
+            out[4 * n + 2 * P * K + s + m] = (T)cp[c][m];
+        }
+        // V: forward with right-hand side sub_s e_0, then back substitution.
+        vv[c][0] = lo[c][0] * im[c][0];
+        for (int m = 1; m < L; ++m) vv[c][m] = -lo[c][m] * vv[c][m - 1] * im[c][m];
+        for (int m = L - 2; m >= 0; --m) vv[c][m] -= cp[c][m] * vv[c][m + 1];
+        // W: right-hand side sup_{s+L-1} e_{L-1}, whose forward value is c'.
+        double wn = cp[c][L - 1];
+        Wend[2 * c + 1] = wn;
+        out[2 * n + 2 * (s + L - 1) + 1] = (T)wn;
+        for (int m = L - 2; m >= 0; --m) {
+            wn = -cp[c][m] * wn;
+            out[2 * n + 2 * (s + m) + 1] = (T)wn;
+        }
+        Wend[2 * c] = wn;
+        for (int m = 0; m < L; ++m) out[2 * n + 2 * (s + m)] = (T)vv[c][m];
+        Vend[2 * c] = vv[c][0];
+        Vend[2 * c + 1] = vv[c][L - 1];
+    }
+    __syncwarp();
+    if (P == 1) return;
+    // Reduced system M z = r: row 2q is chunk q's last row, row 2q + 1 is
+    // chunk q+1's first row (q = 0..P-2). Lane j owns column j of [M | I].
+    for (int i = 0; i < K; ++i)
+        if (lane < 2 * K) A[i][lane] = (lane == i || lane == K + i) ? 1.0 : 0.0;
+    __syncwarp();
+    if (lane == 0)
+        for (int q = 0; q + 1 < P; ++q) {
+            if (q >= 1) A[2 * q][2 * q - 2] = Vend[2 * q + 1];
+            A[2 * q][2 * q + 1] = Wend[2 * q + 1];
+            A[2 * q + 1][2 * q] = Vend[2 * (q + 1)];
+            if (q + 2 < P) A[2 * q + 1][2 * q + 3] = Wend[2 * (q + 1)];
+        }
+    __syncwarp();
+    for (int c = 0; c < K; ++c) {
+        if (lane == 0) {
+            int r = c;
+            for (int i = c + 1; i < K; ++i)
+                if (fabs(A[i][c]) > fabs(A[r][c])) r = i;
+            piv_row = r;
+        }
+        __syncwarp();
+        const int r = piv_row;
+        if (r != c && lane < 2 * K) {
+            const double t = A[c][lane];
+            A[c][lane] = A[r][lane];
+            A[r][lane] = t;
+        }
+        __syncwarp();
+        const double ip = 1.0 / A[c][c];
+        __syncwarp();
+        if (lane < 2 * K) A[c][lane] *= ip;
+        __syncwarp();
+        for (int i = 0; i < K; ++i) {
+            const double f = A[i][c];
+            __syncwarp();
+            if (i != c && lane < 2 * K) A[i][lane] -= f * A[c][lane];
+            __syncwarp();
+        }
+    }
+    // Chunk c needs x_{s-1} = z_{2(c-1)} (c >= 1) and x_{s+L} = z_{2c+1}
+    // (c <= P-2).
+    for (int idx = lane; idx < P * K; idx += 32) {
+        const int c = idx / K, q = idx % K;
+        out[4 * n + 2 * idx] = (T)(c >= 1 ? A[2 * (c - 1)][K + q] : 0.0);
+        out[4 * n + 2 * idx + 1] = (T)(c + 1 < P ? A[2 * c + 1][K + q] : 0.0);
+    }
+}
+
 // Dirichlet data at t^{n+1} on r = r_min (face 0) and r = r_max (face 1):
 // the exact bond p(t,S) = P(0,S)/P(0,t) exp(-G(S-t) x - G(S-t)^2 y / 2),
 // x = r - f(0,t) (Section 3.1), for a bond, and the caplet's intrinsic
@@ -451,6 +620,8 @@ size_t tables_bytes(int nr, int nv, int ny, int nsteps, int B, size_t elem)
     s += align_up((size_t)B * nsteps * 2 * ny * elem);
     s += align_up((size_t)B * 3 * nv * elem);
     s += align_up((size_t)B * nv * 3 * ny * elem);
+    s += align_up((size_t)B * part_sys_size(nv, kMaxSplit) * elem);
+    s += align_up((size_t)B * nv * part_sys_size(ny, kMaxSplit) * elem);
     s += align_up((size_t)B * FL_N * sizeof(int));
     s += align_up((size_t)B * nsteps * sizeof(float));
     s += align_up((size_t)B * 3 * (nr + nv + ny) * sizeof(double));
@@ -475,6 +646,8 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
     g.dir = take(B * g.nsteps * 2 * g.ny * elem);
     g.vf = take(B * 3 * g.nv * elem);
     g.yf = take(B * g.nv * 3 * g.ny * elem);
+    g.vp = take(B * part_sys_size(g.nv, kMaxSplit) * elem);
+    g.yp = take(B * g.nv * part_sys_size(g.ny, kMaxSplit) * elem);
     g.fl = (int*)take(B * FL_N * sizeof(int));
     g.acc = (float*)take(B * g.nsteps * sizeof(float));
     double* ax = (double*)take(B * 3 * (g.nr + g.nv + g.ny) * sizeof(double));
@@ -487,12 +660,17 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
 cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s)
 {
     const dim3 faces(g.nsteps, g.B);
+    if (g.p2P < 1 || g.p2P > kMaxSplit || g.p3P < 1 || g.p3P > kMaxSplit) return cudaErrorInvalidValue;
     if (elem == sizeof(float)) {
         k_setup<float><<<g.B, 256, 0, s>>>(g);
         k_faces<float><<<faces, 128, 0, s>>>(g);
+        if (g.p2P > 1) k_split<float><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
+        if (g.p3P > 1) k_split<float><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
     } else {
         k_setup<double><<<g.B, 256, 0, s>>>(g);
         k_faces<double><<<faces, 128, 0, s>>>(g);
+        if (g.p2P > 1) k_split<double><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
+        if (g.p3P > 1) k_split<double><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
     }
     return cudaGetLastError();
 }
@@ -538,6 +716,10 @@ March<T> march_args(const GroupTables& g)
     P.yf = (const T*)g.yf;
     P.fl = g.fl;
     P.acc = g.acc;
+    P.vp = (const T*)g.vp;
+    P.yp = (const T*)g.yp;
+    P.p2P = g.p2P;
+    P.p3P = g.p3P;
     return P;
 }
 

@@ -65,6 +65,11 @@ class hjm_trace(C.Structure):
     _fields_ = [("launches", C.c_longlong * HJM_TRACE_KINDS), ("total_ms", C.c_double * HJM_TRACE_KINDS)]
 
 
+class hjm_tile(C.Structure):
+    _fields_ = [("p1_lanes", C.c_int), ("p1_nodes", C.c_int), ("p1_lines", C.c_int), ("p2_warps", C.c_int),
+                ("p3_warps", C.c_int), ("p1_staged", C.c_int), ("p1_planes", C.c_int)]
+
+
 class hjm_surrogate_cfg(C.Structure):
     _fields_ = [("n_train", C.c_size_t), ("hidden", C.c_int), ("depth", C.c_int), ("epochs", C.c_int),
                 ("batch", C.c_int), ("lr", C.c_float), ("seed", C.c_uint64), ("box_lo", C.c_double * 9),
@@ -110,6 +115,9 @@ def _load():
         "hjm_mlp_gemm": ([C.c_int, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, C.c_int, vp, C.c_int, vp], st),
         "hjm_trace_enable": ([st], st),
         "hjm_trace_read": ([P(hjm_trace), st], st),
+        "hjm_tile_get": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
+        "hjm_tile_set": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
+        "hjm_autotune": ([P(hjm_batch_item), C.c_size_t, st, C.c_int, vp], st),
         "hjm_status_string": ([st], C.c_char_p),
         "hjm_last_error": ([], C.c_char_p),
     }
@@ -126,7 +134,7 @@ EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch
             "hjm_surrogate_fit", "hjm_surrogate_infer", "hjm_surrogate_forward", "hjm_surrogate_loss_grad",
             "hjm_surrogate_get_params", "hjm_surrogate_set_params", "hjm_surrogate_error_table",
             "hjm_surrogate_save", "hjm_surrogate_load", "hjm_surrogate_destroy", "hjm_mlp_gemm",
-            "hjm_trace_enable", "hjm_trace_read",
+            "hjm_trace_enable", "hjm_trace_read", "hjm_tile_get", "hjm_tile_set", "hjm_autotune",
             "hjm_status_string", "hjm_last_error")
 
 
@@ -267,6 +275,28 @@ def hjm_price_static(item, precision, out, stream=None):
     it = item if isinstance(item, hjm_batch_item) else batch_item(item)
     _check(lib.hjm_price_static(C.byref(it), PRECISIONS[precision], _ptr(out), _stream(stream)))
     return out
+
+
+def hjm_tile_get(n_r, n_v, n_y, precision=HJM_FP32):
+    """Launch shape in use for a grid shape: (p1_lanes, p1_nodes, p1_lines, p2_warps, p3_warps,
+    p1_staged, p1_planes)."""
+    t = hjm_tile()
+    _check(lib.hjm_tile_get(int(n_r), int(n_v), int(n_y), PRECISIONS[precision], C.byref(t)))
+    return (t.p1_lanes, t.p1_nodes, t.p1_lines, t.p2_warps, t.p3_warps, t.p1_staged, t.p1_planes)
+
+
+def hjm_tile_set(n_r, n_v, n_y, precision=HJM_FP32, tile=None):
+    """Fix the launch shape of a grid shape (a 7-tuple, or 5 values with p1_staged = 0), or
+    restore the default (None)."""
+    vals = [int(x) for x in tile] + [0] * (7 - len(tile)) if tile is not None else None
+    ptr = C.byref(hjm_tile(*vals)) if tile is not None else None
+    _check(lib.hjm_tile_set(int(n_r), int(n_v), int(n_y), PRECISIONS[precision], ptr))
+
+
+def hjm_autotune(items, precision=HJM_FP32, steps=8, stream=None):
+    """Time every candidate launch shape on the items' grid shapes and keep the fastest."""
+    arr = items if isinstance(items, C.Array) else make_items(items)
+    _check(lib.hjm_autotune(arr, len(arr), PRECISIONS[precision], int(steps), _stream(stream)))
 
 
 def hjm_trace_enable(on):
