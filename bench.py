@@ -24,6 +24,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -257,6 +258,102 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_surrogate(args):
+    """--workload config5: the pricing surrogate. Trains on PDE labels (FP32
+    march on the label grid, untimed), then times hjm_surrogate_infer on a
+    batch of 65,536 fresh rows with 5% out of the training box (network
+    answers gated by the held-out error table, every other row priced by the
+    march); value = caplet forward premia per second end to end. The
+    answered rows are then judged against the march (untimed)."""
+    import numpy as np
+    import torch
+    from paper_1108_1688_gb300 import _build
+    _build.build()
+    from paper_1108_1688_gb300 import hjm
+    from paper_1108_1688_gb300 import workloads as W
+    lg = [int(v) for v in args.label_grid.split("x")]
+    label = W.surrogate_label_grid(*lg)
+    n_rows = 65536
+    cfg = hjm.surrogate_cfg(args.labels, args.epochs, 1024, 3e-3, W.SEED_BASE + 5, W.SURROGATE_BOX_LO,
+                            W.SURROGATE_BOX_HI, label, None)
+    t0 = time.perf_counter()
+    h = hjm.hjm_surrogate_train(cfg)
+    train_s = time.perf_counter() - t0
+    table = hjm.hjm_surrogate_error_table(h)
+    x = W.surrogate_draws(n_rows, seed=W.SEED_BASE + 51, out_of_box=0.05)
+    stream = torch.cuda.current_stream()
+    xd = torch.tensor(x).cuda()
+    out = torch.empty(n_rows, dtype=torch.float64, device="cuda")
+    used = torch.zeros(n_rows, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        hjm.hjm_surrogate_infer(h, xd, out, used, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            hjm.hjm_surrogate_infer(h, xd, out, used, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    # end to end: rows from pinned host memory, prices back to the host
+    xh = torch.tensor(x).pin_memory()
+    outh = torch.empty(n_rows, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        xd.copy_(xh, non_blocking=True)
+        hjm.hjm_surrogate_infer(h, xd, out, used, stream=stream)
+        outh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    # the network alone
+    y = torch.empty(n_rows, dtype=torch.float32, device="cuda")
+    hjm.hjm_surrogate_forward(h, xd, y, stream=stream)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(20):
+        hjm.hjm_surrogate_forward(h, xd, y, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    net_ms = ev0.elapsed_time(ev1) / 20
+    # judge every row with the march on the label grid
+    got = out.cpu().numpy()
+    u = used.cpu().numpy().astype(bool)
+    items = [W.surrogate_item(r, label) for r in x]
+    C = np.empty(n_rows)
+    for a in range(0, n_rows, 4096):
+        C[a:a + 4096] = hjm.hjm_price_batch(items[a:a + 4096], "fp32")
+    want = np.array([c * math.exp(math.log1p(float(r[8]) * float(r[6])) / float(r[6]) * float(r[5]))
+                     for c, r in zip(C, x)])
+    err = np.abs(got - want)
+    ans = ~u
+    line = {
+        "metric": METRIC, "value": n_rows * args.steps / (ms * 1e-3), "unit": "caplet prices/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f32",
+        "data": "synthetic",
+        "config": {"workload": "surrogate 9->4x256 SiLU->1, %d PDE labels on %s (%d epochs), inference batch "
+                               "%d rows with 5%% out of the box, PDE fallback" % (args.labels, args.label_grid,
+                                                                                args.epochs, n_rows),
+                   "l2": "batch of %d rows (2.4 MB) is L2-resident; no flush (the fallback march dominates)"
+                         % n_rows},
+        "e2e": {"value": n_rows * args.steps / e2e_s, "unit": "caplet prices/s",
+                "h2d_bytes_per_step": n_rows * 9 * 4, "d2h_bytes_per_step": n_rows * 8},
+        "gpu_launches": None,
+        "clocks": clk.summary(),
+        "surrogate": {"train_s": round(train_s, 1), "coverage": round(float(ans.mean()), 4),
+                      "max_err_answered": float(err[ans].max()) if ans.any() else None,
+                      "median_err_answered": float(np.median(err[ans])) if ans.any() else None,
+                      "max_err_fallback": float(err[u].max()) if u.any() else None,
+                      "bins_under_gate": int((table <= 5e-5).sum()), "bins": int(table.size),
+                      "network_ms_per_batch": round(net_ms, 4),
+                      "network_rows_per_s": n_rows / (net_ms * 1e-3)},
+    }
+    hjm.hjm_surrogate_destroy(h)
+    print(json.dumps(line))
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -403,16 +500,22 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2", choices=["config1", "config2", "config3", "config4"])
+    ap.add_argument("--workload", default="config2",
+                    choices=["config1", "config2", "config3", "config4", "config5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shapes")
     ap.add_argument("--instruments", type=int, default=None, help="config2 only: fewer caplets (profiling)")
     ap.add_argument("--march-steps", type=int, default=None, help="config2 only: fewer Douglas steps (profiling)")
+    ap.add_argument("--labels", type=int, default=1 << 20, help="config5: PDE labels")
+    ap.add_argument("--epochs", type=int, default=120, help="config5: training epochs")
+    ap.add_argument("--label-grid", default="96x48x48x192", help="config5: label march n_r x n_y x n_v x steps")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "config5":
+        run_surrogate(args)
     else:
         run_ours(args)
 

@@ -198,12 +198,12 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * segment per CTA (1..64). p2_warps / p3_warps: warps sharing each v / y
  * line of passes 2 and 3: 1 (one thread per line), or 2, 4, 8 when the line
  * has at least 2 nodes per warp and at most 32 (pass 3 splits y lines only
- * in groups where every instrument has gamma = 0). p1_staged = 1 makes
- * pass 1 copy the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v
- * nodes into shared memory and march over p1_planes (1..4096) y nodes per
- * CTA (needs n_r * element size a multiple of 16 and the ring within the
- * shared memory of a CTA); p1_staged = 0 reads the rows from global memory
- * (p1_planes = 0). A shape changes speed and the rounding of the line
+ * in groups where every instrument has gamma = 0). p1_staged selects how
+ * pass 1 gets its five stencil rows: 0 straight from global memory, 1 a CTA
+ * copies the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v nodes
+ * into a shared-memory ring and marches over p1_planes (1..4096) y nodes
+ * (p1_planes = 0 unless staged; staged needs n_r * element size a multiple
+ * of 16 and the ring within the shared memory of a CTA). A shape changes speed and the rounding of the line
  * solves, nothing else.
  * tile_cfg in hjm_price_info packs p1_lanes | p1_nodes << 8 | p1_lines << 14
  * | p2_warps << 21 | p3_warps << 25 | p1_staged << 29. */

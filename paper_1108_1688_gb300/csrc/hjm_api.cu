@@ -85,6 +85,8 @@ static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const 
     if (c.kind == HJM_CURVE_NELSON_SIEGEL && !(c.tau > 0.0))
         return fail(HJM_EINVAL, "Nelson-Siegel tau must be > 0");
     if (g.n_r < 5 || g.n_v < 5 || g.n_y < 5) return fail(HJM_EINVAL, "each axis needs >= 5 nodes");
+    if ((long long)g.n_r * g.n_v * g.n_y > 0x7fffffffLL)
+        return fail(HJM_ERANGE, "n_r * n_v * n_y above 2^31 - 1 nodes");  // 32-bit offsets in the kernels
     if (g.n_steps < 1) return fail(HJM_EINVAL, "n_steps must be >= 1");
     if (!(g.r_max > g.r_min) || !(g.y_max > 0.0) || !(g.v_max > 0.0))
         return fail(HJM_EINVAL, "empty domain");

@@ -48,12 +48,15 @@ __device__ __forceinline__ void cp_async_wait16()
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Loads nodes e0 .. e0+M-1 of a row (zero past n_r); vec: the row start is
+// 16-byte aligned and n_r a multiple of the vector width (checked once per
+// launch), so whole chunks use 16-byte loads.
 template <typename T, int M>
-__device__ __forceinline__ void p1_load(const T* __restrict__ row, int e0, int nr, T (&u)[M])
+__device__ __forceinline__ void p1_load(const T* __restrict__ row, int e0, int nr, T (&u)[M], bool vec = false)
 {
     constexpr int V = 16 / sizeof(T);
     if constexpr (M % V == 0) {
-        if (e0 + M <= nr && (reinterpret_cast<uintptr_t>(row + e0) & 15) == 0) {
+        if (e0 + M <= nr && (vec || (reinterpret_cast<uintptr_t>(row + e0) & 15) == 0)) {
 #pragma unroll
             for (int q = 0; q < M / V; ++q) {
                 if constexpr (sizeof(T) == 4) {
@@ -76,11 +79,11 @@ __device__ __forceinline__ void p1_load(const T* __restrict__ row, int e0, int n
 }
 
 template <typename T, int M>
-__device__ __forceinline__ void p1_store(T* __restrict__ row, int e0, int nr, const T (&u)[M])
+__device__ __forceinline__ void p1_store(T* __restrict__ row, int e0, int nr, const T (&u)[M], bool vec = false)
 {
     constexpr int V = 16 / sizeof(T);
     if constexpr (M % V == 0) {
-        if (e0 + M <= nr && (reinterpret_cast<uintptr_t>(row + e0) & 15) == 0) {
+        if (e0 + M <= nr && (vec || (reinterpret_cast<uintptr_t>(row + e0) & 15) == 0)) {
 #pragma unroll
             for (int q = 0; q < M / V; ++q) {
                 if constexpr (sizeof(T) == 4)
@@ -175,6 +178,37 @@ __device__ __forceinline__ void seg_partition_solve(T (&a)[M], T (&b)[M], T (&c)
     d[0] = xS;
     d[M - 1] = xE;
 }
+
+// Arithmetic on pairs of values: for FP32 the paired FP32 instructions of
+// sm_100-class GPUs (one instruction for both lanes of a float2), for FP64
+// two scalar operations. Every operation rounds each component exactly as
+// its scalar counterpart (a - b is fma(b, -1, a)).
+template <typename T>
+struct Two;
+template <>
+struct Two<float> {
+    using V = float2;
+    static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+    static __device__ __forceinline__ V splat(float a) { return make_float2(a, a); }
+    static __device__ __forceinline__ float x(V a) { return a.x; }
+    static __device__ __forceinline__ float y(V a) { return a.y; }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+    static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+    static __device__ __forceinline__ V sub(V a, V b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+};
+template <>
+struct Two<double> {
+    using V = double2;
+    static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+    static __device__ __forceinline__ V splat(double a) { return make_double2(a, a); }
+    static __device__ __forceinline__ double x(V a) { return a.x; }
+    static __device__ __forceinline__ double y(V a) { return a.y; }
+    static __device__ __forceinline__ V fma(V a, V b, V c) { return make_double2(::fma(a.x, b.x, c.x), ::fma(a.y, b.y, c.y)); }
+    static __device__ __forceinline__ V mul(V a, V b) { return make_double2(a.x * b.x, a.y * b.y); }
+    static __device__ __forceinline__ V add(V a, V b) { return make_double2(a.x + b.x, a.y + b.y); }
+    static __device__ __forceinline__ V sub(V a, V b) { return make_double2(a.x - b.x, a.y - b.y); }
+};
 
 // Shared-memory layout of the r tables: tsm[q][sl][MP], lane sl's M nodes
 // contiguous, padded to MP so that 16-byte vector reads by consecutive lanes
@@ -291,7 +325,20 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const T wd_next = __shfl_down_sync(0xffffffffu, ub[0] - ua[0], 1, S);
 
 #define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
-    // 1. right-hand side, every node as if interior in r.
+    // 1. right-hand side, every node as if interior in r. Nodes are taken
+    // in pairs (m, m+1) so the FP32 march runs on the paired FP32 pipe (two
+    // lanes of arithmetic per instruction); sh[h] = (U_{2h-1}, U_{2h}) and
+    // tw[h] = (wd_{2h-1}, wd_{2h}) are the pairs shifted by one node.
+    using PV = typename Two<T>::V;
+    constexpr int H = M / 2;
+    // rolling shifted pairs (current and next), built just in time
+    PV shc = Two<T>::mk(uc_prev, uc[0]);
+    PV wdc = Two<T>::sub(Two<T>::mk(ub[0], ub[1]), Two<T>::mk(ua[0], ua[1]));
+    PV twc = Two<T>::mk(wd_prev, Two<T>::x(wdc));
+    const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v), aFy2 = Two<T>::splat(aFy);
+    const PV vq2 = Two<T>::splat(vq), cA2 = Two<T>::splat(cA), cB2 = Two<T>::splat(cB);
+    const PV vy2 = Two<T>::splat(vy), kyy2 = Two<T>::splat(kyy), yA2 = Two<T>::splat(yA), yB2 = Two<T>::splat(yB);
+    const PV dt2 = Two<T>::splat(dt);
 #pragma unroll
     for (int m0 = 0; m0 < M; m0 += W) {
         T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W], tC3[W], tCY[W];
@@ -303,21 +350,39 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
         TABV(RT_C3, m0, tC3);
         TABV(RT_CY, m0, tCY);
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const int m = m0 + q;
-            const T u = uc[m];
-            const T um = m > 0 ? uc[m - 1] : uc_prev;
-            const T up = m < M - 1 ? uc[m + 1] : uc_next;
-            const T wp = m < M - 1 ? ub[m + 1] - ua[m + 1] : wd_next;
-            const T wm = m > 0 ? ub[m - 1] - ua[m - 1] : wd_prev;
-            const T g1 = tC1[q] * v;                               // zeta_rr / (J^2 h^2)
-            const T g4F = aFy * tIJ[q] + (tC4B[q] - v * tC4V[q]);  // g4 / (2h) at t^n
-            T f = g1 * ((up - u) - (u - um)) + g4F * (up - um) - tR[q] * u;
-            f += tC3[q] * vq * (wp - wm);
-            f += cA * (ua[m] - u) + cB * (ub[m] - u);
-            const T g6 = tCY[q] * vy + kyy;
-            f += g6 * (yA * (ya[m] - u) + yB * (yb[m] - u));
-            d[m] = dt * f;
+        for (int q = 0; q < W; q += 2) {
+            const int m = m0 + q, h = m / 2;
+            PV shn, twn, wdn = wdc;
+            if (h + 1 < H) {
+                shn = Two<T>::mk(uc[m + 1], uc[m + 2]);
+                wdn = Two<T>::sub(Two<T>::mk(ub[m + 2], ub[m + 3]), Two<T>::mk(ua[m + 2], ua[m + 3]));
+                twn = Two<T>::mk(Two<T>::y(wdc), Two<T>::x(wdn));
+            } else {
+                shn = Two<T>::mk(uc[M - 1], uc_next);
+                twn = Two<T>::mk(Two<T>::y(wdc), wd_next);
+            }
+            const PV u = Two<T>::mk(uc[m], uc[m + 1]);
+            const PV Dp = Two<T>::sub(shn, u);  // U_{m+1} - U_m
+            const PV Dm = Two<T>::sub(u, shc);  // U_m - U_{m-1}
+            const PV g1 = Two<T>::mul(Two<T>::mk(tC1[q], tC1[q + 1]), v2);  // zeta_rr / (J^2 h^2)
+            const PV g4F = Two<T>::fma(aFy2, Two<T>::mk(tIJ[q], tIJ[q + 1]),
+                                       Two<T>::fma(nv2, Two<T>::mk(tC4V[q], tC4V[q + 1]),
+                                                   Two<T>::mk(tC4B[q], tC4B[q + 1])));  // g4 / (2h) at t^n
+            PV f = Two<T>::fma(g1, Two<T>::sub(Dp, Dm), Two<T>::mul(g4F, Two<T>::add(Dp, Dm)));
+            f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
+            f = Two<T>::fma(Two<T>::mul(Two<T>::mk(tC3[q], tC3[q + 1]), vq2), Two<T>::sub(twn, twc), f);
+            f = Two<T>::fma(cA2, Two<T>::sub(Two<T>::mk(ua[m], ua[m + 1]), u), f);
+            f = Two<T>::fma(cB2, Two<T>::sub(Two<T>::mk(ub[m], ub[m + 1]), u), f);
+            const PV g6 = Two<T>::fma(Two<T>::mk(tCY[q], tCY[q + 1]), vy2, kyy2);
+            const PV yy = Two<T>::fma(yA2, Two<T>::sub(Two<T>::mk(ya[m], ya[m + 1]), u),
+                                      Two<T>::mul(yB2, Two<T>::sub(Two<T>::mk(yb[m], yb[m + 1]), u)));
+            f = Two<T>::fma(g6, yy, f);
+            const PV r = Two<T>::mul(dt2, f);
+            d[m] = Two<T>::x(r);
+            d[m + 1] = Two<T>::y(r);
+            shc = shn;
+            twc = twn;
+            wdc = wdn;
         }
     }
     const T gLo = I.dir[j], gHi = I.dir[ny + j];
@@ -344,24 +409,36 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
         }
     }
 
-    // 2. rows of I - theta dt A_r(t^{n+1/2}).
+    // 2. rows of I - theta dt A_r(t^{n+1/2}), node pairs as above.
     T a[M], bb[M], c[M];
+    {
+        const PV aIy2 = Two<T>::splat(aIy), nw2 = Two<T>::splat(-w), w2 = Two<T>::splat(w);
+        const PV one2 = Two<T>::splat(T(1)), two2 = Two<T>::splat(T(2));
 #pragma unroll
-    for (int m0 = 0; m0 < M; m0 += W) {
-        T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W];
-        TABV(RT_R, m0, tR);
-        TABV(RT_IJ, m0, tIJ);
-        TABV(RT_C1, m0, tC1);
-        TABV(RT_C4V, m0, tC4V);
-        TABV(RT_C4B, m0, tC4B);
+        for (int m0 = 0; m0 < M; m0 += W) {
+            T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W];
+            TABV(RT_R, m0, tR);
+            TABV(RT_IJ, m0, tIJ);
+            TABV(RT_C1, m0, tC1);
+            TABV(RT_C4V, m0, tC4V);
+            TABV(RT_C4B, m0, tC4B);
 #pragma unroll
-        for (int q = 0; q < W; ++q) {
-            const int m = m0 + q;
-            const T g1 = tC1[q] * v;
-            const T g4I = aIy * tIJ[q] + (tC4B[q] - v * tC4V[q]);
-            a[m] = -w * (g1 - g4I);
-            bb[m] = T(1) + w * (T(2) * g1 + tR[q]);
-            c[m] = -w * (g1 + g4I);
+            for (int q = 0; q < W; q += 2) {
+                const int m = m0 + q;
+                const PV g1 = Two<T>::mul(Two<T>::mk(tC1[q], tC1[q + 1]), v2);
+                const PV g4I = Two<T>::fma(aIy2, Two<T>::mk(tIJ[q], tIJ[q + 1]),
+                                           Two<T>::fma(nv2, Two<T>::mk(tC4V[q], tC4V[q + 1]),
+                                                       Two<T>::mk(tC4B[q], tC4B[q + 1])));
+                const PV aa = Two<T>::mul(nw2, Two<T>::sub(g1, g4I));
+                const PV bv = Two<T>::fma(w2, Two<T>::fma(two2, g1, Two<T>::mk(tR[q], tR[q + 1])), one2);
+                const PV cc = Two<T>::mul(nw2, Two<T>::add(g1, g4I));
+                a[m] = Two<T>::x(aa);
+                a[m + 1] = Two<T>::y(aa);
+                bb[m] = Two<T>::x(bv);
+                bb[m + 1] = Two<T>::y(bv);
+                c[m] = Two<T>::x(cc);
+                c[m + 1] = Two<T>::y(cc);
+            }
         }
     }
 #undef TABV
@@ -440,21 +517,33 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
     p1_tables<T, S, M>(P, b, tsm);
     __syncthreads();
     const T* tl = tsm + sl * MP;
+    // 16-byte row access for every row when n_r is a multiple of the vector
+    // width and the fields are 16-byte aligned (uniform, checked once).
+    const bool vec = nr % (16 / (int)sizeof(T)) == 0 &&
+                     ((reinterpret_cast<uintptr_t>(Ub) | reinterpret_cast<uintptr_t>(Ob)) & 15) == 0;
+    // Lines of this segment: line0, line0 + G, ...; (k, j) advanced without
+    // divisions. Element offsets within an instrument fit in 32 bits.
+    const int line0 = cb * lpc + warp * R * G + seg;
+    int k = line0 % nv, j = line0 / nv;
     for (int it = 0; it < R; ++it) {
-        const int line = cb * lpc + (warp * R + it) * G + seg;
-        const bool valid = line < L;
-        const int lc = valid ? line : L - 1;  // keep addresses in bounds
-        const int k = lc % nv, j = lc / nv;
+        const bool valid = line0 + it * G < L;
+        const int kk = valid ? k : nv - 1, jj = valid ? j : ny - 1;  // keep addresses in bounds
         int ka, kb, ja, jb;
-        p1_neighbours(k, j, nv, ny, ka, kb, ja, jb);
+        p1_neighbours(kk, jj, nv, ny, ka, kb, ja, jb);
+        const int off = (jj * nv + kk) * nr;
         T uc[M], ua[M], ub[M], ya[M], yb[M], d[M];
-        p1_load<T, M>(Ub + ((long long)j * nv + k) * nr, e0, nr, uc);
-        p1_load<T, M>(Ub + ((long long)j * nv + ka) * nr, e0, nr, ua);
-        p1_load<T, M>(Ub + ((long long)j * nv + kb) * nr, e0, nr, ub);
-        p1_load<T, M>(Ub + ((long long)ja * nv + k) * nr, e0, nr, ya);
-        p1_load<T, M>(Ub + ((long long)jb * nv + k) * nr, e0, nr, yb);
-        p1_line<T, S, M>(I, tl, sl, k, j, uc, ua, ub, ya, yb, d);
-        if (valid) p1_store<T, M>(Ob + ((long long)j * nv + k) * nr, e0, nr, d);
+        p1_load<T, M>(Ub + off, e0, nr, uc, vec);
+        p1_load<T, M>(Ub + off + (ka - kk) * nr, e0, nr, ua, vec);
+        p1_load<T, M>(Ub + off + (kb - kk) * nr, e0, nr, ub, vec);
+        p1_load<T, M>(Ub + off + (ja - jj) * nv * nr, e0, nr, ya, vec);
+        p1_load<T, M>(Ub + off + (jb - jj) * nv * nr, e0, nr, yb, vec);
+        p1_line<T, S, M>(I, tl, sl, kk, jj, uc, ua, ub, ya, yb, d);
+        if (valid) p1_store<T, M>(Ob + off, e0, nr, d, vec);
+        k += G;
+        while (k >= nv) {
+            k -= nv;
+            ++j;
+        }
     }
 }
 
@@ -632,9 +721,9 @@ bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
     if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
     if (!split_valid(nv, t.p2_P) || !split_valid(ny, t.p3_P)) return false;
     if (t.p1_stage == 0) return t.p1_J == 0;
-    if (t.p1_stage != 1 || t.p1_J < 1 || t.p1_J > 4096) return false;
     // staged rows are copied in 16-byte pieces
     if ((nr * (int)elem) % 16 != 0) return false;
+    if (t.p1_stage != 1 || t.p1_J < 1 || t.p1_J > 4096) return false;
     return p1s_smem(nr, t.p1_S, t.p1_M, t.p1_R, elem) <= kP1SmemLimit;
 }
 
@@ -646,7 +735,8 @@ int pass1_chunk(int nr)
 template <typename T, int S, int M>
 static cudaError_t p1_launch(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s)
 {
-    if (t.p1_stage == 1 && (reinterpret_cast<uintptr_t>(U) & 15) == 0) {
+    const bool aligned = ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (t.p1_stage == 1 && aligned) {
         const int KB = 4 * (32 / S) * t.p1_R;
         const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
         const size_t smem = p1s_smem(P.nr, S, M, t.p1_R, sizeof(T));
@@ -673,7 +763,9 @@ cudaError_t init_pass1()
 #define P1_ATTR(T_, S_, M_)                                                                                  \
     if (e == cudaSuccess)                                                                                    \
         e = cudaFuncSetAttribute(k_pass1s<T_, S_, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
-                                 (int)kP1SmemLimit);
+                                 (int)kP1SmemLimit);                                                         \
+                                                         \
+
     P1_SHAPES_F32(P1_ATTR)
     P1_SHAPES_F64(P1_ATTR)
 #undef P1_ATTR
