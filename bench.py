@@ -56,7 +56,9 @@ def workload_items(name, instruments=None, march_steps=None):
         return (W.config2_draws(n, n_steps=ns),
                 "%d caplets 5y-into-6m ATM, NS curves, 128x64x64, %d steps" % (n, ns))
     if name == "config4":
-        return [W.config4()], "1 caplet 10y-into-6m ATM, flat 3%, 512x256x256, 1000 steps"
+        ns = march_steps or 1000
+        return ([W.with_grid(W.config4(), n_steps=ns)],
+                "1 caplet 10y-into-6m ATM, flat 3%%, 512x256x256, %d steps" % ns)
     if name == "config3":
         return W.config3_batch(), "256 caplets, expiries 1..10y, uneven grids 64..256 x n/2 x n/2, 2n steps"
     if name == "config1":
@@ -383,12 +385,24 @@ def run_ours(args):
     # Launch shapes: the library's autotuner times the candidate shapes of
     # every grid shape of the workload once (untimed, before the warm-up).
     tiles = {}
-    if not args.no_autotune:
+    if args.tile:
+        t = [int(v) for v in args.tile.split(",")]
+        for x in items:
+            g = x["grid"]
+            hjm.hjm_tile_set(g["n_r"], g["n_v"], g["n_y"], prec, t)
+    elif args.tiles and os.path.exists(args.tiles):
+        # launch shapes saved by an earlier run of the same workload
+        for key, t in json.load(open(args.tiles)).items():
+            nr_, ny_, nv_ = (int(v) for v in key.split("x"))
+            hjm.hjm_tile_set(nr_, nv_, ny_, prec, t)
+    elif not args.no_autotune:
         hjm.hjm_autotune(arr, prec, steps=8, stream=stream)
     for x in items:
         g = x["grid"]
         key = "%dx%dx%d" % (g["n_r"], g["n_y"], g["n_v"])
         tiles[key] = list(hjm.hjm_tile_get(g["n_r"], g["n_v"], g["n_y"], prec))
+    if args.tiles and not os.path.exists(args.tiles):
+        json.dump(tiles, open(args.tiles, "w"))
 
     for _ in range(args.warmup):
         step_dev()
@@ -474,7 +488,9 @@ def run_ours(args):
                    "precision": prec, "l2": "working set %.0f MB > L2 (no flush)" % (2 * total_points * elem / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "param_upload_bytes_per_step": n * item_bytes,
-                   "tiles": {"autotuned": not args.no_autotune, "r_x_y_x_v": tiles}},
+                   "tiles": {"autotuned": not (args.no_autotune or args.tile or args.tiles),
+                             "from_file": bool(args.tiles), "fixed": bool(args.tile),
+                             "r_x_y_x_v": tiles}},
         "e2e": {"value": world * ps * args.steps / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": n * item_bytes, "d2h_bytes_per_step": n * 8},
         "gpu_launches": launches_per_step * args.steps,
@@ -506,8 +522,14 @@ def main(argv=None):
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shapes")
+    ap.add_argument("--tile", default=None,
+                    help="launch shape for every grid shape of the workload: 7 integers "
+                         "p1_lanes,p1_nodes,p1_lines,p2_warps,p3_warps,p1_staged,p1_planes")
+    ap.add_argument("--tiles", default=None,
+                    help="JSON file of launch shapes: read if it exists (no autotuning), else written "
+                         "after autotuning (profiling runs replay the same shapes)")
     ap.add_argument("--instruments", type=int, default=None, help="config2 only: fewer caplets (profiling)")
-    ap.add_argument("--march-steps", type=int, default=None, help="config2 only: fewer Douglas steps (profiling)")
+    ap.add_argument("--march-steps", type=int, default=None, help="config2/4: fewer Douglas steps (profiling)")
     ap.add_argument("--labels", type=int, default=1 << 20, help="config5: PDE labels")
     ap.add_argument("--epochs", type=int, default=120, help="config5: training epochs")
     ap.add_argument("--label-grid", default="96x48x48x192", help="config5: label march n_r x n_y x n_v x steps")

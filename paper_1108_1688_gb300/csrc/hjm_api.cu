@@ -930,10 +930,10 @@ extern "C" hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_pr
         for (int phase = 0; phase < 2; ++phase) {
             if (phase == 1) {
                 cands.clear();
-                for (int Pw : {1, 2, 4, 8}) {
+                for (int Pw : {1, 2, 4, 8, 0, -1}) {  // split lines, then several lines per lane
                     Tile t = best;
-                    t.p2_P = split_valid(nv, Pw) ? Pw : 1;
-                    t.p3_P = split_valid(ny, Pw) && !g.gpos ? Pw : 1;
+                    t.p2_P = (Pw >= 1 ? split_valid(nv, Pw) : wide_valid(nv, nr, Pw, elem)) ? Pw : 1;
+                    t.p3_P = (Pw >= 1 ? split_valid(ny, Pw) : wide_valid(ny, nr, Pw, elem)) && !g.gpos ? Pw : 1;
                     cands.push_back(t);
                 }
                 best_ms[1] = best_ms[2] = 3.0e38f;

@@ -163,6 +163,11 @@ Tile default_tile(int nr, int nv, int ny, size_t elem);
 bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem);
 // Whether a line of n nodes can be split into Pw chunks (Pw = 1: unsplit).
 bool split_valid(int n, int Pw);
+// Wide line solves (several lines per lane): lines per lane selected by a
+// pass-2/3 tile value (0: 16-byte lanes, -1: 8-byte lanes, FP32), else 0;
+// and whether that choice fits a line of n nodes with n_r r nodes.
+int wide_lanes(int p, size_t elem);
+bool wide_valid(int n, int nr, int p, size_t elem);
 
 // The three Douglas passes of step n (in/out as documented in hjm.h).
 template <typename T>

@@ -369,6 +369,181 @@ bool split_valid(int n, int Pw)
                        split_smem(n, Pw, 1, sizeof(double)) <= 227 * 1024);
 }
 
+// ------------------------------------------------------- wide line solves
+
+// Copies of 8 or 16 bytes (VL consecutive r nodes) global -> shared.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_vec(void* smem_dst, const void* gmem_src)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    if constexpr (BYTES == 16)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+
+template <typename T, int VL>
+struct Lanes {
+    T v[VL];
+};
+
+template <typename T, int VL>
+__device__ __forceinline__ Lanes<T, VL> ld_lanes(const T* p)
+{
+    Lanes<T, VL> r;
+    if constexpr (VL * sizeof(T) == 16) {
+        if constexpr (sizeof(T) == 4) {
+            const float4 x = *reinterpret_cast<const float4*>(p);
+            r.v[0] = x.x;
+            r.v[1] = x.y;
+            r.v[2] = x.z;
+            r.v[3] = x.w;
+        } else {
+            const double2 x = *reinterpret_cast<const double2*>(p);
+            r.v[0] = x.x;
+            r.v[1] = x.y;
+        }
+    } else {
+        const float2 x = *reinterpret_cast<const float2*>(p);
+        r.v[0] = x.x;
+        r.v[1] = x.y;
+    }
+    return r;
+}
+
+template <typename T, int VL>
+__device__ __forceinline__ void st_lanes(T* p, const Lanes<T, VL>& r)
+{
+    if constexpr (VL * sizeof(T) == 16) {
+        if constexpr (sizeof(T) == 4)
+            *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+        else
+            *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
+    } else {
+        *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
+    }
+}
+
+// Passes 2 (AXIS 0) and 3 (AXIS 1, gamma = 0 groups) with VL consecutive
+// lines per lane (32 VL lines per warp): the lines are gathered with 8- or
+// 16-byte asynchronous copies (VL r nodes each, a warp reads 32 VL
+// contiguous nodes of a row) into shared memory and solved by Thomas with
+// the precomputed LU factors, the VL recurrences of a lane side by side.
+// Pass 3 stages U^n the same way. Needs n_r a multiple of VL and 8/16-byte
+// aligned fields (checked by the launcher).
+template <typename T, int VL, int AXIS>
+__global__ void __launch_bounds__(32) k_wide_lines(const March<T> P, const T* in, const T* Un, T* out,
+                                                   const int step_n)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x;
+    const int nr = P.nr, nv = P.nv, ny = P.ny;
+    const int n = AXIS == 0 ? nv : ny;
+    const int other = AXIS == 0 ? ny : nv;
+    T* col = reinterpret_cast<T*>(smem_raw);  // [n][32 VL] right-hand side, then d'
+    T* ucol = col + (size_t)n * 32 * VL;      // [n][32 VL] U^n (pass 3)
+    const int tiles = (nr + 32 * VL - 1) / (32 * VL);
+    const long long blk = blockIdx.x;
+    const int it = (int)(blk % tiles);
+    const int o = (int)((blk / tiles) % other);
+    const int b = (int)(blk / ((long long)tiles * other));
+    const int i0 = (it * 32 + lane) * VL;
+    if (i0 >= nr) return;
+    const long long stride = AXIS == 0 ? (long long)nr : (long long)nr * nv;
+    const long long base = (long long)b * P.N + (AXIS == 0 ? (long long)o * nv * nr : (long long)o * nr) + i0;
+    const T* src = in + base;
+    T* dst = out + base;
+    T* cl = col + lane * VL;
+    T* ul = ucol + lane * VL;
+    for (int kk = 0; kk < n; ++kk) cp_async_vec<VL * sizeof(T)>(cl + kk * 32 * VL, src + kk * stride);
+    if constexpr (AXIS == 1)
+        for (int kk = 0; kk < n; ++kk) cp_async_vec<VL * sizeof(T)>(ul + kk * 32 * VL, Un + base + kk * stride);
+    cp_async_commit();
+    cp_async_wait_pending(0);
+    const T* __restrict__ sub = AXIS == 0 ? P.vf + (size_t)b * 3 * nv : P.yf + ((size_t)b * nv + o) * 3 * ny;
+    const T* __restrict__ cpr = sub + n;
+    const T* __restrict__ im = cpr + n;
+    Lanes<T, VL> dp;
+#pragma unroll
+    for (int c = 0; c < VL; ++c) dp.v[c] = T(0);
+    for (int kk = 0; kk < n; ++kk) {
+        const T sk = __ldg(sub + kk), ik = __ldg(im + kk);
+        Lanes<T, VL> x = ld_lanes<T, VL>(cl + kk * 32 * VL);
+#pragma unroll
+        for (int c = 0; c < VL; ++c) dp.v[c] = (x.v[c] - sk * dp.v[c]) * ik;
+        st_lanes<T, VL>(cl + kk * 32 * VL, dp);
+    }
+    // Dirichlet lines (r faces) keep the identity system: their components
+    // take the right-hand side as it came in.
+    const int* fl = P.fl + (size_t)b * FL_N;
+    bool dirc[VL];
+    bool anyd = false;
+#pragma unroll
+    for (int c = 0; c < VL; ++c) {
+        const int i = i0 + c;
+        dirc[c] = i == nr - 1 || (i == 0 && fl[FL_RLO_DIR]);
+        anyd = anyd || dirc[c];
+    }
+    Lanes<T, VL> x = dp;
+    for (int kk = n - 1; kk >= 0; --kk) {
+        if (kk < n - 1) {
+            const T ck = __ldg(cpr + kk);
+            const Lanes<T, VL> y = ld_lanes<T, VL>(cl + kk * 32 * VL);
+#pragma unroll
+            for (int c = 0; c < VL; ++c) x.v[c] = y.v[c] - ck * x.v[c];
+        }
+        Lanes<T, VL> r = x;
+        if (anyd) {
+            const Lanes<T, VL> orig = ld_lanes<T, VL>(src + kk * stride);  // read before this lane's store
+#pragma unroll
+            for (int c = 0; c < VL; ++c)
+                if (dirc[c]) r.v[c] = orig.v[c];
+        }
+        if constexpr (AXIS == 1) {
+            const Lanes<T, VL> u = ld_lanes<T, VL>(ul + kk * 32 * VL);
+            if (kk == 0)
+#pragma unroll
+                for (int c = 0; c < VL; ++c) note_increment(P, fl, b, i0 + c, o, step_n, r.v[c]);  // dU3, j = 0
+#pragma unroll
+            for (int c = 0; c < VL; ++c) r.v[c] += u.v[c];
+        }
+        st_lanes<T, VL>(dst + kk * stride, r);
+    }
+}
+
+template <typename T, int AXIS>
+static cudaError_t wide_launch(const March<T>& P, const T* in, const T* Un, T* out, int VL, int step_n,
+                               cudaStream_t s)
+{
+    const int n = AXIS == 0 ? P.nv : P.ny;
+    const int other = AXIS == 0 ? P.ny : P.nv;
+    const long long blocks = (long long)P.B * other * ((P.nr + 32 * VL - 1) / (32 * VL));
+    const size_t smem = (size_t)n * 32 * VL * sizeof(T) * (AXIS == 1 ? 2 : 1);
+    if (smem > 227 * 1024 || P.nr % VL != 0) return cudaErrorInvalidValue;
+    if (VL * sizeof(T) == 16)
+        k_wide_lines<T, 16 / sizeof(T), AXIS><<<(unsigned)blocks, 32, smem, s>>>(P, in, Un, out, step_n);
+    else if (sizeof(T) == 4 && VL == 2)
+        k_wide_lines<T, 2, AXIS><<<(unsigned)blocks, 32, smem, s>>>(P, in, Un, out, step_n);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+// Lines per lane of a wide tile value (0: 16-byte lanes, -1: 8-byte lanes,
+// FP32 only), 0 when the value does not select the wide kernels.
+int wide_lanes(int p, size_t elem)
+{
+    if (p == 0) return (int)(16 / elem);
+    if (p == -1 && elem == 4) return 2;
+    return 0;
+}
+
+bool wide_valid(int n, int nr, int p, size_t elem)
+{
+    const int VL = wide_lanes(p, elem);
+    return VL > 0 && nr % VL == 0 && (size_t)n * 32 * VL * elem * 2 <= 227 * 1024;
+}
+
 // ------------------------------------------------------------- launchers
 
 static const size_t kSmemLimit = 227 * 1024;
@@ -394,6 +569,13 @@ cudaError_t init_kernels()
     SPLIT_ATTR(double, 4, 0) SPLIT_ATTR(double, 8, 0) SPLIT_ATTR(double, 16, 0) SPLIT_ATTR(double, 32, 0)
     SPLIT_ATTR(double, 4, 1) SPLIT_ATTR(double, 8, 1) SPLIT_ATTR(double, 16, 1) SPLIT_ATTR(double, 32, 1)
 #undef SPLIT_ATTR
+#define WIDE_ATTR(T_, VL_, AX_)                                                                              \
+    if ((e = cudaFuncSetAttribute(k_wide_lines<T_, VL_, AX_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                  (int)kSmemLimit)))                                                        \
+        return e;
+    WIDE_ATTR(float, 4, 0) WIDE_ATTR(float, 4, 1) WIDE_ATTR(float, 2, 0) WIDE_ATTR(float, 2, 1)
+    WIDE_ATTR(double, 2, 0) WIDE_ATTR(double, 2, 1)
+#undef WIDE_ATTR
     if ((e = cudaFuncSetAttribute(k_pass2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
         return e;
     if ((e = cudaFuncSetAttribute(k_pass2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
@@ -406,6 +588,9 @@ cudaError_t init_kernels()
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s)
 {
+    const int vl2 = wide_lanes(P.p2P, sizeof(T));
+    if (vl2 > 0 && (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & (vl2 * sizeof(T) - 1)) == 0))
+        return wide_launch<T, 0>(P, in, nullptr, out, vl2, 0, s);
     if (P.p2P > 1) {
         if (!split_valid(P.nv, P.p2P)) return cudaErrorInvalidValue;
         return split_launch<T, 0>(P, in, nullptr, out, P.p2P, 0, s);
@@ -421,7 +606,12 @@ template <typename T>
 cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
                          int n, cudaStream_t s)
 {
-    // Split y lines need line-invariant y systems (gamma = 0 in the group).
+    // Split and wide y lines need line-invariant y systems (gamma = 0 in the group).
+    const int vl3 = wide_lanes(P.p3P, sizeof(T));
+    if (vl3 > 0 && !any_gamma_pos &&
+        (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(Un) | reinterpret_cast<uintptr_t>(out)) &
+          (vl3 * sizeof(T) - 1)) == 0))
+        return wide_launch<T, 1>(P, in, Un, out, vl3, n, s);
     if (P.p3P > 1 && !any_gamma_pos) {
         if (!split_valid(P.ny, P.p3P)) return cudaErrorInvalidValue;
         return split_launch<T, 1>(P, in, Un, out, P.p3P, n, s);
