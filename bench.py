@@ -183,16 +183,33 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel, workload, points_per_launch):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources; else None."""
+def kernel_name(kind, tile):
+    """The kernel that runs a pass under a launch shape (7-tuple as from
+    hjm_tile_get), for the roofline line."""
+    if tile is None:
+        return "k_" + kind
+    if kind == "pass1":
+        return "k_pass1s" if tile[5] == 1 else "k_pass1"
+    if kind in ("pass2", "pass3"):
+        p = tile[3] if kind == "pass2" else tile[4]
+        return "k_" + kind if p == 1 else ("k_split_lines" if p > 1 else "k_wide_lines")
+    return "k_" + kind
+
+
+def recorded_traffic(kernel, workload, points_per_launch, tile=None):
+    """DRAM bytes per launch from the committed ncu summary of this workload,
+    if it was taken on the current kernel sources with the launch shape in
+    use; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     if d.get("source_digest") != source_digest():
         return None
-    rec = d.get("kernels", {}).get(kernel)
+    w = d.get("workloads", {}).get(workload)
+    if not w or (tile is not None and w.get("tile") != tile):
+        return None
+    rec = w.get("kernels", {}).get(kernel)
     if not rec:
         return None
     return rec["dram_bytes_per_point"] * points_per_launch
@@ -445,6 +462,8 @@ def run_ours(args):
     total_points = sum(x["grid"]["n_r"] * x["grid"]["n_v"] * x["grid"]["n_y"] for x in items)
     elem = 4 if prec == "fp32" else 8
     dom = max(KERNEL_KINDS, key=lambda k: trace[k][1])
+    shape_tiles = {tuple(t) for t in tiles.values()}
+    tile_used = list(shape_tiles)[0] if len(shape_tiles) == 1 else None
     launches, tot_ms = trace[dom]
     avg_ms = tot_ms / max(launches, 1)
     roof = None
@@ -456,10 +475,11 @@ def run_ours(args):
         alg = WORDS_PER_POINT[dom] * elem * pts_launch
         peak, peak_kind = measured_peaks()
         achieved = alg / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+        roof = {"bound": "hbm", "kernel": kernel_name(dom, tile_used), "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
-                "traffic": recorded_traffic(dom, args.workload, pts_launch)}
+                "traffic": recorded_traffic(dom, "%s-%s" % (args.workload, prec), pts_launch,
+                                            ",".join(map(str, tile_used)) if tile_used else None)}
     shares = {k: round(trace[k][1] / max(sum(v[1] for v in trace.values()), 1e-12), 4) for k in KERNEL_KINDS}
 
     # step launches: set-up, terminal, 3 per Douglas step, read-out per shape
