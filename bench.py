@@ -190,9 +190,11 @@ def kernel_name(kind, tile):
         return "k_" + kind
     if kind == "pass1":
         return "k_pass1s" if tile[5] == 1 else "k_pass1"
+    if kind == "pass3" and tile[3] == 0:
+        return "k_pass23"
     if kind in ("pass2", "pass3"):
         p = tile[3] if kind == "pass2" else tile[4]
-        return "k_" + kind if p == 1 else ("k_split_lines" if p > 1 else "k_wide_lines")
+        return "k_" + kind if p == 1 else "k_split_lines"
     return "k_" + kind
 
 

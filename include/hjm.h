@@ -195,12 +195,15 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * of a warp holding p1_nodes consecutive nodes each (p1_lanes * p1_nodes >=
  * n_r; compiled: FP32 (8: 8, 16), (16: 4, 8, 16), (32: 2, 4, 8, 16); FP64
  * (16: 2, 4, 8), (32: 2, 4, 8, 16)) and processes p1_lines lines per lane
- * segment per CTA (1..64). p2_warps / p3_warps: how passes 2 and 3 map v /
- * y lines: 1 one lane per line; 2, 4, 8 warps sharing each line (at least 2
- * and at most 32 nodes per warp); 0 four (FP32) or two (FP64) lines per lane
- * and -1 two lines per lane (FP32), which need n_r a multiple of that count
- * (pass 3 splits or widens y lines only in groups where every instrument
- * has gamma = 0). p1_staged selects how
+ * segment per CTA (1..64). p2_warps / p3_warps: warps sharing each v / y
+ * line of passes 2 and 3: 1 (one lane per line), or 2, 4, 8 when the line
+ * has at least 2 and at most 32 nodes per warp (pass 3 splits y lines only
+ * in groups where every instrument has gamma = 0). p2_warps = 0 fuses
+ * passes 2 and 3: a CTA holds the whole (v, y) plane of 8 consecutive r
+ * nodes in shared memory and runs both line solves there (gamma = 0
+ * groups, n_r * element size a multiple of 16, the plane within a CTA's
+ * shared memory); p3_warps is then unused (1). Stepwise access
+ * (hjm_douglas_pass) always runs the passes separately. p1_staged selects how
  * pass 1 gets its five stencil rows: 0 straight from global memory, 1 a CTA
  * copies the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v nodes
  * into a shared-memory ring and marches over p1_planes (1..4096) y nodes

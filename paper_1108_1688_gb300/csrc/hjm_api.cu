@@ -314,6 +314,11 @@ hjm_status run_steps(const Group& g, int n_from, int n_to, cudaStream_t s)
             TraceScope ts(2, s);
             CU_TRY(launch_pass1<T>(P, U, A, n, g.tile, s));
         }
+        if (g.tile.p2_P == 0 && !g.gpos) {  // passes 2 and 3 fused (traced as pass 3)
+            TraceScope ts(4, s);
+            CU_TRY(launch_pass23<T>(P, A, U, U, n, s));
+            continue;
+        }
         {
             TraceScope ts(3, s);
             CU_TRY(launch_pass2<T>(P, A, A, s));
@@ -856,9 +861,14 @@ static hjm_status time_passes(Group& g, int ns, cudaStream_t s, cudaEvent_t* ev,
         CU_TRY(cudaEventRecord(ev[0], s));
         CU_TRY(launch_pass1<T>(P, U, A, sn, g.tile, s));
         CU_TRY(cudaEventRecord(ev[1], s));
-        CU_TRY(launch_pass2<T>(P, A, A, s));
-        CU_TRY(cudaEventRecord(ev[2], s));
-        CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, sn, s));
+        if (g.tile.p2_P == 0 && !g.gpos) {
+            CU_TRY(cudaEventRecord(ev[2], s));
+            CU_TRY(launch_pass23<T>(P, A, U, U, sn, s));
+        } else {
+            CU_TRY(launch_pass2<T>(P, A, A, s));
+            CU_TRY(cudaEventRecord(ev[2], s));
+            CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, sn, s));
+        }
         CU_TRY(cudaEventRecord(ev[3], s));
         CU_TRY(cudaEventSynchronize(ev[3]));
         if (n < 0) continue;
@@ -924,19 +934,29 @@ extern "C" hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_pr
         Tile best = default_tile(nr, nv, ny, elem);
         // Pass 1 shapes (passes 2 and 3 at their defaults), then the line
         // splits of passes 2 and 3 (pass 1 at its best): each pass keeps the
-        // fastest of its own options, best of two timings.
+        // fastest of its own options, best of two timings; last, passes 2
+        // and 3 fused, kept when faster than the two best separate passes.
         std::vector<Tile> cands = pass1_candidates(nr, nv, ny, elem, best);
         float best_ms[3] = {3.0e38f, 3.0e38f, 3.0e38f};
-        for (int phase = 0; phase < 2; ++phase) {
+        for (int phase = 0; phase < 3; ++phase) {
             if (phase == 1) {
                 cands.clear();
-                for (int Pw : {1, 2, 4, 8, 0, -1}) {  // split lines, then several lines per lane
+                for (int Pw : {1, 2, 4, 8}) {
                     Tile t = best;
-                    t.p2_P = (Pw >= 1 ? split_valid(nv, Pw) : wide_valid(nv, nr, Pw, elem)) ? Pw : 1;
-                    t.p3_P = (Pw >= 1 ? split_valid(ny, Pw) : wide_valid(ny, nr, Pw, elem)) && !g.gpos ? Pw : 1;
+                    t.p2_P = split_valid(nv, Pw) ? Pw : 1;
+                    t.p3_P = split_valid(ny, Pw) && !g.gpos ? Pw : 1;
                     cands.push_back(t);
                 }
                 best_ms[1] = best_ms[2] = 3.0e38f;
+            }
+            if (phase == 2) {
+                cands.clear();
+                for (int F : {0}) {
+                    Tile t = best;
+                    t.p2_P = F;
+                    t.p3_P = 1;
+                    if (!g.gpos && tile_valid(t, nr, nv, ny, elem)) cands.push_back(t);
+                }
             }
             for (const Tile& cand : cands) {
                 g.tile = cand;
@@ -964,6 +984,12 @@ extern "C" hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_pr
                         best_ms[2] = mn[2];
                         best.p3_P = cand.p3_P;
                     }
+                }
+                if (phase == 2 && mn[1] + mn[2] < best_ms[1] + best_ms[2]) {
+                    best_ms[1] = mn[1];
+                    best_ms[2] = mn[2];
+                    best.p2_P = cand.p2_P;
+                    best.p3_P = 1;
                 }
             }
         }
@@ -1111,6 +1137,10 @@ hjm_status static_march(const GroupTables& t, void* U, void* A, int nsteps, bool
     const March<T> P = march_args<T>(t);
     for (int n = 0; n < nsteps; ++n) {
         CU_TRY(launch_pass1<T>(P, (const T*)U, (T*)A, n, tile, s));
+        if (tile.p2_P == 0 && !gpos) {
+            CU_TRY(launch_pass23<T>(P, (const T*)A, (const T*)U, (T*)U, n, s));
+            continue;
+        }
         CU_TRY(launch_pass2<T>(P, (const T*)A, (T*)A, s));
         CU_TRY(launch_pass3<T>(P, (const T*)A, (const T*)U, (T*)U, gpos, n, s));
     }

@@ -153,7 +153,7 @@ struct Tile {
     int p1_S;  // pass 1: lanes per r line (8, 16, 32)
     int p1_M;  // pass 1: r nodes per lane; p1_S * p1_M >= n_r
     int p1_R;  // pass 1: lines per lane segment per CTA
-    int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8)
+    int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8); 0: passes 2 and 3 fused
     int p3_P;  // pass 3: warps sharing each y line (1, 2, 4, 8)
     int p1_stage;  // pass 1: 0 rows from global memory, 1 staged y planes
     int p1_J;      // pass 1 staged: y planes marched per CTA (0 when not staged)
@@ -163,11 +163,12 @@ Tile default_tile(int nr, int nv, int ny, size_t elem);
 bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem);
 // Whether a line of n nodes can be split into Pw chunks (Pw = 1: unsplit).
 bool split_valid(int n, int Pw);
-// Wide line solves (several lines per lane): lines per lane selected by a
-// pass-2/3 tile value (0: 16-byte lanes, -1: 8-byte lanes, FP32), else 0;
-// and whether that choice fits a line of n nodes with n_r r nodes.
-int wide_lanes(int p, size_t elem);
-bool wide_valid(int n, int nr, int p, size_t elem);
+// Passes 2 and 3 fused over slabs of 8 r nodes (tile p2 = 0) when the
+// slab's (v, y) plane fits in shared memory; gamma = 0 groups.
+bool pass23_valid(int nr, int nv, int ny, int p2, size_t elem);
+template <typename T>
+cudaError_t launch_pass23(const March<T>& P, const T* in, const T* Un, T* out, int n, cudaStream_t s);
+
 
 // The three Douglas passes of step n (in/out as documented in hjm.h).
 template <typename T>

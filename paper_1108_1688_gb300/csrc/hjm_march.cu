@@ -56,7 +56,7 @@ __device__ __forceinline__ void cp_async_wait_pending(int pending)
 // once) and runs the Thomas forward sweep d'_k = (d_k - sub_k d'_{k-1}) / m_k.
 // The column then holds d'; returns d'_{n-1}.
 template <typename T>
-__device__ __forceinline__ T gather_forward(T* col, int lane, const T* src, long long stride, int n,
+__device__ __forceinline__ T gather_forward(T* col, int lane, const T* src, int stride, int n,
                                             const T* __restrict__ sub, const T* __restrict__ im)
 {
     for (int kk = 0; kk < n; ++kk) cp_async_elem(&col[kk * 32 + lane], src + kk * stride);
@@ -92,10 +92,10 @@ __global__ void __launch_bounds__(32) k_pass2(const March<T> P, const T* in, T* 
     const int lane = threadIdx.x;
     const int nr = P.nr, nv = P.nv;
     const int tiles = (nr + 31) / 32;
-    const long long blk = blockIdx.x;
+    const unsigned blk = blockIdx.x;
     const int it = (int)(blk % tiles);
     const int j = (int)((blk / tiles) % P.ny);
-    const int b = (int)(blk / ((long long)tiles * P.ny));
+    const int b = (int)(blk / (unsigned)(tiles * P.ny));
     const int i = it * 32 + lane;
     if (i >= nr) return;
     const long long base = (long long)b * P.N + (long long)j * nv * nr + i;
@@ -104,17 +104,17 @@ __global__ void __launch_bounds__(32) k_pass2(const March<T> P, const T* in, T* 
     const int* fl = P.fl + (size_t)b * FL_N;
     if (i == nr - 1 || (i == 0 && fl[FL_RLO_DIR])) {  // Dirichlet line: identity system
         if (src != dst)
-            for (int kk = 0; kk < nv; ++kk) dst[(long long)kk * nr] = src[(long long)kk * nr];
+            for (int kk = 0; kk < nv; ++kk) dst[kk * nr] = src[kk * nr];
         return;
     }
     const T* __restrict__ sub = P.vf + (size_t)b * 3 * nv;
     const T* __restrict__ cpr = sub + nv;
     const T* __restrict__ im = cpr + nv;
     T x = gather_forward<T>(col, lane, src, nr, nv, sub, im);
-    dst[(long long)(nv - 1) * nr] = x;
+    dst[(nv - 1) * nr] = x;
     for (int kk = nv - 2; kk >= 0; --kk) {
         x = col[kk * 32 + lane] - __ldg(cpr + kk) * x;
-        dst[(long long)kk * nr] = x;
+        dst[kk * nr] = x;
     }
 }
 
@@ -131,13 +131,13 @@ __global__ void __launch_bounds__(32) k_pass3(const March<T> P, const T* in, con
     T* ucol = col + (size_t)ny * 32;          // U^n
     T* ccol = ucol + (size_t)ny * 32;         // c' (gamma > 0 only)
     const int tiles = (nr + 31) / 32;
-    const long long blk = blockIdx.x;
+    const unsigned blk = blockIdx.x;
     const int it = (int)(blk % tiles);
     const int k = (int)((blk / tiles) % nv);
-    const int b = (int)(blk / ((long long)tiles * nv));
+    const int b = (int)(blk / (unsigned)(tiles * nv));
     const int i = it * 32 + lane;
     if (i >= nr) return;
-    const long long stride = (long long)nr * nv;
+    const int stride = nr * nv;  // element offsets within an instrument fit in 32 bits
     const long long base = (long long)b * P.N + (long long)k * nr + i;
     const T* src = in + base;
     const T* usrc = Un + base;
@@ -250,14 +250,14 @@ __global__ void __launch_bounds__(256) k_split_lines(const March<T> P, const T* 
     T* col = red + K * 32;                    // [n][32] right-hand side
     T* ucol = col + n * 32;                   // [n][32] U^n (pass 3)
     const int tiles = (nr + 31) / 32;
-    const long long blk = blockIdx.x;
+    const unsigned blk = blockIdx.x;
     const int it = (int)(blk % tiles);
     const int o = (int)((blk / tiles) % other);
-    const int b = (int)(blk / ((long long)tiles * other));
+    const int b = (int)(blk / (unsigned)(tiles * other));
     const int i = it * 32 + lane;
     const bool live = i < nr;  // lanes past n_r only join the barrier
     const int ic = live ? i : nr - 1;
-    const long long stride = AXIS == 0 ? (long long)nr : (long long)nr * nv;
+    const int stride = AXIS == 0 ? nr : nr * nv;  // 32-bit offsets within an instrument
     const long long base = (long long)b * P.N + (AXIS == 0 ? (long long)o * nv * nr : (long long)o * nr) + ic;
     int s, L;
     part_chunk(n, Pw, c, s, L);
@@ -369,179 +369,240 @@ bool split_valid(int n, int Pw)
                        split_smem(n, Pw, 1, sizeof(double)) <= 227 * 1024);
 }
 
-// ------------------------------------------------------- wide line solves
+// ------------------------------------------------- fused passes 2 and 3
 
-// Copies of 8 or 16 bytes (VL consecutive r nodes) global -> shared.
-template <int BYTES>
-__device__ __forceinline__ void cp_async_vec(void* smem_dst, const void* gmem_src)
-{
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
-    if constexpr (BYTES == 16)
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem_src) : "memory");
-    else
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem_src) : "memory");
-}
-
-template <typename T, int VL>
-struct Lanes {
-    T v[VL];
+template <typename T, int V>
+struct Vec16;
+template <>
+struct Vec16<float, 4> {
+    using type = float4;
+};
+template <>
+struct Vec16<double, 2> {
+    using type = double2;
 };
 
-template <typename T, int VL>
-__device__ __forceinline__ Lanes<T, VL> ld_lanes(const T* p)
+// 16-byte shared read of V elements.
+template <typename T, int V>
+__device__ __forceinline__ void lds_pair(const T* p, T (&x)[V])
 {
-    Lanes<T, VL> r;
-    if constexpr (VL * sizeof(T) == 16) {
-        if constexpr (sizeof(T) == 4) {
-            const float4 x = *reinterpret_cast<const float4*>(p);
-            r.v[0] = x.x;
-            r.v[1] = x.y;
-            r.v[2] = x.z;
-            r.v[3] = x.w;
-        } else {
-            const double2 x = *reinterpret_cast<const double2*>(p);
-            r.v[0] = x.x;
-            r.v[1] = x.y;
-        }
+    const typename Vec16<T, V>::type v = *reinterpret_cast<const typename Vec16<T, V>::type*>(p);
+    if constexpr (V == 4) {
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+        x[3] = v.w;
     } else {
-        const float2 x = *reinterpret_cast<const float2*>(p);
-        r.v[0] = x.x;
-        r.v[1] = x.y;
-    }
-    return r;
-}
-
-template <typename T, int VL>
-__device__ __forceinline__ void st_lanes(T* p, const Lanes<T, VL>& r)
-{
-    if constexpr (VL * sizeof(T) == 16) {
-        if constexpr (sizeof(T) == 4)
-            *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
-        else
-            *reinterpret_cast<double2*>(p) = make_double2(r.v[0], r.v[1]);
-    } else {
-        *reinterpret_cast<float2*>(p) = make_float2(r.v[0], r.v[1]);
+        x[0] = v.x;
+        x[1] = v.y;
     }
 }
 
-// Passes 2 (AXIS 0) and 3 (AXIS 1, gamma = 0 groups) with VL consecutive
-// lines per lane (32 VL lines per warp): the lines are gathered with 8- or
-// 16-byte asynchronous copies (VL r nodes each, a warp reads 32 VL
-// contiguous nodes of a row) into shared memory and solved by Thomas with
-// the precomputed LU factors, the VL recurrences of a lane side by side.
-// Pass 3 stages U^n the same way. Needs n_r a multiple of VL and 8/16-byte
-// aligned fields (checked by the launcher).
-template <typename T, int VL, int AXIS>
-__global__ void __launch_bounds__(32) k_wide_lines(const March<T> P, const T* in, const T* Un, T* out,
-                                                   const int step_n)
+// 16-byte global store of u + x.
+template <typename T, int V>
+__device__ __forceinline__ void add_store(T* p, const typename Vec16<T, V>::type& u, const T (&x)[V])
+{
+    if constexpr (V == 4)
+        *reinterpret_cast<float4*>(p) = make_float4(u.x + x[0], u.y + x[1], u.z + x[2], u.w + x[3]);
+    else
+        *reinterpret_cast<double2*>(p) = make_double2(u.x + x[0], u.y + x[1]);
+}
+
+// Passes 2 and 3 of a step in one kernel when the (v, y) plane of a slab of
+// SL = 8 consecutive r nodes (32-byte rows) fits in shared memory (gamma = 0
+// groups): the CTA
+// gathers dU1 of its slab (16-byte copies, SL r nodes of every (k, j) row),
+// solves every v line of the slab in place, then every y line, then writes
+// U^{n+1} = U^n + dU3. The same Thomas sweeps with the same factors as the
+// separate passes, so the results are the same; dU2 never goes to global
+// memory (12 bytes per point instead of 8 + 12).
+// Shared layout S[j][k SL + ii], row stride RJ = n_v SL + pad with RJ = SL
+// (mod 32): lanes (ii fastest) of a v line sweep or a y line sweep hit
+// distinct banks.
+template <typename T, int SL>
+__global__ void __launch_bounds__(1024) k_pass23(const March<T> P, const T* in, const T* Un, T* out, const int n,
+                                                 const int RJ)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int lane = threadIdx.x;
+    T* S = reinterpret_cast<T*>(smem_raw);
+    constexpr int V = 16 / sizeof(T);  // elements per 16-byte piece
+    constexpr int H = SL / V;          // 16-byte pieces per row of the slab
+    const int tid = threadIdx.x, nth = blockDim.x;
     const int nr = P.nr, nv = P.nv, ny = P.ny;
-    const int n = AXIS == 0 ? nv : ny;
-    const int other = AXIS == 0 ? ny : nv;
-    T* col = reinterpret_cast<T*>(smem_raw);  // [n][32 VL] right-hand side, then d'
-    T* ucol = col + (size_t)n * 32 * VL;      // [n][32 VL] U^n (pass 3)
-    const int tiles = (nr + 32 * VL - 1) / (32 * VL);
-    const long long blk = blockIdx.x;
-    const int it = (int)(blk % tiles);
-    const int o = (int)((blk / tiles) % other);
-    const int b = (int)(blk / ((long long)tiles * other));
-    const int i0 = (it * 32 + lane) * VL;
-    if (i0 >= nr) return;
-    const long long stride = AXIS == 0 ? (long long)nr : (long long)nr * nv;
-    const long long base = (long long)b * P.N + (AXIS == 0 ? (long long)o * nv * nr : (long long)o * nr) + i0;
+    const int slabs = (nr + SL - 1) / SL;
+    const int b = blockIdx.x / slabs;
+    const int i0 = (blockIdx.x % slabs) * SL;
+    const int sw = min(SL, nr - i0);  // live r nodes of this slab
+    const long long base = (long long)b * P.N + i0;
     const T* src = in + base;
-    T* dst = out + base;
-    T* cl = col + lane * VL;
-    T* ul = ucol + lane * VL;
-    for (int kk = 0; kk < n; ++kk) cp_async_vec<VL * sizeof(T)>(cl + kk * 32 * VL, src + kk * stride);
-    if constexpr (AXIS == 1)
-        for (int kk = 0; kk < n; ++kk) cp_async_vec<VL * sizeof(T)>(ul + kk * 32 * VL, Un + base + kk * stride);
+    const int* fl = P.fl + (size_t)b * FL_N;
+    const int rows = nv * ny;
+    // Work items are (row, piece); (j, k) of item q = tid + t nth advanced
+    // without divisions.
+    const int qn = rows * H;
+    const int dq = nth / H, dk0 = dq % nv, dj0 = dq / nv;
+    // 1. gather dU1 of the slab (a ragged last slab copies element-wise)
+    if (sw == SL) {
+        int h = tid % H, r = tid / H, k = r % nv, j = r / nv;
+        for (int q = tid; q < qn; q += nth) {
+            const unsigned sa = (unsigned)__cvta_generic_to_shared(S + j * RJ + k * SL + h * V);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(src + (j * nv + k) * nr + h * V)
+                         : "memory");
+            k += dk0;
+            j += dj0;
+            if (k >= nv) {
+                k -= nv;
+                ++j;
+            }
+        }
+    } else {
+        for (int q = tid; q < rows * SL; q += nth) {
+            const int r = q / SL, ii = q % SL;
+            if (ii < sw) cp_async_elem(S + (r / nv) * RJ + (r % nv) * SL + ii, src + r * nr + ii);
+        }
+    }
     cp_async_commit();
     cp_async_wait_pending(0);
-    const T* __restrict__ sub = AXIS == 0 ? P.vf + (size_t)b * 3 * nv : P.yf + ((size_t)b * nv + o) * 3 * ny;
-    const T* __restrict__ cpr = sub + n;
-    const T* __restrict__ im = cpr + n;
-    Lanes<T, VL> dp;
-#pragma unroll
-    for (int c = 0; c < VL; ++c) dp.v[c] = T(0);
-    for (int kk = 0; kk < n; ++kk) {
-        const T sk = __ldg(sub + kk), ik = __ldg(im + kk);
-        Lanes<T, VL> x = ld_lanes<T, VL>(cl + kk * 32 * VL);
-#pragma unroll
-        for (int c = 0; c < VL; ++c) dp.v[c] = (x.v[c] - sk * dp.v[c]) * ik;
-        st_lanes<T, VL>(cl + kk * 32 * VL, dp);
+    __syncthreads();
+    const int rlo = fl[FL_RLO_DIR];
+    // 2. v lines (ii, j) and 3. y lines (ii, k): Thomas with the precomputed
+    // factors, four nodes loaded ahead of the recurrence.
+    auto thomas = [&](T* line, int len, int st, const T* __restrict__ sub, const T* __restrict__ cpr,
+                      const T* __restrict__ im) {
+        T dp = T(0);
+        int k = 0;
+        for (; k + 4 <= len; k += 4) {
+            const T x0 = line[k * st], x1 = line[(k + 1) * st], x2 = line[(k + 2) * st], x3 = line[(k + 3) * st];
+            dp = (x0 - __ldg(sub + k) * dp) * __ldg(im + k);
+            line[k * st] = dp;
+            dp = (x1 - __ldg(sub + k + 1) * dp) * __ldg(im + k + 1);
+            line[(k + 1) * st] = dp;
+            dp = (x2 - __ldg(sub + k + 2) * dp) * __ldg(im + k + 2);
+            line[(k + 2) * st] = dp;
+            dp = (x3 - __ldg(sub + k + 3) * dp) * __ldg(im + k + 3);
+            line[(k + 3) * st] = dp;
+        }
+        for (; k < len; ++k) {
+            dp = (line[k * st] - __ldg(sub + k) * dp) * __ldg(im + k);
+            line[k * st] = dp;
+        }
+        T x = dp;
+        int m = len - 2;
+        for (; m - 3 >= 0; m -= 4) {
+            const T y0 = line[m * st], y1 = line[(m - 1) * st], y2 = line[(m - 2) * st], y3 = line[(m - 3) * st];
+            x = y0 - __ldg(cpr + m) * x;
+            line[m * st] = x;
+            x = y1 - __ldg(cpr + m - 1) * x;
+            line[(m - 1) * st] = x;
+            x = y2 - __ldg(cpr + m - 2) * x;
+            line[(m - 2) * st] = x;
+            x = y3 - __ldg(cpr + m - 3) * x;
+            line[(m - 3) * st] = x;
+        }
+        for (; m >= 0; --m) {
+            x = line[m * st] - __ldg(cpr + m) * x;
+            line[m * st] = x;
+        }
+    };
+    {
+        const T* sub = P.vf + (size_t)b * 3 * nv;
+        for (int q = tid; q < SL * ny; q += nth) {
+            const int ii = q % SL, j = q / SL, i = i0 + ii;
+            if (ii >= sw || i == nr - 1 || (i == 0 && rlo)) continue;  // Dirichlet lines: identity
+            thomas(S + j * RJ + ii, nv, SL, sub, sub + nv, sub + 2 * nv);
+        }
     }
-    // Dirichlet lines (r faces) keep the identity system: their components
-    // take the right-hand side as it came in.
-    const int* fl = P.fl + (size_t)b * FL_N;
-    bool dirc[VL];
-    bool anyd = false;
-#pragma unroll
-    for (int c = 0; c < VL; ++c) {
-        const int i = i0 + c;
-        dirc[c] = i == nr - 1 || (i == 0 && fl[FL_RLO_DIR]);
-        anyd = anyd || dirc[c];
+    __syncthreads();
+    for (int q = tid; q < SL * nv; q += nth) {
+        const int ii = q % SL, k = q / SL, i = i0 + ii;
+        if (ii >= sw || i == nr - 1 || (i == 0 && rlo)) continue;
+        const T* sub = P.yf + ((size_t)b * nv + k) * 3 * ny;
+        thomas(S + k * SL + ii, ny, RJ, sub, sub + ny, sub + 2 * ny);
     }
-    Lanes<T, VL> x = dp;
-    for (int kk = n - 1; kk >= 0; --kk) {
-        if (kk < n - 1) {
-            const T ck = __ldg(cpr + kk);
-            const Lanes<T, VL> y = ld_lanes<T, VL>(cl + kk * 32 * VL);
+    __syncthreads();
+    // 4. U^{n+1} = U^n + dU3 in 16-byte pieces, four loads ahead of the
+    // stores (each piece is read before it is written, by the same thread),
+    // and the rounding indicator on j = 0.
+    const T* ub = Un + base;
+    T* ob = out + base;
+    if (sw == SL) {
+        int h = tid % H, r = tid / H, k = r % nv, j = r / nv;
+        for (int q0 = tid; q0 < qn; q0 += 4 * nth) {
+            typename Vec16<T, V>::type u[4];
+            int jj[4], kk[4], hh[4];
 #pragma unroll
-            for (int c = 0; c < VL; ++c) x.v[c] = y.v[c] - ck * x.v[c];
+            for (int t = 0; t < 4; ++t) {
+                jj[t] = j;
+                kk[t] = k;
+                hh[t] = h;
+                if (q0 + t * nth < qn)
+                    u[t] = *reinterpret_cast<const typename Vec16<T, V>::type*>(ub + (j * nv + k) * nr + h * V);
+                k += dk0;
+                j += dj0;
+                if (k >= nv) {
+                    k -= nv;
+                    ++j;
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (q0 + t * nth >= qn) break;
+                const T* sp = S + jj[t] * RJ + kk[t] * SL + hh[t] * V;
+                T x[V];
+                lds_pair<T, V>(sp, x);
+                if (jj[t] == 0)
+#pragma unroll
+                    for (int c = 0; c < V; ++c) note_increment(P, fl, b, i0 + hh[t] * V + c, kk[t], n, x[c]);
+                add_store<T, V>(ob + (jj[t] * nv + kk[t]) * nr + hh[t] * V, u[t], x);
+            }
         }
-        Lanes<T, VL> r = x;
-        if (anyd) {
-            const Lanes<T, VL> orig = ld_lanes<T, VL>(src + kk * stride);  // read before this lane's store
-#pragma unroll
-            for (int c = 0; c < VL; ++c)
-                if (dirc[c]) r.v[c] = orig.v[c];
+    } else {
+        for (int q = tid; q < rows * SL; q += nth) {
+            const int r = q / SL, ii = q % SL;
+            if (ii >= sw) continue;
+            const int j = r / nv, k = r % nv;
+            const T x = S[j * RJ + k * SL + ii];
+            if (j == 0) note_increment(P, fl, b, i0 + ii, k, n, x);
+            ob[r * nr + ii] = ub[r * nr + ii] + x;
         }
-        if constexpr (AXIS == 1) {
-            const Lanes<T, VL> u = ld_lanes<T, VL>(ul + kk * 32 * VL);
-            if (kk == 0)
-#pragma unroll
-                for (int c = 0; c < VL; ++c) note_increment(P, fl, b, i0 + c, o, step_n, r.v[c]);  // dU3, j = 0
-#pragma unroll
-            for (int c = 0; c < VL; ++c) r.v[c] += u.v[c];
-        }
-        st_lanes<T, VL>(dst + kk * stride, r);
     }
 }
 
-template <typename T, int AXIS>
-static cudaError_t wide_launch(const March<T>& P, const T* in, const T* Un, T* out, int VL, int step_n,
-                               cudaStream_t s)
+// Row stride (elements) of the fused kernel's shared plane: RJ = SL (mod 32).
+static int p23_row_stride(int nv, int SL)
 {
-    const int n = AXIS == 0 ? P.nv : P.ny;
-    const int other = AXIS == 0 ? P.ny : P.nv;
-    const long long blocks = (long long)P.B * other * ((P.nr + 32 * VL - 1) / (32 * VL));
-    const size_t smem = (size_t)n * 32 * VL * sizeof(T) * (AXIS == 1 ? 2 : 1);
-    if (smem > 227 * 1024 || P.nr % VL != 0) return cudaErrorInvalidValue;
-    if (VL * sizeof(T) == 16)
-        k_wide_lines<T, 16 / sizeof(T), AXIS><<<(unsigned)blocks, 32, smem, s>>>(P, in, Un, out, step_n);
-    else if (sizeof(T) == 4 && VL == 2)
-        k_wide_lines<T, 2, AXIS><<<(unsigned)blocks, 32, smem, s>>>(P, in, Un, out, step_n);
-    else
+    const int base = nv * SL;
+    return base + ((SL - base % 32) % 32 + 32) % 32;
+}
+
+size_t pass23_smem(int nv, int ny, int SL, size_t elem)
+{
+    return (size_t)ny * p23_row_stride(nv, SL) * elem;
+}
+
+bool pass23_valid(int nr, int nv, int ny, int p2, size_t elem)
+{
+    constexpr int SL = 8;
+    if (p2 != 0 || (nr * (int)elem) % 16 != 0) return false;
+    if (SL * (nv > ny ? nv : ny) > 1024 * 8) return false;
+    return pass23_smem(nv, ny, SL, elem) <= 227 * 1024;
+}
+
+template <typename T>
+cudaError_t launch_pass23(const March<T>& P, const T* in, const T* Un, T* out, int n, cudaStream_t s)
+{
+    constexpr int SL = 8;
+    if (!pass23_valid(P.nr, P.nv, P.ny, P.p2P, sizeof(T))) return cudaErrorInvalidValue;
+    if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(Un) | reinterpret_cast<uintptr_t>(out)) &
+         15) != 0)
         return cudaErrorInvalidValue;
+    const int RJ = p23_row_stride(P.nv, SL);
+    const size_t smem = pass23_smem(P.nv, P.ny, SL, sizeof(T));
+    const int lines = SL * (P.nv > P.ny ? P.nv : P.ny);
+    const int threads = lines < 1024 ? ((lines + 31) / 32) * 32 : 1024;
+    const unsigned blocks = (unsigned)(P.B * ((P.nr + SL - 1) / SL));
+    k_pass23<T, SL><<<blocks, threads, smem, s>>>(P, in, Un, out, n, RJ);
     return cudaGetLastError();
-}
-
-// Lines per lane of a wide tile value (0: 16-byte lanes, -1: 8-byte lanes,
-// FP32 only), 0 when the value does not select the wide kernels.
-int wide_lanes(int p, size_t elem)
-{
-    if (p == 0) return (int)(16 / elem);
-    if (p == -1 && elem == 4) return 2;
-    return 0;
-}
-
-bool wide_valid(int n, int nr, int p, size_t elem)
-{
-    const int VL = wide_lanes(p, elem);
-    return VL > 0 && nr % VL == 0 && (size_t)n * 32 * VL * elem * 2 <= 227 * 1024;
 }
 
 // ------------------------------------------------------------- launchers
@@ -569,13 +630,11 @@ cudaError_t init_kernels()
     SPLIT_ATTR(double, 4, 0) SPLIT_ATTR(double, 8, 0) SPLIT_ATTR(double, 16, 0) SPLIT_ATTR(double, 32, 0)
     SPLIT_ATTR(double, 4, 1) SPLIT_ATTR(double, 8, 1) SPLIT_ATTR(double, 16, 1) SPLIT_ATTR(double, 32, 1)
 #undef SPLIT_ATTR
-#define WIDE_ATTR(T_, VL_, AX_)                                                                              \
-    if ((e = cudaFuncSetAttribute(k_wide_lines<T_, VL_, AX_>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                  (int)kSmemLimit)))                                                        \
+    if ((e = cudaFuncSetAttribute(k_pass23<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
         return e;
-    WIDE_ATTR(float, 4, 0) WIDE_ATTR(float, 4, 1) WIDE_ATTR(float, 2, 0) WIDE_ATTR(float, 2, 1)
-    WIDE_ATTR(double, 2, 0) WIDE_ATTR(double, 2, 1)
-#undef WIDE_ATTR
+    if ((e = cudaFuncSetAttribute(k_pass23<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
+        return e;
+
     if ((e = cudaFuncSetAttribute(k_pass2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
         return e;
     if ((e = cudaFuncSetAttribute(k_pass2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit)))
@@ -588,9 +647,6 @@ cudaError_t init_kernels()
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s)
 {
-    const int vl2 = wide_lanes(P.p2P, sizeof(T));
-    if (vl2 > 0 && (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & (vl2 * sizeof(T) - 1)) == 0))
-        return wide_launch<T, 0>(P, in, nullptr, out, vl2, 0, s);
     if (P.p2P > 1) {
         if (!split_valid(P.nv, P.p2P)) return cudaErrorInvalidValue;
         return split_launch<T, 0>(P, in, nullptr, out, P.p2P, 0, s);
@@ -606,12 +662,7 @@ template <typename T>
 cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
                          int n, cudaStream_t s)
 {
-    // Split and wide y lines need line-invariant y systems (gamma = 0 in the group).
-    const int vl3 = wide_lanes(P.p3P, sizeof(T));
-    if (vl3 > 0 && !any_gamma_pos &&
-        (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(Un) | reinterpret_cast<uintptr_t>(out)) &
-          (vl3 * sizeof(T) - 1)) == 0))
-        return wide_launch<T, 1>(P, in, Un, out, vl3, n, s);
+    // Split y lines need line-invariant y systems (gamma = 0 in the group).
     if (P.p3P > 1 && !any_gamma_pos) {
         if (!split_valid(P.ny, P.p3P)) return cudaErrorInvalidValue;
         return split_launch<T, 1>(P, in, Un, out, P.p3P, n, s);
@@ -629,5 +680,10 @@ template cudaError_t launch_pass3<float>(const March<float>&, const float*, cons
                                          int, cudaStream_t);
 template cudaError_t launch_pass3<double>(const March<double>&, const double*, const double*, double*,
                                           bool, int, cudaStream_t);
+
+template cudaError_t launch_pass23<float>(const March<float>&, const float*, const float*, float*, int,
+                                          cudaStream_t);
+template cudaError_t launch_pass23<double>(const March<double>&, const double*, const double*, double*, int,
+                                           cudaStream_t);
 
 }  // namespace hjm

@@ -719,8 +719,8 @@ Tile default_tile(int nr, int nv, int ny, size_t elem)
 bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
 {
     if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
-    if (!(split_valid(nv, t.p2_P) || wide_valid(nv, nr, t.p2_P, elem))) return false;
-    if (!(split_valid(ny, t.p3_P) || wide_valid(ny, nr, t.p3_P, elem))) return false;
+    if (!(split_valid(nv, t.p2_P) || pass23_valid(nr, nv, ny, t.p2_P, elem)) || !split_valid(ny, t.p3_P))
+        return false;
     if (t.p1_stage == 0) return t.p1_J == 0;
     // staged rows are copied in 16-byte pieces
     if ((nr * (int)elem) % 16 != 0) return false;

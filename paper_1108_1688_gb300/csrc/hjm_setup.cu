@@ -660,8 +660,8 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
 cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s)
 {
     const dim3 faces(g.nsteps, g.B);
-    // split counts: -1, 0 (wide line solves) or 1 (whole lines) need no extra factors
-    if (g.p2P < -1 || g.p2P > kMaxSplit || g.p3P < -1 || g.p3P > kMaxSplit) return cudaErrorInvalidValue;
+    // p2P of 0 (passes 2 and 3 fused) or 1 needs no split factors for v
+    if (g.p2P < 0 || g.p2P > kMaxSplit || g.p3P < 1 || g.p3P > kMaxSplit) return cudaErrorInvalidValue;
     if (elem == sizeof(float)) {
         k_setup<float><<<g.B, 256, 0, s>>>(g);
         k_faces<float><<<faces, 128, 0, s>>>(g);

@@ -1,7 +1,7 @@
 // The pricing surrogate (not a part of the paper's method): a multilayer
 // perceptron trained on caplet prices produced by this library's own FP32
 // Douglas ADI march, used for fast repeated pricing (calibration loops),
-// with the march as its fallback and the judge of its error.
+// with the march as its fallback and as the reference that measures its error.
 //
 // Inputs x = (kappa, lambda, theta, epsilon, rho, T, delta, K, F): the model
 // parameters (gamma = 0, v0 = 1), expiry T, accrual delta = T_M - T, strike

@@ -58,11 +58,9 @@ def tiles_for(it, prec):
             out.append((S, M, R, 1, 1))
     for P in (2, 4, 8):
         out.append((out[0][0], out[0][1], 2, P if split_ok(nv, P) else 1, P if split_ok(ny, P) else 1))
-    # several lines per lane (n_r a multiple of the lines per lane)
-    for W in ((0, -1) if prec == "fp32" else (0,)):
-        vl = (4 if prec == "fp32" else 2) if W == 0 else 2
-        if nr % vl == 0:
-            out.append((out[0][0], out[0][1], 2, W, W))
+    # passes 2 and 3 fused over slabs of 8 r nodes
+    if nr * (8 if prec == "fp64" else 4) % 16 == 0:
+        out.append((out[0][0], out[0][1], 2, 0, 1))
     # staged y planes (rows copied in 16-byte pieces): every shape, with
     # strips of 1 or 2 lines per segment and runs of 1 or 3 planes
     if nr * (8 if prec == "fp64" else 4) % 16 == 0:
@@ -142,7 +140,7 @@ def test_tile_calls_validate_and_restore(H):
                 (16, 8, 0, 1, 1),      # no lines
                 (16, 8, 4, 3, 1),      # 3 warps per line
                 (16, 8, 4, 1, 64),     # more warps than the y line allows
-                (16, 8, 4, -2, 1)]:    # no such line mapping
+                (16, 8, 4, -1, 1)]:    # no such pass-2 mapping
         with pytest.raises(H.HJMError):
             H.hjm_tile_set(128, 64, 64, "fp32", bad)
     H.hjm_tile_set(128, 64, 64, "fp32", (32, 4, 2, 8, 4))
