@@ -117,6 +117,9 @@ typedef struct {
     int n_steps;
     float time_us;            /* device time of the whole call, microseconds */
     int tile_cfg;             /* launch shape used, packed as described at hjm_tile */
+    double d_dr;              /* dC/dr at the read-out point r = f(0,0), v = v0, y = 0 */
+    double d_dv;              /* dC/dv there (derivatives of the FP64 read-out
+                                 interpolant, i.e. of the final field) */
 } hjm_price_info;
 
 typedef struct hjm_grid hjm_grid;

@@ -111,6 +111,8 @@ def lib():
             L.orc_march.argtypes = [C.c_void_p, dp]
             L.orc_readout.argtypes = [C.c_void_p, dp]
             L.orc_readout.restype = C.c_double
+            L.orc_readout_greeks.argtypes = [C.c_void_p, dp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+            L.orc_readout_greeks.restype = None
             L.orc_time.argtypes = [C.c_void_p, C.c_double]
             L.orc_time.restype = C.c_double
             L.orc_dirichlet.argtypes = [C.c_void_p] + [C.c_double] * 3
@@ -222,6 +224,12 @@ class Ctx:
 
     def readout(self, U):
         return lib().orc_readout(self._h, np.ascontiguousarray(U, dtype=np.float64))
+
+    def readout_greeks(self, U):
+        """(dC/dr, dC/dv) at the read-out point."""
+        a, b = C.c_double(), C.c_double()
+        lib().orc_readout_greeks(self._h, np.ascontiguousarray(U, dtype=np.float64), C.byref(a), C.byref(b))
+        return a.value, b.value
 
     def dirichlet(self, t, r, y):
         return lib().orc_dirichlet(self._h, float(t), float(r), float(y))

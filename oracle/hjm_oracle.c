@@ -708,6 +708,53 @@ double orc_readout(const orc_ctx* x, const double* U)
     return s;
 }
 
+/* Derivatives of the price in r and v at the read-out point (the Greeks
+ * listed with the paper's figures: sensitivity to the short rate and to the
+ * volatility level): the derivatives of the read-out interpolant of R10,
+ * d/dz = (1 / (h J(xi))) d/ds with s = xi / h the node-unit coordinate and
+ * J = dz/dxi the metric Jacobian at the read-out point. */
+static void lagrange4_d(double s, double* dw)
+{
+    for (int m = 0; m < 4; ++m) {
+        double sum = 0.0;
+        for (int l = 0; l < 4; ++l) {
+            if (l == m) continue;
+            double p = 1.0 / (double)(m - l);
+            for (int q = 0; q < 4; ++q)
+                if (q != m && q != l) p *= (s - q) / (double)(m - q);
+            sum += p;
+        }
+        dw[m] = sum;
+    }
+}
+
+void orc_readout_greeks(const orc_ctx* x, const double* U, double* d_dr, double* d_dv)
+{
+    double xir = metric_xi(x, 0, orc_curve_f(&x->c, 0.0)), xiv = metric_xi(x, 1, x->m.v0);
+    double xr = xir / x->h[0], xv = xiv / x->h[1];
+    int ir = (int)floor(xr) - 1, iv = (int)floor(xv) - 1;
+    if (ir < 0) ir = 0;
+    if (ir > x->n[0] - 4) ir = x->n[0] - 4;
+    if (iv < 0) iv = 0;
+    if (iv > x->n[1] - 4) iv = x->n[1] - 4;
+    double wr[4], wv[4], dwr[4], dwv[4];
+    lagrange4(xr - ir, wr);
+    lagrange4(xv - iv, wv);
+    lagrange4_d(xr - ir, dwr);
+    lagrange4_d(xv - iv, dwv);
+    double sr = 0.0, sv = 0.0;
+    for (int b = 0; b < 4; ++b)
+        for (int a = 0; a < 4; ++a) {
+            sr += dwr[a] * wv[b] * U[at(x, ir + a, iv + b, 0)];
+            sv += wr[a] * dwv[b] * U[at(x, ir + a, iv + b, 0)];
+        }
+    double z, Jr, Jv, J2;
+    metric_at(xir, x->lo[0], x->hi[0], x->alpha[0], x->centre[0], &z, &Jr, &J2);
+    metric_at(xiv, x->lo[1], x->hi[1], x->alpha[1], x->centre[1], &z, &Jv, &J2);
+    *d_dr = sr / (x->h[0] * Jr);
+    *d_dv = sv / (x->h[1] * Jv);
+}
+
 int orc_price(const orc_curve* c, const orc_model* m, const orc_grid* g,
               const orc_inst* in, double* price)
 {

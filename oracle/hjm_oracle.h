@@ -115,6 +115,9 @@ void orc_step(const orc_ctx* x, int n, double* U);
 void orc_march(const orc_ctx* x, double* U);
 /* Interpolated value at r = f(0,0), v = v0 on the y = 0 plane. */
 double orc_readout(const orc_ctx* x, const double* U);
+/* dC/dr and dC/dv at the read-out point: derivatives of the read-out
+ * interpolant (divided by the metric Jacobian there). */
+void orc_readout_greeks(const orc_ctx* x, const double* U, double* d_dr, double* d_dv);
 /* Calendar time of step index n (n may be fractional). */
 double orc_time(const orc_ctx* x, double n);
 /* Dirichlet data g(t, r, y). */

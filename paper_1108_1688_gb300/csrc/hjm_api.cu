@@ -247,7 +247,8 @@ struct Group {
     void* U = nullptr;
     void* A = nullptr;
     double* prices = nullptr;
-    double* ind = nullptr;  // rounding indicators
+    double* ind = nullptr;     // rounding indicators
+    double* greeks = nullptr;  // [2 B]: dC/dr, dC/dv at the read-out point
 };
 
 // ------------------------------------------------------------ tracing
@@ -352,7 +353,7 @@ hjm_status group_sequence(const Group& g, size_t elem, cudaStream_t s)
     hjm_status st = run_steps_any(g, elem, 0, g.nsteps, s);
     if (st != HJM_OK) return st;
     TraceScope ts(5, s);
-    CU_TRY(launch_readout(g.t, g.U, elem, g.prices, g.ind, s));
+    CU_TRY(launch_readout(g.t, g.U, elem, g.prices, g.ind, g.greeks, s));
     return HJM_OK;
 }
 
@@ -414,6 +415,16 @@ __global__ void k_scatter(const double* src, const long long* idx, int n, double
     if (t < n) dst[idx[t]] = src[t];
 }
 
+// Pairs: dst[2 idx[t] + c] = src[2 t + c].
+__global__ void k_scatter2(const double* src, const long long* idx, int n, double* dst)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        dst[2 * idx[t]] = src[2 * t];
+        dst[2 * idx[t] + 1] = src[2 * t + 1];
+    }
+}
+
 bool is_device_ptr(const void* p)
 {
     cudaPointerAttributes a;
@@ -427,7 +438,7 @@ bool is_device_ptr(const void* p)
 // Plan the groups of a batch and carve their buffers out of the workspace.
 hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
                 std::vector<Group>& groups, InstParams** d_params, long long** d_idx,
-                double** d_prices_all, double** d_ind_all = nullptr)
+                double** d_prices_all, double** d_ind_all = nullptr, double** d_greeks_all = nullptr)
 {
     // Groups hold at most kMaxGroup instruments (the set-up kernels index
     // instruments with the grid's y dimension).
@@ -456,7 +467,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         gr.gpos = gr.gpos || items[i].model.gamma > 0.0;
     }
     size_t bytes = align256(n * sizeof(InstParams)) + align256(n * sizeof(long long)) +
-                   4 * align256(n * sizeof(double));
+                   4 * align256(n * sizeof(double)) + 2 * align256(2 * n * sizeof(double));
     for (auto& g : groups) {
         const size_t B = g.idx.size();
         const size_t N = (size_t)g.nr * g.nv * g.ny;
@@ -480,6 +491,10 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
     p += align256(n * sizeof(double));
     double* group_ind = (double*)p;
     p += align256(n * sizeof(double));
+    if (d_greeks_all) *d_greeks_all = (double*)p;
+    p += align256(2 * n * sizeof(double));
+    double* group_greeks = (double*)p;
+    p += align256(2 * n * sizeof(double));
     size_t off = 0;
     for (auto& g : groups) {
         const size_t B = g.idx.size();
@@ -498,6 +513,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         g.t.params = *d_params + off;
         g.prices = group_prices + off;
         g.ind = group_ind + off;
+        g.greeks = group_greeks + 2 * off;
         tables_carve(g.t, p, elem);
         p += tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
         off += B;
@@ -519,14 +535,15 @@ Workspace* stream_workspace(cudaStream_t s)
 // workspace) will hold the prices and rounding indicators once the stream
 // reaches them. Caller holds g_mu and has validated the items.
 hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
-                       cudaStream_t s, double** d_prices_out, double** d_ind_out)
+                       cudaStream_t s, double** d_prices_out, double** d_ind_out, double** d_greeks_out = nullptr)
 {
     std::vector<Group> groups;
     InstParams* d_params;
     long long* d_idx;
     double* d_prices;
     double* d_ind;
-    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices, &d_ind);
+    double* d_greeks;
+    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices, &d_ind, &d_greeks);
     if (st != HJM_OK) return st;
     // Parameters in group order, and the scatter map back to caller order.
     std::vector<InstParams> hp;
@@ -554,6 +571,11 @@ hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, siz
     CU_TRY(cudaGetLastError());
     k_scatter<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].ind, d_idx, (int)n, d_ind);
     CU_TRY(cudaGetLastError());
+    if (d_greeks_out) {
+        k_scatter2<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(groups[0].greeks, d_idx, (int)n, d_greeks);
+        CU_TRY(cudaGetLastError());
+        *d_greeks_out = d_greeks;
+    }
     *d_prices_out = d_prices;
     *d_ind_out = d_ind;
     return HJM_OK;
@@ -576,10 +598,14 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
         CU_TRY(cudaEventCreate(&ev1));
         CU_TRY(cudaEventRecord(ev0, s));
     }
-    double *d_prices, *d_ind;
-    hjm_status st = march_batch(ws, items, n, elem, s, &d_prices, &d_ind);
+    double *d_prices, *d_ind, *d_greeks = nullptr;
+    hjm_status st = march_batch(ws, items, n, elem, s, &d_prices, &d_ind, infos ? &d_greeks : nullptr);
     if (st != HJM_OK) return st;
-    std::vector<double> hp, hi;
+    std::vector<double> hp, hi, hg;
+    if (infos) {
+        hg.resize(2 * n);
+        CU_TRY(cudaMemcpyAsync(hg.data(), d_greeks, 2 * n * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     std::vector<int> used(n, prec == HJM_FP64 ? HJM_FP64 : HJM_FP32), esc(n, 0);
     if (sync) {
         hp.resize(n);
@@ -600,11 +626,16 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
             }
         }
         if (!redo.empty()) {
-            st = march_batch(ws, redo.data(), redo.size(), sizeof(double), s, &d_prices, &d_ind);
+            double* d_g64 = nullptr;
+            st = march_batch(ws, redo.data(), redo.size(), sizeof(double), s, &d_prices, &d_ind,
+                             infos ? &d_g64 : nullptr);
             if (st != HJM_OK) return st;
-            std::vector<double> p64(redo.size()), i64(redo.size());
+            std::vector<double> p64(redo.size()), i64(redo.size()), g64(infos ? 2 * redo.size() : 0);
             CU_TRY(cudaMemcpyAsync(p64.data(), d_prices, redo.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
             CU_TRY(cudaMemcpyAsync(i64.data(), d_ind, redo.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (infos)
+                CU_TRY(cudaMemcpyAsync(g64.data(), d_g64, 2 * redo.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                       s));
             CU_TRY(cudaStreamSynchronize(s));
             if (g_trace_on) trace_collect();
             for (size_t q = 0; q < redo.size(); ++q) {
@@ -612,6 +643,10 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
                 hi[where[q]] = i64[q];
                 used[where[q]] = HJM_FP64;
                 esc[where[q]] = 1;
+                if (infos) {
+                    hg[2 * where[q]] = g64[2 * q];
+                    hg[2 * where[q] + 1] = g64[2 * q + 1];
+                }
             }
         }
     }
@@ -636,6 +671,8 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
             infos[i].err_estimate = hi[i];
             infos[i].n_steps = items[i].grid.n_steps;
             infos[i].time_us = ms * 1000.f;
+            infos[i].d_dr = hg[2 * i];
+            infos[i].d_dv = hg[2 * i + 1];
             {
                 const hjm_grid_spec& gs = items[i].grid;
                 const Tile t = tile_for(gs.n_r, gs.n_v, gs.n_y, used[i] == HJM_FP64 ? sizeof(double) : sizeof(float));
@@ -1216,6 +1253,6 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     st = elem == sizeof(float) ? static_march<float>(t, U, A, g.n_steps, gpos, tile, s)
                                : static_march<double>(t, U, A, g.n_steps, gpos, tile, s);
     if (st != HJM_OK) return st;
-    CU_TRY(launch_readout(t, U, elem, price_out, ind, s));
+    CU_TRY(launch_readout(t, U, elem, price_out, ind, nullptr, s));
     return HJM_OK;
 }

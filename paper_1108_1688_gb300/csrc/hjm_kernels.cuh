@@ -143,9 +143,10 @@ cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s);
 // Terminal field U^0 (Section 7.2 cell average for caplets, 1 for bonds).
 cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStream_t s);
 // FP64 readout of every instrument's price into prices[B]; when indicators
-// is not null also the a-posteriori rounding indicator of the march.
+// is not null also the a-posteriori rounding indicator of the march; when
+// greeks is not null also dC/dr and dC/dv at the read-out point ([B][2]).
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           double* indicators, cudaStream_t s);
+                           double* indicators, double* greeks, cudaStream_t s);
 
 // Launch shapes of the three passes for one grid shape (heuristic default or
 // picked by the autotuner).
@@ -168,7 +169,6 @@ bool split_valid(int n, int Pw);
 bool pass23_valid(int nr, int nv, int ny, int p2, size_t elem);
 template <typename T>
 cudaError_t launch_pass23(const March<T>& P, const T* in, const T* Un, T* out, int n, cudaStream_t s);
-
 
 // The three Douglas passes of step n (in/out as documented in hjm.h).
 template <typename T>

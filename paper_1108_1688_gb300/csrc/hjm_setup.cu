@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
 // Lagrange interpolation in the computational coordinates on the 4 x 4
 // nodes nearest the point, kept inside the grid.
 template <typename T>
-__global__ void k_readout(GroupTables g, const T* U, double* prices, double* indicators)
+__global__ void k_readout(GroupTables g, const T* U, double* prices, double* indicators, double* greeks)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.B) return;
@@ -591,6 +591,39 @@ __global__ void k_readout(GroupTables g, const T* U, double* prices, double* ind
         s += wv[c] * row;
     }
     prices[b] = s;
+    if (greeks) {
+        // Derivatives of the interpolant in r and v, divided by the metric
+        // Jacobian at the read-out point (d/dz = (n-1) / J d/ds).
+        double dwr[4], dwv[4];
+        for (int a = 0; a < 4; ++a) {
+            double qr = 0.0, qv = 0.0;
+            for (int l = 0; l < 4; ++l) {
+                if (l == a) continue;
+                double pr = 1.0 / (double)(a - l), pv = pr;
+                for (int c = 0; c < 4; ++c) {
+                    if (c == a || c == l) continue;
+                    pr *= (sr - i0 - c) / (double)(a - c);
+                    pv *= (sv - k0 - c) / (double)(a - c);
+                }
+                qr += pr;
+                qv += pv;
+            }
+            dwr[a] = qr;
+            dwv[a] = qv;
+        }
+        double gr = 0.0, gv = 0.0;
+        for (int c = 0; c < 4; ++c)
+            for (int a = 0; a < 4; ++a) {
+                const double u = (double)Ub[(long long)(k0 + c) * nr + i0 + a];
+                gr += dwr[a] * wv[c] * u;
+                gv += wr[a] * dwv[c] * u;
+            }
+        double z, Jr, Jv, J2;
+        metric(sr / (nr - 1), p.rmin, p.rmax, p.ar, D.centre_r, z, Jr, J2);
+        metric(sv / (nv - 1), 0.0, p.vmax, p.av, p.kv, z, Jv, J2);
+        greeks[2 * b] = gr * (nr - 1) / Jr;
+        greeks[2 * b + 1] = gv * (nv - 1) / Jv;
+    }
     if (indicators) {
         // A-posteriori rounding indicator of the march (reading of the
         // precision-control step): unit roundoff of the march type times the
@@ -687,13 +720,13 @@ cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStre
 }
 
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           double* indicators, cudaStream_t s)
+                           double* indicators, double* greeks, cudaStream_t s)
 {
     const int blocks = (g.B + 63) / 64;
     if (elem == sizeof(float))
-        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices, indicators);
+        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices, indicators, greeks);
     else
-        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators);
+        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators, greeks);
     return cudaGetLastError();
 }
 

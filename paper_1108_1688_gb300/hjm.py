@@ -54,7 +54,8 @@ class hjm_instrument(C.Structure):
 
 class hjm_price_info(C.Structure):
     _fields_ = [("precision_used", C.c_int), ("escalated", C.c_int), ("err_estimate", C.c_double),
-                ("n_steps", C.c_int), ("time_us", C.c_float), ("tile_cfg", C.c_int)]
+                ("n_steps", C.c_int), ("time_us", C.c_float), ("tile_cfg", C.c_int), ("d_dr", C.c_double),
+                ("d_dv", C.c_double)]
 
 
 HJM_TRACE_KINDS = 6

@@ -247,3 +247,26 @@ def test_size_limits(H):
     with pytest.raises(H.HJMError) as ei:
         H.hjm_grid_create(bad["curve"], bad["model"], bad["grid"])
     assert ei.value.status == H.HJM_ERANGE
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("name", ["config1_bond_M2", "caplet_ragged_37x11x13", "caplet_M4_midpoint_NS",
+                                  "bond_gamma09_nr13"])
+def test_greeks_match_oracle(H, orc, name, prec):
+    # dC/dr and dC/dv at the read-out point (derivatives of the FP64 read-out
+    # interpolant of the final field) against the oracle's on its own march.
+    it = CASES[name]()
+    with orc.Ctx(it) as X:
+        U = X.march()
+        want_r, want_v = X.readout_greeks(U)
+        _, Jr, _ = X.axis(0)
+        _, Jv, _ = X.axis(1)
+    p, infos = H.hjm_price_batch([it], prec, infos=True)
+    got_r, got_v = infos[0].d_dr, infos[0].d_dv
+    g = it["grid"]
+    # scale of a derivative of the interpolant: field size x nodes per unit
+    sr = np.max(np.abs(U)) * (g["n_r"] - 1) / np.min(Jr)
+    sv = np.max(np.abs(U)) * (g["n_v"] - 1) / np.min(Jv)
+    rel = 1e-9 if prec == "fp64" else 2e-4
+    assert abs(got_r - want_r) <= rel * sr, (got_r, want_r, sr)
+    assert abs(got_v - want_v) <= rel * sv, (got_v, want_v, sv)

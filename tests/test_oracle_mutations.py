@@ -49,6 +49,10 @@ MUTATIONS = [
      "(-3.0 * u0 + 4.0 * u1 - u2) / h"),
     ("v lines read with r stride", "else if (d == 1) { *i = (int)(line % x->n[0]); *k = p;",
      "else if (d == 1) { *i = (int)(line % x->n[1]); *k = p;"),
+    ("Greek without the metric Jacobian", "*d_dr = sr / (x->h[0] * Jr);", "*d_dr = sr / x->h[0];"),
+    ("derivative weight sign", "double p = 1.0 / (double)(m - l);", "double p = 1.0 / (double)(l - m);"),
+    ("vega from the r weights", "sv += wr[a] * dwv[b] * U[at(x, ir + a, iv + b, 0)];",
+     "sv += dwr[a] * wv[b] * U[at(x, ir + a, iv + b, 0)];"),
 ]
 
 
@@ -83,6 +87,7 @@ def _pins(orc):
     yield lambda: P.test_dirichlet_data(orc)
     yield lambda: P.test_payoff_average_exact_in_r(orc)
     yield lambda: P.test_readout_exact_on_bicubics(orc)
+    yield lambda: P.test_greeks_exact_on_bicubics(orc)
     yield lambda: P.test_config1_bond_price(orc)
     yield lambda: P.test_bond_ns_curve_converges(orc)
     yield lambda: P.test_gaussian_limit_converges_to_closed_form(orc, P.W.flat_curve(0.03))

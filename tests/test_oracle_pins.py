@@ -21,7 +21,11 @@ least one of them:
   Douglas step         equal to the dense product of the three inverses
                        (Section 5.1) on tiny grids (brute force)
   payoff average       equal to brute-force quadrature (Section 7.2)
-  readout              exact on bicubic polynomials
+  readout              exact on bicubic polynomials; its r and v derivatives
+                       (the Greeks) exact on bicubics, the bond's dp/dr
+                       converging at second order to -G(T) P(0,T) (Section
+                       3.1 bond formula at x = y = 0), the bond's dp/dv
+                       vanishing
   march                bond reproduces P(0,T) within 1e-5 (Sections 4.1, 6.1)
                        for many volatilities and the gamma = 0.9 set (Section
                        3.3); Gaussian caplet limit converges to the closed
@@ -654,3 +658,43 @@ def test_invalid_model_and_instrument_rejected(orc):
     with pytest.raises(orc.OracleError):
         orc.price(x)
     assert it["grid"]["n_r"] == 40
+
+
+def test_greeks_exact_on_bicubics(orc):
+    # d/dr and d/dv of the read-out interpolant on a uniform grid reproduce
+    # the derivatives of any field cubic in r and in v.
+    it = W.config1()
+    it["grid"].update(alpha_r=0.0, alpha_v=0.0, alpha_y=0.0, n_r=21, n_v=13, n_y=7)
+    with orc.Ctx(it) as X:
+        r, _, _ = X.axis(0)
+        v, _, _ = X.axis(1)
+        R, Vv = np.meshgrid(r, v)  # [k][i]
+        f = lambda r_, v_: (0.3 + 2 * r_ - 5 * r_ ** 2 + 7 * r_ ** 3) * (1.5 - 0.2 * v_ + 0.05 * v_ ** 2 - 0.01 * v_ ** 3)
+        fr = lambda r_, v_: (2 - 10 * r_ + 21 * r_ ** 2) * (1.5 - 0.2 * v_ + 0.05 * v_ ** 2 - 0.01 * v_ ** 3)
+        fv = lambda r_, v_: (0.3 + 2 * r_ - 5 * r_ ** 2 + 7 * r_ ** 3) * (-0.2 + 0.1 * v_ - 0.03 * v_ ** 2)
+        U = np.empty(X.shape)
+        U[:] = f(R, Vv)[None, :, :]
+        r0, v0 = 0.03, it["model"]["v0"]
+        dr, dv = X.readout_greeks(U)
+        assert abs(X.readout(U) - f(r0, v0)) <= 1e-12 * abs(f(r0, v0))
+        assert abs(dr - fr(r0, v0)) <= 1e-10 * abs(fr(r0, v0))
+        assert abs(dv - fv(r0, v0)) <= 1e-10 * abs(fv(r0, v0))
+
+
+def test_bond_delta_converges_to_closed_form(orc):
+    # dp/dr of the model bond at t = 0, x = y = 0 is -G(T) P(0,T) (Section
+    # 3.1); the march's read-out derivative converges to it at second order,
+    # and the bond does not depend on v.
+    errs, vegas = [], []
+    for nr, ny, nv, ns in ((40, 20, 20, 100), (80, 40, 40, 200)):
+        it = W.config1()
+        it["grid"] = W.default_grid(it["curve"], it["model"], 5.0, nr, ny, nv, ns)
+        with orc.Ctx(it) as X:
+            U = X.march()
+            dr, dv = X.readout_greeks(U)
+        kap, T = it["model"]["kappa"], 5.0
+        exact = -(1.0 - math.exp(-kap * T)) / kap * orc.curve_P(it["curve"], T)
+        errs.append(abs(dr / exact - 1.0))
+        vegas.append(abs(dv))
+    assert errs[1] < 1e-4 and errs[0] / errs[1] > 3.5, errs
+    assert vegas[0] < 2e-6 and vegas[1] < vegas[0], vegas
