@@ -234,6 +234,109 @@ struct Pair<double> {
 //      values (weights: the inverse of the reduced system, precomputed);
 //   4. x = y - x_before V - x_after W, store.
 // Lines whose r node is a Dirichlet face keep the identity system.
+// The per-thread work of k_split_lines on a chunk of L nodes (FULL: L = MC,
+// every loop unpredicated). cl / ul point at the chunk's first node of this
+// lane's column in shared memory (node stride 32).
+template <typename T, int MC, int AXIS, bool FULL>
+__device__ __forceinline__ T split_body(const T* src, const T* usrc, T* dst, int stride, T* cl, T* ul, T* red,
+                                           int lane, int c, int Pw, int L, const typename Pair<T>::type* AB,
+                                           const typename Pair<T>::type* VW, const typename Pair<T>::type* CF,
+                                           const T* CP, bool live, bool dirl)
+{
+    using T2 = typename Pair<T>::type;
+    const int K = 2 * (Pw - 1);
+    // 1. gather (all copies in flight at once)
+    {
+        const T* p = src;
+#pragma unroll
+        for (int m = 0; m < MC; ++m) {
+            if (FULL || m < L) cp_async_elem(cl + m * 32, p);
+            p += stride;
+        }
+        if constexpr (AXIS == 1) {
+            const T* q = usrc;
+#pragma unroll
+            for (int m = 0; m < MC; ++m) {
+                if (FULL || m < L) cp_async_elem(ul + m * 32, q);
+                q += stride;
+            }
+        }
+    }
+    cp_async_commit();
+    cp_async_wait_pending(0);
+    T d[MC];
+#pragma unroll
+    for (int m = 0; m < MC; ++m)
+        if (FULL || m < L) d[m] = cl[m * 32];
+    // 2. chunk solve with the local LU
+    {
+        const T2 f = __ldg(AB);
+        d[0] *= f.y;
+    }
+#pragma unroll
+    for (int m = 1; m < MC; ++m)
+        if (FULL || m < L) {
+            const T2 f = __ldg(AB + m);
+            d[m] = (d[m] - f.x * d[m - 1]) * f.y;
+        }
+    T ylast;
+    if constexpr (FULL) {
+        ylast = d[MC - 1];
+#pragma unroll
+        for (int m = MC - 2; m >= 0; --m) d[m] -= __ldg(CP + m) * d[m + 1];
+    } else {
+        T nxt = T(0);
+        ylast = T(0);
+#pragma unroll
+        for (int m = MC - 1; m >= 0; --m)
+            if (m < L) {
+                const T cpm = m < L - 1 ? __ldg(CP + m) : T(0);
+                d[m] -= cpm * nxt;
+                nxt = d[m];
+                if (m == L - 1) ylast = nxt;
+            }
+    }
+    // 3. reduced system across the chunks of each line
+    if (Pw > 1) {
+        if (c >= 1) red[(2 * c - 1) * 32 + lane] = d[0];
+        if (c + 1 < Pw) red[(2 * c) * 32 + lane] = ylast;
+        __syncthreads();
+        T xb = T(0), xa = T(0);
+        for (int q = 0; q < K; ++q) {
+            const T r = red[q * 32 + lane];
+            const T2 w = __ldg(CF + q);
+            xb += w.x * r;
+            xa += w.y * r;
+        }
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+            if (FULL || m < L) {
+                const T2 f = __ldg(VW + m);
+                d[m] -= f.x * xb + f.y * xa;
+            }
+    }
+    if (!live) return T(0);
+    if (dirl) {
+#pragma unroll
+        for (int m = 0; m < MC; ++m)
+            if (FULL || m < L) d[m] = cl[m * 32];
+    }
+    const T x0 = d[0];  // dU3 at the chunk's first node
+    // 4. store (pass 3: U^n + dU3)
+    T* p = dst;
+#pragma unroll
+    for (int m = 0; m < MC; ++m) {
+        if (FULL || m < L) {
+            if constexpr (AXIS == 1)
+                *p = ul[m * 32] + d[m];
+            else
+                *p = d[m];
+        }
+        p += stride;
+    }
+    return x0;
+}
+
 template <typename T, int MC, int AXIS>
 __global__ void __launch_bounds__(256) k_split_lines(const March<T> P, const T* in, const T* Un, T* out,
                                                      const int step_n)
@@ -268,76 +371,23 @@ __global__ void __launch_bounds__(256) k_split_lines(const March<T> P, const T* 
     const T2* CF = reinterpret_cast<const T2*>(F + 4 * n) + c * K;
     const T* CP = F + 4 * n + 2 * Pw * K + s;
 
-    // 1. gather.
-    const T* src = in + base + s * stride;
-    for (int m = 0; m < L; ++m) cp_async_elem(&col[(s + m) * 32 + lane], src + m * stride);
-    if constexpr (AXIS == 1) {
-        const T* usrc = Un + base + s * stride;
-        for (int m = 0; m < L; ++m) cp_async_elem(&ucol[(s + m) * 32 + lane], usrc + m * stride);
-    }
-    cp_async_commit();
-    cp_async_wait_pending(0);
-    T d[MC];
-#pragma unroll
-    for (int m = 0; m < MC; ++m)
-        if (m < L) d[m] = col[(s + m) * 32 + lane];
-    // 2. chunk solve with the local LU.
-    {
-        const T2 f = __ldg(AB);
-        d[0] *= f.y;
-    }
-#pragma unroll
-    for (int m = 1; m < MC; ++m)
-        if (m < L) {
-            const T2 f = __ldg(AB + m);
-            d[m] = (d[m] - f.x * d[m - 1]) * f.y;
-        }
-    T nxt = T(0), ylast = T(0);
-#pragma unroll
-    for (int m = MC - 1; m >= 0; --m)
-        if (m < L) {
-            const T cpm = m < L - 1 ? __ldg(CP + m) : T(0);
-            d[m] -= cpm * nxt;
-            nxt = d[m];
-            if (m == L - 1) ylast = nxt;
-        }
-    // 3. reduced system across the chunks of each line.
-    if (Pw > 1) {
-        if (c >= 1) red[(2 * c - 1) * 32 + lane] = d[0];
-        if (c + 1 < Pw) red[(2 * c) * 32 + lane] = ylast;
-        __syncthreads();
-        T xb = T(0), xa = T(0);
-        for (int q = 0; q < K; ++q) {
-            const T r = red[q * 32 + lane];
-            const T2 w = __ldg(CF + q);
-            xb += w.x * r;
-            xa += w.y * r;
-        }
-#pragma unroll
-        for (int m = 0; m < MC; ++m)
-            if (m < L) {
-                const T2 f = __ldg(VW + m);
-                d[m] -= f.x * xb + f.y * xa;
-            }
-    }
-    if (!live) return;
     const int* fl = P.fl + (size_t)b * FL_N;
-    if (i == nr - 1 || (i == 0 && fl[FL_RLO_DIR])) {  // Dirichlet line: identity system
-#pragma unroll
-        for (int m = 0; m < MC; ++m)
-            if (m < L) d[m] = col[(s + m) * 32 + lane];
-    }
-    if constexpr (AXIS == 1)
-        if (c == 0) note_increment(P, fl, b, i, o, step_n, d[0]);  // dU3 at j = 0
+    const bool dirl = i == nr - 1 || (i == 0 && fl[FL_RLO_DIR]);  // Dirichlet line: identity system
+    const T* src = in + base + s * stride;
     T* dst = out + base + s * stride;
-#pragma unroll
-    for (int m = 0; m < MC; ++m)
-        if (m < L) {
-            if constexpr (AXIS == 1)
-                dst[m * stride] = ucol[(s + m) * 32 + lane] + d[m];
-            else
-                dst[m * stride] = d[m];
-        }
+    const T* usrc = AXIS == 1 ? Un + base + s * stride : nullptr;
+    // every chunk holds exactly MC nodes: unpredicated body (uniform in the
+    // CTA, which matters for the barrier inside)
+    const bool full = n % Pw == 0 && n / Pw == MC;
+    T x0;
+    if (full)
+        x0 = split_body<T, MC, AXIS, true>(src, usrc, dst, stride, col + s * 32 + lane, ucol + s * 32 + lane, red,
+                                           lane, c, Pw, MC, AB, VW, CF, CP, live, dirl);
+    else
+        x0 = split_body<T, MC, AXIS, false>(src, usrc, dst, stride, col + s * 32 + lane, ucol + s * 32 + lane, red,
+                                            lane, c, Pw, L, AB, VW, CF, CP, live, dirl);
+    if constexpr (AXIS == 1)
+        if (live && c == 0) note_increment(P, fl, b, i, o, step_n, x0);  // dU3 at j = 0
 }
 
 static size_t split_smem(int n, int Pw, int axis, size_t elem)
