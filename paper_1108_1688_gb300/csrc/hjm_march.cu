@@ -4,19 +4,22 @@
 //   pass 1  dU0 = dt F(U^n; t^n)           explicit operator, Eq. (1) in the
 //                                           metric form of Section 4.3, with
 //                                           the r-v mixed term (Section 5)
-//           (I - theta dt A_r) dU1 = dU0   fused: one warp per r line
-//   pass 2  (I - theta dt A_v) dU2 = dU1   one thread per v line
-//   pass 3  (I - theta dt A_y) dU3 = dU2   one thread per y line, fused
-//           U^{n+1} = U^n + dU3            with the update
+//           (I - theta dt A_r) dU1 = dU0   fused: lane segments per r line
+//   pass 2  (I - theta dt A_v) dU2 = dU1   strided v lines
+//   pass 3  (I - theta dt A_y) dU3 = dU2   strided y lines, fused with
+//           U^{n+1} = U^n + dU3            the update
 //
-// Passes 2 and 3 give each thread one strided line; the line is gathered
-// into shared memory with asynchronous copies (one 4- or 8-byte copy per
-// node, coalesced across the 32 consecutive r nodes of a warp, issued
-// all at once, so a warp has its whole tile in flight) and solved by the
-// Thomas algorithm (Section 5) in place, with the LU factors of the line-
-// invariant systems precomputed by the set-up kernel. Pass 3 gathers U^n the
-// same way for the update (measured faster than reading it a few rows ahead
-// during the back substitution).
+// The strided lines run in one of three ways (chosen per grid shape):
+//   k_pass2 / k_pass3   one lane per line: the line is gathered into shared
+//                       memory with asynchronous copies (coalesced across
+//                       the 32 consecutive r nodes of a warp, all in flight
+//                       at once) and solved by Thomas (Section 5) with the
+//                       precomputed LU factors of the line-invariant systems
+//                       (pass 3 stages U^n the same way);
+//   k_split_lines       2-8 warps per line, one chunk each, joined through a
+//                       precomputed reduced system (spike partition);
+//   k_pass23            passes 2 and 3 together on a shared-memory slab of
+//                       8 r nodes when its (v, y) plane fits.
 #include "hjm_kernels.cuh"
 
 namespace hjm {
@@ -59,13 +62,24 @@ template <typename T>
 __device__ __forceinline__ T gather_forward(T* col, int lane, const T* src, int stride, int n,
                                             const T* __restrict__ sub, const T* __restrict__ im)
 {
-    for (int kk = 0; kk < n; ++kk) cp_async_elem(&col[kk * 32 + lane], src + kk * stride);
+    {
+        const T* p = src;
+        T* c = col + lane;
+#pragma unroll 8
+        for (int kk = 0; kk < n; ++kk) {
+            cp_async_elem(c, p);
+            c += 32;
+            p += stride;
+        }
+    }
     cp_async_commit();
     cp_async_wait_pending(0);
     T dp = T(0);
+    T* c = col + lane;
+#pragma unroll 4
     for (int kk = 0; kk < n; ++kk) {
-        dp = (col[kk * 32 + lane] - __ldg(sub + kk) * dp) * __ldg(im + kk);
-        col[kk * 32 + lane] = dp;
+        dp = (c[kk * 32] - __ldg(sub + kk) * dp) * __ldg(im + kk);
+        c[kk * 32] = dp;
     }
     return dp;
 }
@@ -111,10 +125,14 @@ __global__ void __launch_bounds__(32) k_pass2(const March<T> P, const T* in, T* 
     const T* __restrict__ cpr = sub + nv;
     const T* __restrict__ im = cpr + nv;
     T x = gather_forward<T>(col, lane, src, nr, nv, sub, im);
-    dst[(nv - 1) * nr] = x;
+    T* p = dst + (nv - 1) * nr;
+    *p = x;
+    const T* c = col + lane;
+#pragma unroll 4
     for (int kk = nv - 2; kk >= 0; --kk) {
-        x = col[kk * 32 + lane] - __ldg(cpr + kk) * x;
-        dst[kk * nr] = x;
+        x = c[kk * 32] - __ldg(cpr + kk) * x;
+        p -= nr;
+        *p = x;
     }
 }
 
@@ -145,9 +163,20 @@ __global__ void __launch_bounds__(32) k_pass3(const March<T> P, const T* in, con
     const int* fl = P.fl + (size_t)b * FL_N;
     // Both columns in flight at once (U^n is staged too: the update is in
     // place, so it cannot be read from global memory behind the stores).
-    for (int jj = 0; jj < ny; ++jj) {
-        cp_async_elem(&col[jj * 32 + lane], src + jj * stride);
-        cp_async_elem(&ucol[jj * 32 + lane], usrc + jj * stride);
+    {
+        const T* p = src;
+        const T* q = usrc;
+        T* c = col + lane;
+        T* u = ucol + lane;
+#pragma unroll 8
+        for (int jj = 0; jj < ny; ++jj) {
+            cp_async_elem(c, p);
+            cp_async_elem(u, q);
+            c += 32;
+            u += 32;
+            p += stride;
+            q += stride;
+        }
     }
     cp_async_commit();
     cp_async_wait_pending(0);
@@ -161,15 +190,21 @@ __global__ void __launch_bounds__(32) k_pass3(const March<T> P, const T* in, con
         const T* __restrict__ cpr = sub + ny;
         const T* __restrict__ im = cpr + ny;
         T dp = T(0);
+        T* c = col + lane;
+        const T* u = ucol + lane;
+#pragma unroll 4
         for (int jj = 0; jj < ny; ++jj) {
-            dp = (col[jj * 32 + lane] - __ldg(sub + jj) * dp) * __ldg(im + jj);
-            col[jj * 32 + lane] = dp;
+            dp = (c[jj * 32] - __ldg(sub + jj) * dp) * __ldg(im + jj);
+            c[jj * 32] = dp;
         }
         T x = dp;
-        dst[(ny - 1) * stride] = ucol[(ny - 1) * 32 + lane] + x;
+        T* p = dst + (ny - 1) * stride;
+        *p = u[(ny - 1) * 32] + x;
+#pragma unroll 4
         for (int jj = ny - 2; jj >= 0; --jj) {
-            x = col[jj * 32 + lane] - __ldg(cpr + jj) * x;
-            dst[jj * stride] = ucol[jj * 32 + lane] + x;
+            x = c[jj * 32] - __ldg(cpr + jj) * x;
+            p -= stride;
+            *p = u[jj * 32] + x;
         }
         note_increment(P, fl, b, i, k, n, x);
         return;
