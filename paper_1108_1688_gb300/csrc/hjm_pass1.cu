@@ -7,17 +7,16 @@
 // r lines are contiguous in memory. A line is owned by a segment of S lanes
 // of a warp (S = 8, 16 or 32; 32/S lines per warp side by side); lane l of
 // the segment holds M consecutive nodes e = l*M .. l*M+M-1, loaded with
-// 16-byte vector loads. The per-node r factors of the operator (7 tables)
-// are loaded once per CTA (a CTA never spans two instruments) into shared
-// memory, laid out so every read is conflict-free (or, as a variant, into
-// registers), and reused for every line the CTA processes. The line system is
-// solved by a partition method: each lane eliminates its chunk down to
-// equations in its first and last unknowns, the S interface equations are
-// solved by parallel cyclic reduction over width-S warp shuffles, and each
-// lane back-substitutes.
-#include <stdio.h>
-#include <stdlib.h>
-
+// 16-byte vector loads (k_pass1), or from a shared-memory ring of staged y
+// planes (k_pass1s). The per-node r factors of the operator (7 tables) are
+// loaded once per CTA (a CTA never spans two instruments) into shared
+// memory, laid out so the lanes' 16-byte reads are conflict-free, and reused
+// for every line the CTA processes. In FP32 the per-node arithmetic runs on
+// node pairs with the paired FP32 instructions. The line system is solved by
+// a partition method: each lane eliminates its chunk down to equations in
+// its first and last unknowns, the S interface equations are solved by
+// parallel cyclic reduction over width-S warp shuffles, and each lane
+// back-substitutes.
 #include "hjm_kernels.cuh"
 
 namespace hjm {
