@@ -13,6 +13,10 @@
  *   Discretisation ........... Section 5 (theta scheme, centred differences,
  *                              tridiagonal operators, delta form)
  *   Douglas ADI .............. Section 5.1
+ *   Craig-Sneyd family ....... Section 5.1 (the paper names Craig-Sneyd as
+ *                              the alternative it tried; the modified CS and
+ *                              Hundsdorfer-Verwer schemes are those of the
+ *                              In 't Hout-Welfert work it cites)
  *   Softened payoff .......... Section 7.2 (control-volume average)
  *   y faces .................. Section 7.3 (first/second order one-sided)
  *   Exact bond (pin) ......... Section 3.1 bond formula, Section 4.1
@@ -48,6 +52,13 @@
  *       r integral is closed form, the y integral 8-point Gauss-Legendre.
  *   R12 r^gamma is taken as 1 when gamma == 0 (any r), so negative rates are
  *       allowed in the Gaussian case only.
+ *   R13 Craig-Sneyd family: a second explicit stage and a second sweep of
+ *       the three line solves, as In 't Hout and Welfert define CS, modified
+ *       CS and Hundsdorfer-Verwer. Every explicit operator of such a step is
+ *       taken at t^{n+1/2} (the operator frozen over the step, whatever
+ *       explicit_midpoint says), which keeps the schemes second order with
+ *       the time-dependent drift; the implicit stages use the same line
+ *       operators as the Douglas stages (R5, R6, R8).
  */
 #include "hjm_oracle.h"
 
@@ -213,6 +224,7 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
     if (g->theta_adi < 0.0 || g->theta_adi > 1.0) return 1;
     if (g->y_boundary_order != 1 && g->y_boundary_order != 2) return 1;
     if (g->explicit_midpoint != 0 && g->explicit_midpoint != 1) return 1;
+    if (g->scheme < 0 || g->scheme > 3) return 1;
     if (!(in->T > 0.0)) return 1;
     if (in->kind != 0 && in->kind != 1) return 1;
     double r0 = orc_curve_f(c, 0.0);
@@ -420,10 +432,12 @@ void orc_apply_F(const orc_ctx* x, double t, const double* U, double* F)
 /* Delta U^0 = dt F(U^n; t^n) (Section 5.1, first Douglas stage, reading R6);
  * on Dirichlet nodes the increment that lands on g(t^{n+1}) (reading R8).
  * With explicit_midpoint set, F is taken at t^{n+1/2} instead, the time at
- * which the implicit operators are taken (an option, not the paper's form). */
+ * which the implicit operators are taken (an option, not the paper's form);
+ * the Craig-Sneyd family always takes it there (R13). */
 void orc_explicit(const orc_ctx* x, int n, const double* U, double* dU0)
 {
-    double t = orc_time(x, x->g.explicit_midpoint ? n + 0.5 : n), t1 = orc_time(x, n + 1);
+    int mid = x->g.explicit_midpoint || x->g.scheme != 0;
+    double t = orc_time(x, mid ? n + 0.5 : n), t1 = orc_time(x, n + 1);
     orc_apply_F(x, t, U, dU0);
     for (int j = 0; j < x->n[2]; ++j)
         for (int k = 0; k < x->n[1]; ++k)
@@ -567,24 +581,59 @@ long orc_solve_dir(const orc_ctx* x, int d, double t, const double* rhs, double*
 
 /* ------------------------------------------------------------ Douglas */
 
-/* One Douglas ADI step (Section 5.1, readings R5, R6):
- *   dU0 = dt F(U^n; t^n)
- *   (I - theta dt A_r(t^{n+1/2})) dU1 = dU0
- *   (I - theta dt A_v(t^{n+1/2})) dU2 = dU1
- *   (I - theta dt A_y(t^{n+1/2})) dU3 = dU2
- *   U^{n+1} = U^n + dU3 */
+/* One ADI step n -> n+1 in place. Douglas (Section 5.1, readings R5, R6):
+ *   Y0 = U^n + dt F(U^n)                       (dU0 of orc_explicit)
+ *   Yd = Y(d-1) + theta dt A_d (Yd - U^n),  d = r, v, y
+ *        i.e. (I - theta dt A_d(t^{n+1/2})) (Yd - U^n) = Y(d-1) - U^n
+ *   U^{n+1} = Yy.
+ * The Craig-Sneyd family (R13) continues from Y0 and Yy (= Y3):
+ *   CS:  Z0 = Y0 + 1/2 dt (A_0 Y3 - A_0 U^n)
+ *   MCS: Z0 = Y0 + theta dt (A_0 Y3 - A_0 U^n)
+ *               + (1/2 - theta) dt (F(Y3) - F(U^n))
+ *   HV:  Z0 = Y0 + 1/2 dt (F(Y3) - F(U^n))
+ *   Zd = Z(d-1) + theta dt A_d (Zd - B),  B = U^n (CS, MCS) or Y3 (HV)
+ *   U^{n+1} = Zy.
+ * A_0 is the mixed term, F the full explicit operator (both zero on
+ * Dirichlet nodes, where Y0 = Y3 = Z0 = g(t^{n+1})). */
 void orc_step(const orc_ctx* x, int n, double* U)
 {
     long N = orc_n_points(x);
-    double* w0 = (double*)malloc(sizeof(double) * N * 2);
-    double* w1 = w0 + N;
-    double th = orc_time(x, n + 0.5);
-    orc_explicit(x, n, U, w0);
-    orc_solve_dir(x, 0, th, w0, w1);
-    orc_solve_dir(x, 1, th, w1, w0);
-    orc_solve_dir(x, 2, th, w0, w1);
-    for (long p = 0; p < N; ++p) U[p] += w1[p];
-    free(w0);
+    int sch = x->g.scheme;
+    double th = orc_time(x, n + 0.5), dt = x->dt, theta = x->g.theta_adi;
+    double* w = (double*)malloc(sizeof(double) * N * 5);
+    double *z = w, *a = w + N, *b = w + 2 * N, *y3 = w + 3 * N, *f = w + 4 * N;
+    /* z = Y0 - U^n; a = Y3 - U^n after the three solves */
+    orc_explicit(x, n, U, z);
+    orc_solve_dir(x, 0, th, z, a);
+    orc_solve_dir(x, 1, th, a, b);
+    orc_solve_dir(x, 2, th, b, a);
+    if (sch == 0) {
+        for (long p = 0; p < N; ++p) U[p] += a[p];
+        free(w);
+        return;
+    }
+    for (long p = 0; p < N; ++p) y3[p] = U[p] + a[p];
+    /* z = Z0 - U^n */
+    if (sch == 1 || sch == 2) {
+        double c = sch == 1 ? 0.5 : theta;
+        orc_apply_dir(x, 3, th, y3, b);
+        orc_apply_dir(x, 3, th, U, f);
+        for (long p = 0; p < N; ++p) z[p] += c * dt * (b[p] - f[p]);
+    }
+    if (sch == 2 || sch == 3) {
+        double c = sch == 2 ? 0.5 - theta : 0.5;
+        orc_apply_F(x, th, y3, b);
+        orc_apply_F(x, th, U, f);
+        for (long p = 0; p < N; ++p) z[p] += c * dt * (b[p] - f[p]);
+    }
+    /* z = Z0 - B, then the three solves give Zy - B */
+    if (sch == 3)
+        for (long p = 0; p < N; ++p) z[p] -= a[p];
+    orc_solve_dir(x, 0, th, z, b);
+    orc_solve_dir(x, 1, th, b, f);
+    orc_solve_dir(x, 2, th, f, b);
+    for (long p = 0; p < N; ++p) U[p] = (sch == 3 ? y3[p] : U[p]) + b[p];
+    free(w);
 }
 
 /* ------------------------------------------------------- terminal field */

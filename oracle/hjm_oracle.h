@@ -55,6 +55,8 @@ typedef struct {
     double theta_adi;         /* theta of the theta scheme; 0.5 = CN */
     int y_boundary_order;     /* 1 or 2: one-sided order on the y faces in F */
     int explicit_midpoint;    /* 0: F at t^n (paper); 1: F at t^{n+1/2} */
+    int scheme;               /* ADI scheme: 0 Douglas (Section 5.1), 1 Craig-Sneyd,
+                                 2 modified Craig-Sneyd, 3 Hundsdorfer-Verwer */
 } orc_grid;
 
 /* Instrument: kind 0 zero-coupon bond maturing at T; kind 1 caplet with
@@ -109,7 +111,7 @@ long orc_solve_dir(const orc_ctx* x, int d, double t, const double* rhs, double*
  * lower axis fastest). len = n_d. */
 void orc_line_matrix(const orc_ctx* x, int d, double t, long line,
                      double* sub, double* diag, double* sup);
-/* One Douglas step n -> n+1 in place. */
+/* One ADI step n -> n+1 in place (the grid's scheme). */
 void orc_step(const orc_ctx* x, int n, double* U);
 /* Terminal field followed by all n_steps steps. */
 void orc_march(const orc_ctx* x, double* U);

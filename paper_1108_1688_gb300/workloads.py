@@ -77,7 +77,7 @@ def curve_level_bound(curve):
 
 def default_grid(curve, mdl, T, n_r, n_y, n_v, n_steps, *, r_width_sd=7.0,
                  alpha_frac=(ALPHA_FRAC_R, ALPHA_FRAC_V, ALPHA_FRAC_Y),
-                 theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0, r_inf=None):
+                 theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0, scheme=0, r_inf=None):
     """Grid specification following the domain recipe in the module docstring."""
     kap = mdl["kappa"]
     v_max = max(5.0, 1.0 + 10.0 * mdl["epsilon"] / math.sqrt(2.0 * max(mdl["theta"], 1e-12)))
@@ -101,7 +101,7 @@ def default_grid(curve, mdl, T, n_r, n_y, n_v, n_steps, *, r_width_sd=7.0,
                 alpha_y=alpha_frac[2] * y_max,
                 k_r=0.0, k_v=1.0, center_r_on_strike=1,
                 theta_adi=float(theta_adi), y_boundary_order=int(y_boundary_order),
-                explicit_midpoint=int(explicit_midpoint))
+                explicit_midpoint=int(explicit_midpoint), scheme=int(scheme))
 
 
 def item(curve, mdl, grid, inst):
@@ -204,7 +204,7 @@ def surrogate_label_grid(n_r=96, n_y=48, n_v=48, n_steps=192):
     domain of each label from its draw)."""
     return dict(n_r=n_r, n_y=n_y, n_v=n_v, n_steps=n_steps, r_min=0.0, r_max=0.0, y_max=0.0, v_max=0.0,
                 alpha_r=0.0, alpha_y=0.0, alpha_v=0.0, k_r=0.0, k_v=1.0, center_r_on_strike=1,
-                theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0)
+                theta_adi=0.5, y_boundary_order=2, explicit_midpoint=0, scheme=0)
 
 
 def surrogate_draws(n, seed, box_lo=SURROGATE_BOX_LO, box_hi=SURROGATE_BOX_HI, out_of_box=0.0):

@@ -36,8 +36,8 @@ MUTATIONS = [
     ("theta dropped in Douglas stages", "double w = x->g.theta_adi * x->dt;", "double w = x->dt;"),
     ("Thomas uses the wrong sub-diagonal", "dp[i] = (d[i] - a[i] * dp[i - 1]) / m;",
      "dp[i] = (d[i] - a[i - 1] * dp[i - 1]) / m;"),
-    ("v and y solves swapped", "orc_solve_dir(x, 1, th, w1, w0);\n    orc_solve_dir(x, 2, th, w0, w1);",
-     "orc_solve_dir(x, 2, th, w1, w0);\n    orc_solve_dir(x, 1, th, w0, w1);"),
+    ("v and y solves swapped", "orc_solve_dir(x, 1, th, a, b);\n    orc_solve_dir(x, 2, th, b, a);",
+     "orc_solve_dir(x, 2, th, a, b);\n    orc_solve_dir(x, 1, th, b, a);"),
     ("Dirichlet data at t^n", "dU0[p] = orc_dirichlet(x, t1,", "dU0[p] = orc_dirichlet(x, t,"),
     ("payoff kink sign", "double rstar = log(DA) / G;", "double rstar = -log(DA) / G;"),
     ("Delta_M without the strike", "x->DM = 1.0 + (in->TM - in->T) * x->K;", "x->DM = 1.0 + (in->TM - in->T);"),
@@ -53,6 +53,17 @@ MUTATIONS = [
     ("derivative weight sign", "double p = 1.0 / (double)(m - l);", "double p = 1.0 / (double)(l - m);"),
     ("vega from the r weights", "sv += wr[a] * dwv[b] * U[at(x, ir + a, iv + b, 0)];",
      "sv += dwr[a] * wv[b] * U[at(x, ir + a, iv + b, 0)];"),
+    ("CS mixed correction with weight 1", "double c = sch == 1 ? 0.5 : theta;",
+     "double c = sch == 1 ? 1.0 : theta;"),
+    ("MCS mixed correction with weight 1/2", "double c = sch == 1 ? 0.5 : theta;", "double c = 0.5;"),
+    ("HV correction with weight theta", "double c = sch == 2 ? 0.5 - theta : 0.5;",
+     "double c = sch == 2 ? 0.5 - theta : theta;"),
+    ("MCS second sweep about Y3", "(sch == 3 ? y3[p] : U[p])", "(sch >= 2 ? y3[p] : U[p])"),
+    ("HV second sweep about U^n",
+     "if (sch == 3)\n        for (long p = 0; p < N; ++p) z[p] -= a[p];",
+     "if (sch == 4)\n        for (long p = 0; p < N; ++p) z[p] -= a[p];"),
+    ("CS family explicit operators at t^n", "int mid = x->g.explicit_midpoint || x->g.scheme != 0;",
+     "int mid = x->g.explicit_midpoint;"),
 ]
 
 
@@ -91,6 +102,10 @@ def _pins(orc):
     yield lambda: P.test_config1_bond_price(orc)
     yield lambda: P.test_bond_ns_curve_converges(orc)
     yield lambda: P.test_gaussian_limit_converges_to_closed_form(orc, P.W.flat_curve(0.03))
+    yield lambda: P.test_craig_sneyd_reductions(orc)
+    for sch in range(4):
+        yield lambda sch=sch: P.test_craig_sneyd_family_time_order(orc, sch)
+    yield lambda: P.test_craig_sneyd_family_second_order_with_time_dependent_drift(orc, 1)
 
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])

@@ -32,6 +32,13 @@ least one of them:
                        form; observed space-time order >= 1.8; first- and
                        second-order y faces agree (Section 7.3); price smooth
                        in strike after softening (Section 7.2)
+  Craig-Sneyd family   CS without the mixed term is Douglas, modified CS at
+                       theta = 1/2 is CS (both exact reductions of the
+                       schemes' definitions); with a strong mixed term
+                       Douglas is first order in time and CS, modified CS and
+                       Hundsdorfer-Verwer second order, also with a
+                       time-dependent drift (Section 5.1 and the
+                       In 't Hout-Welfert analysis it cites)
 """
 import math
 
@@ -630,10 +637,70 @@ def test_softened_price_is_smooth_in_strike(orc):
     assert np.max(d2) < 0.1 * np.max(np.abs(errs)), (np.max(d2), np.max(np.abs(errs)))
 
 
+# ------------------------------------------------------ Craig-Sneyd family
+
+SCHEME_THETA = {0: 0.5, 1: 0.5, 2: 1.0 / 3.0, 3: 0.5 + math.sqrt(3.0) / 6.0}
+
+
+def test_craig_sneyd_reductions(orc):
+    # Exact reductions of the definitions (Section 5.1 names Craig-Sneyd as the
+    # alternative to Douglas): without the mixed term (rho = 0) the CS
+    # correction stage vanishes and CS is Douglas; at theta = 1/2 the modified
+    # CS correction (1/2 - theta) vanishes and MCS is CS.
+    c = W.ns_curve(0.03, -0.01, 0.015, 2.0)
+    m0 = W.model(0.1, 0.02, 0.0, 1.0, 0.8, 0.0)
+    g = dict(theta_adi=0.5, explicit_midpoint=1)
+    it = lambda m, sch: W.item(c, m, W.default_grid(c, m, 2.0, 20, 10, 12, 12, scheme=sch, **g), W.caplet(2.0, 2.5))
+    p_do, p_cs = orc.price(it(m0, 0)), orc.price(it(m0, 1))
+    assert abs(p_cs - p_do) <= 1e-13 * abs(p_do), (p_cs, p_do)
+    m1 = W.model(0.1, 0.02, 0.0, 1.0, 0.8, -0.8)
+    p_cs, p_mcs, p_do = orc.price(it(m1, 1)), orc.price(it(m1, 2)), orc.price(it(m1, 0))
+    assert abs(p_mcs - p_cs) <= 1e-13 * abs(p_cs), (p_mcs, p_cs)
+    assert abs(p_cs - p_do) > 1e-9  # the mixed term does make them differ
+
+
+def _time_errors(orc, curve, scheme, midpoint, steps=(8, 16, 32), ref_steps=512):
+    m = W.model(0.1, 0.02, 0.0, 1.0, 1.0, -0.9)
+    th = SCHEME_THETA[scheme]
+    it = lambda ns: W.item(curve, m, W.default_grid(curve, m, 2.0, 24, 16, 16, ns, theta_adi=th, scheme=scheme,
+                                                    explicit_midpoint=midpoint), W.caplet(2.0, 2.5))
+    ref = orc.price(it(ref_steps))
+    return [abs(orc.price(it(ns)) - ref) for ns in steps]
+
+
+@pytest.mark.parametrize("scheme", [0, 1, 2, 3])
+def test_craig_sneyd_family_time_order(orc, scheme):
+    # Strong correlation (rho = -0.9, epsilon = 1) on a fixed spatial grid,
+    # flat curve, errors against 512 steps: Douglas with the explicit mixed
+    # term is first order in time (error ratio about 2 per halving), CS,
+    # modified CS (theta = 1/3) and Hundsdorfer-Verwer (theta = 1/2 + sqrt(3)/6)
+    # are second order (ratio about 4).
+    e = _time_errors(orc, W.flat_curve(0.03), scheme, 1)
+    ratios = [e[i] / e[i + 1] for i in range(len(e) - 1)]
+    if scheme == 0:
+        assert all(1.6 < r < 2.8 for r in ratios), (e, ratios)
+    else:
+        assert all(r > 3.3 for r in ratios), (e, ratios)
+
+
+@pytest.mark.parametrize("scheme", [1, 3])
+def test_craig_sneyd_family_second_order_with_time_dependent_drift(orc, scheme):
+    # Nelson-Siegel curve (time-dependent drift a(t) in mu_r) with the grid's
+    # explicit_midpoint = 0: the CS family still takes its explicit operators
+    # at t^{n+1/2} and stays second order, where Douglas with F at t^n is
+    # first order.
+    c = W.ns_curve(0.03, -0.02, 0.02, 1.5)
+    e = _time_errors(orc, c, scheme, 0)
+    assert all(e[i] / e[i + 1] > 3.3 for i in range(len(e) - 1)), e
+    d = _time_errors(orc, c, 0, 0)
+    assert all(d[i] / d[i + 1] < 2.8 for i in range(len(d) - 1)), d
+
+
 # ------------------------------------------------------------ validation
 
 @pytest.mark.parametrize("field,value", [("n_r", 4), ("n_steps", 0), ("y_boundary_order", 3),
-                                         ("theta_adi", 1.5), ("explicit_midpoint", 2)])
+                                         ("theta_adi", 1.5), ("explicit_midpoint", 2), ("scheme", 4),
+                                         ("scheme", -1)])
 def test_invalid_grid_rejected(orc, field, value):
     it = W.with_grid(W.config1(), **{field: value})
     with pytest.raises(orc.OracleError):
