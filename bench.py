@@ -44,11 +44,27 @@ KERNEL_KINDS = ("setup", "terminal", "pass1", "pass2", "pass3", "readout")
 # step as three line passes): pass 1 reads U^n and writes dU1, pass 2 reads
 # dU1 and writes dU2, pass 3 reads dU2 and U^n and writes U^{n+1}.
 WORDS_PER_POINT = {"pass1": 2, "pass2": 2, "pass3": 3}
+# Craig-Sneyd family (--scheme cs|mcs|hv): a Douglas stage into Y3 (the same
+# words) and a correction stage whose pass 1 also reads Y3 (3 words), so the
+# pass-1 launches average 2.5 words per point.
+WORDS_PER_POINT_CS = {"pass1": 2.5, "pass2": 2, "pass3": 3}
+SCHEMES = {"douglas": (0, 0.5), "cs": (1, 0.5), "mcs": (2, 1.0 / 3.0), "hv": (3, 0.5 + 3 ** 0.5 / 6.0)}
 
 
-def workload_items(name, instruments=None, march_steps=None):
+def workload_items(name, instruments=None, march_steps=None, scheme="douglas"):
     """Items of a workload. instruments / march_steps shrink config2 for
-    profiling captures (they change the workload named in the JSON line)."""
+    profiling captures (they change the workload named in the JSON line);
+    scheme other than douglas switches every item to that ADI scheme."""
+    items, desc = _workload_items(name, instruments, march_steps)
+    sch, theta = SCHEMES[scheme]
+    if sch:
+        for x in items:
+            x["grid"].update(scheme=sch, theta_adi=theta)
+        desc += ", %s scheme (theta %.4g)" % (scheme.upper(), theta)
+    return items, desc
+
+
+def _workload_items(name, instruments=None, march_steps=None):
     from paper_1108_1688_gb300 import workloads as W
     if name == "config2":
         n = instruments or 100
@@ -233,7 +249,7 @@ def cpu_baseline(items, budget_s=12.0, max_steps=200):
             n += 1
         dt = time.perf_counter() - t0
     return {"value": n * pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "instrument 0 of the workload: set-up and the first %d of %d Douglas steps "
+            "sample": "instrument 0 of the workload: set-up and the first %d of %d ADI steps "
                       "on %dx%dx%d (serial FP64 C oracle)" % (n, g["n_steps"], g["n_r"], g["n_y"], g["n_v"]),
             "seconds": dt}
 
@@ -246,7 +262,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    items, desc = workload_items(args.workload, args.instruments, args.march_steps)
+    items, desc = workload_items(args.workload, args.instruments, args.march_steps, args.scheme)
     it = items[0]
     g = it["grid"]
     pts = g["n_r"] * g["n_v"] * g["n_y"]
@@ -270,9 +286,9 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": desc, "sample": "%d Douglas step(s) of instrument 0 per step" % per_step},
+        "config": {"workload": desc, "sample": "%d ADI step(s) of instrument 0 per step" % per_step},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d Douglas step(s) of instrument 0 (%dx%dx%d) per step, serial FP64 C"
+                         "sample": "%d ADI step(s) of instrument 0 (%dx%dx%d) per step, serial FP64 C"
                                    % (per_step, g["n_r"], g["n_y"], g["n_v"])},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -387,7 +403,8 @@ def run_ours(args):
     barrier(world)
     from paper_1108_1688_gb300 import hjm
 
-    items, desc = workload_items(args.workload, args.instruments, args.march_steps)
+    items, desc = workload_items(args.workload, args.instruments, args.march_steps, args.scheme)
+    scheme = SCHEMES[args.scheme][0]
     prec = args.precision
     arr = hjm.make_items(items)
     import ctypes
@@ -474,23 +491,28 @@ def run_ours(args):
         # group; for a single-shape workload that is all of them
         shapes = {(x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], x["grid"]["n_steps"]) for x in items}
         pts_launch = total_points / len(shapes)
-        alg = WORDS_PER_POINT[dom] * elem * pts_launch
+        alg = (WORDS_PER_POINT_CS if scheme else WORDS_PER_POINT)[dom] * elem * pts_launch
         peak, peak_kind = measured_peaks()
         achieved = alg / (avg_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "kernel": kernel_name(dom, tile_used), "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
-                "traffic": recorded_traffic(dom, "%s-%s" % (args.workload, prec), pts_launch,
+                "traffic": recorded_traffic(dom, "%s-%s%s" % (args.workload, prec, "-" + args.scheme if scheme else ""),
+                                            pts_launch,
                                             ",".join(map(str, tile_used)) if tile_used else None)}
     shares = {k: round(trace[k][1] / max(sum(v[1] for v in trace.values()), 1e-12), 4) for k in KERNEL_KINDS}
 
-    # step launches: set-up, terminal, 3 per Douglas step, read-out per shape
-    # group, plus the scatter of prices
+    # step launches: set-up, terminal, per ADI step 3 per stage (2 with the
+    # strided passes fused) and 2 stages for the Craig-Sneyd family, read-out
+    # per shape group, plus the scatter of prices
     groups = {}
     for x in items:
-        key = (x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], x["grid"]["n_steps"])
-        groups[key] = x["grid"]["n_steps"]
-    launches_per_step = sum(3 + 3 * s for s in groups.values()) + 1
+        g = x["grid"]
+        key = (g["n_r"], g["n_v"], g["n_y"], g["n_steps"])
+        t = tiles["%dx%dx%d" % (g["n_r"], g["n_y"], g["n_v"])]
+        per_stage = 2 if t[3] == 0 and x["model"]["gamma"] == 0.0 else 3
+        groups[key] = g["n_steps"] * per_stage * (2 if scheme else 1)
+    launches_per_step = sum(3 + s for s in groups.values()) + 1
 
     line = {
         "metric": METRIC,
@@ -541,6 +563,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="config2",
                     choices=["config1", "config2", "config3", "config4", "config5"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--scheme", default="douglas", choices=list(SCHEMES),
+                    help="ADI scheme: the paper's Douglas, or Craig-Sneyd / modified CS / Hundsdorfer-Verwer")
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shapes")

@@ -79,6 +79,15 @@ typedef struct {
  *  theta_adi       theta of the theta scheme (0.5 = Crank-Nicolson)
  *  y_boundary_order    1 or 2: order of the one-sided y differences in F
  *  explicit_midpoint   0: F at t^n as in Section 5; 1: F at t^{n+1/2}
+ *  scheme          hjm_scheme: the Douglas scheme of Section 5.1, or one of
+ *                  the Craig-Sneyd family (Section 5.1 names Craig-Sneyd as
+ *                  the alternative; modified CS and Hundsdorfer-Verwer are
+ *                  those of the In 't Hout-Welfert work it cites). These add
+ *                  a correction stage (explicit operators and the three line
+ *                  solves once more) that makes the step second order in time
+ *                  with the mixed term; they take every explicit operator at
+ *                  t^{n+1/2}, whatever explicit_midpoint says. Usual theta:
+ *                  CS 1/2, MCS 1/3, HV 1/2 + sqrt(3)/6.
  * Boundary rule: r = r_max, and r = r_min when gamma == 0, carry Dirichlet
  * data (exact bond; caplet max(P(t,T) - Delta_M P(t,T_M), 0)); the v and y
  * faces (and r = 0 when gamma > 0) drop the normal second derivative and the
@@ -92,7 +101,25 @@ typedef struct {
     double theta_adi;
     int y_boundary_order;
     int explicit_midpoint;
+    int scheme;
 } hjm_grid_spec;
+
+/* ADI schemes (hjm_grid_spec.scheme). One step of each, with F = A_0 + A_r +
+ * A_v + A_y (A_0 the r-v mixed term, explicit only) and the line operators
+ * A_d implicit:
+ *   Douglas  Y0 = U + dt F(U); Yd = Y(d-1) + theta dt A_d (Yd - U), d = r,v,y;
+ *            U' = Y3
+ *   CS       Z0 = Y0 + dt/2 A_0 (Y3 - U)
+ *   MCS      Z0 = Y0 + theta dt A_0 (Y3 - U) + (1/2 - theta) dt F (Y3 - U)
+ *   HV       Z0 = Y0 + dt/2 F (Y3 - U)
+ *            then Zd = Z(d-1) + theta dt A_d (Zd - B), B = U (CS, MCS) or
+ *            Y3 (HV); U' = Z3. */
+typedef enum {
+    HJM_SCHEME_DOUGLAS = 0,
+    HJM_SCHEME_CS = 1,
+    HJM_SCHEME_MCS = 2,
+    HJM_SCHEME_HV = 3
+} hjm_scheme;
 
 /* Instruments of Section 3.2. ZCB pays 1 at T. CAPLET pays
  * max(1 - Delta_M p(T,T_M), 0) at T with Delta_M = 1 + (T_M - T) K; when
@@ -170,6 +197,11 @@ hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm_precision 
  *   pass 1: in = U^n                -> out = dU1 (explicit F and r solve)
  *   pass 2: in = dU1                -> out = dU2 (v solve)
  *   pass 3: in = dU2, in2 = U^n     -> out = U^{n+1} (y solve and update)
+ *   pass 4: in = U^n, in2 = Y3      -> out = Z1 - B (Craig-Sneyd family:
+ *           the correction stage's explicit operators and r solve, Y3 the
+ *           first stage's result, B as in hjm_scheme)
+ * For the Craig-Sneyd family pass 3 also serves both stages: in2 is the
+ * base the increment is added to (U^n in the first stage, B in the second).
  * in and out may alias for passes 2 and 3 (in place). */
 hjm_status hjm_field(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
                      int n_run, void* field_out);
@@ -324,13 +356,14 @@ hjm_status hjm_mlp_gemm(int M, int N, int K, const void* A, int lda, int trans_a
  * HJM_STATIC_SCRATCH_BYTES bytes that every GPU loading the library holds
  * until the process exits. The call allocates nothing (no cudaMalloc, no
  * cudaFree, no allocating library routine): it copies the item's parameters
- * into the array, runs set-up, terminal field, the n_steps Douglas steps and
+ * into the array, runs set-up, terminal field, the n_steps ADI steps and
  * the read-out on cuda_stream, and writes the price to price_out, which must
  * be device memory (one double). precision: HJM_FP32 or HJM_FP64.
  *
  * Limits and caveats:
  *  - an item whose fields and tables do not fit in the array is rejected with
- *    HJM_ERANGE (FP64 fields of up to about 2^19 points per field fit; the
+ *    HJM_ERANGE (FP64 fields of up to about 2^19 points per field fit, fewer
+ *    with a Craig-Sneyd-family scheme, which holds a third field; the
  *    message states the bytes needed);
  *  - the first call on each device sets up the array's device address and the
  *    kernels' shared-memory limit; make that first call before any stream

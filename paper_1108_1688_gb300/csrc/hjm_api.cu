@@ -101,6 +101,8 @@ static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const 
         return fail(HJM_EINVAL, "y_boundary_order must be 1 or 2");
     if (g.explicit_midpoint != 0 && g.explicit_midpoint != 1)
         return fail(HJM_EINVAL, "explicit_midpoint must be 0 or 1");
+    if (g.scheme < HJM_SCHEME_DOUGLAS || g.scheme > HJM_SCHEME_HV)
+        return fail(HJM_EINVAL, "unknown scheme %d", g.scheme);
     const double r00 = c.kind == HJM_CURVE_FLAT ? c.flat_rate : c.beta0 + c.beta1;  // f(0,0)
     if (r00 < g.r_min || r00 > g.r_max) return fail(HJM_EINVAL, "f(0,0) outside [r_min, r_max]");
     if (pass1_chunk(g.n_r) == 0) return fail(HJM_ERANGE, "n_r = %d above 512", g.n_r);
@@ -155,6 +157,7 @@ static InstParams to_params(const hjm_batch_item& it)
     p.theta_adi = it.grid.theta_adi;
     p.yorder = it.grid.y_boundary_order;
     p.midpoint = it.grid.explicit_midpoint;
+    p.scheme = it.grid.scheme;
     p.kind = it.inst.kind;
     p.T = it.inst.expiry_T;
     p.TM = it.inst.kind == HJM_CAPLET ? it.inst.pay_TM : it.inst.expiry_T;
@@ -240,12 +243,14 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Group {
     int nr, nv, ny, nsteps;
+    int scheme = HJM_SCHEME_DOUGLAS;  // the same for every instrument of the group
     std::vector<size_t> idx;  // positions in the caller's item array
     bool gpos = false;
     Tile tile{};
     GroupTables t{};
     void* U = nullptr;
     void* A = nullptr;
+    void* Y = nullptr;  // Craig-Sneyd family: the first stage's result Y3
     double* prices = nullptr;
     double* ind = nullptr;     // rounding indicators
     double* greeks = nullptr;  // [2 B]: dC/dr, dC/dv at the read-out point
@@ -276,7 +281,7 @@ struct TraceScope {
     }
     TraceScope(int k, cudaStream_t st) : kind(k), s(st)
     {
-        if (!g_trace_on) return;
+        if (!g_trace_on || k < 0) return;  // k < 0: never traced
         a = take();
         b = take();
         cudaEventRecord(a, s);
@@ -304,30 +309,53 @@ void trace_collect()
     g_ev_pending.clear();
 }
 
+// One stage of step n: pass 1 from U (and, for a correction stage, the first
+// stage's result Y) into A, then out = base + the v and y solves of A.
+template <typename T>
+hjm_status adi_stage(const March<T>& P, const T* U, const T* Y, T* A, const T* base, T* out, bool gpos,
+                     const Tile& tile, int n, cudaStream_t s, bool trace)
+{
+    {
+        TraceScope ts(trace ? 2 : -1, s);
+        CU_TRY(launch_pass1<T>(P, U, Y, A, n, tile, s));
+    }
+    if (tile.p2_P == 0 && !gpos) {  // passes 2 and 3 fused (traced as pass 3)
+        TraceScope ts(trace ? 4 : -1, s);
+        CU_TRY(launch_pass23<T>(P, A, base, out, n, s));
+        return HJM_OK;
+    }
+    {
+        TraceScope ts(trace ? 3 : -1, s);
+        CU_TRY(launch_pass2<T>(P, A, A, s));
+    }
+    {
+        TraceScope ts(trace ? 4 : -1, s);
+        CU_TRY(launch_pass3<T>(P, A, base, out, gpos, n, s));
+    }
+    return HJM_OK;
+}
+
+// One ADI step n in place on U (scheme as in hjm.h): Douglas is one stage
+// into U; the Craig-Sneyd family runs the Douglas stage into Y (Y3), then
+// the correction stage from U and Y into U (base U for CS and MCS, Y3 for
+// HV). trace: event pairs around the launches while tracing is enabled.
+template <typename T>
+hjm_status adi_step(const March<T>& P, int scheme, T* U, T* A, T* Y, bool gpos, const Tile& tile, int n,
+                    cudaStream_t s, bool trace)
+{
+    if (scheme == HJM_SCHEME_DOUGLAS) return adi_stage<T>(P, U, nullptr, A, U, U, gpos, tile, n, s, trace);
+    hjm_status st = adi_stage<T>(P, U, nullptr, A, U, Y, gpos, tile, n, s, trace);
+    if (st != HJM_OK) return st;
+    return adi_stage<T>(P, U, Y, A, scheme == HJM_SCHEME_HV ? Y : U, U, gpos, tile, n, s, trace);
+}
+
 template <typename T>
 hjm_status run_steps(const Group& g, int n_from, int n_to, cudaStream_t s)
 {
     const March<T> P = march_args<T>(g.t);
-    T* U = (T*)g.U;
-    T* A = (T*)g.A;
     for (int n = n_from; n < n_to; ++n) {
-        {
-            TraceScope ts(2, s);
-            CU_TRY(launch_pass1<T>(P, U, A, n, g.tile, s));
-        }
-        if (g.tile.p2_P == 0 && !g.gpos) {  // passes 2 and 3 fused (traced as pass 3)
-            TraceScope ts(4, s);
-            CU_TRY(launch_pass23<T>(P, A, U, U, n, s));
-            continue;
-        }
-        {
-            TraceScope ts(3, s);
-            CU_TRY(launch_pass2<T>(P, A, A, s));
-        }
-        {
-            TraceScope ts(4, s);
-            CU_TRY(launch_pass3<T>(P, A, U, U, g.gpos, n, s));
-        }
+        hjm_status st = adi_step<T>(P, g.scheme, (T*)g.U, (T*)g.A, (T*)g.Y, g.gpos, g.tile, n, s, true);
+        if (st != HJM_OK) return st;
     }
     return HJM_OK;
 }
@@ -365,10 +393,10 @@ hjm_status batch_graph(Workspace& ws, const std::vector<Group>& groups, size_t e
 {
     std::string key = std::to_string(elem);
     for (const auto& g : groups) {
-        char buf[200];
-        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%p,%p,%p,%d.%d.%d.%d.%d.%d.%d", g.nr, g.nv, g.ny,
-                 g.nsteps, g.t.B, (int)g.gpos, g.U, g.A, g.t.rt, g.tile.p1_S, g.tile.p1_M, g.tile.p1_R, g.tile.p2_P,
-                 g.tile.p3_P, g.tile.p1_stage, g.tile.p1_J);
+        char buf[240];
+        snprintf(buf, sizeof buf, "|%d,%d,%d,%d,%d,%d,%d,%p,%p,%p,%p,%d.%d.%d.%d.%d.%d.%d", g.nr, g.nv, g.ny,
+                 g.nsteps, g.t.B, (int)g.gpos, g.scheme, g.U, g.A, g.Y, g.t.rt, g.tile.p1_S, g.tile.p1_M,
+                 g.tile.p1_R, g.tile.p2_P, g.tile.p3_P, g.tile.p1_stage, g.tile.p1_J);
         key += buf;
     }
     auto it = ws.graphs.find(key);
@@ -443,10 +471,10 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
     // Groups hold at most kMaxGroup instruments (the set-up kernels index
     // instruments with the grid's y dimension).
     constexpr size_t kMaxGroup = 65535;
-    std::map<std::tuple<int, int, int, int>, size_t> where;
+    std::map<std::tuple<int, int, int, int, int>, size_t> where;
     for (size_t i = 0; i < n; ++i) {
         const hjm_grid_spec& g = items[i].grid;
-        auto key = std::make_tuple(g.n_r, g.n_v, g.n_y, g.n_steps);
+        auto key = std::make_tuple(g.n_r, g.n_v, g.n_y, g.n_steps, g.scheme);
         auto f = where.find(key);
         if (f != where.end() && groups[f->second].idx.size() >= kMaxGroup) {
             where.erase(f);
@@ -458,6 +486,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
             gr.nv = g.n_v;
             gr.ny = g.n_y;
             gr.nsteps = g.n_steps;
+            gr.scheme = g.scheme;
             f = where.emplace(key, groups.size()).first;
             groups.push_back(gr);
         }
@@ -471,7 +500,8 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
     for (auto& g : groups) {
         const size_t B = g.idx.size();
         const size_t N = (size_t)g.nr * g.nv * g.ny;
-        bytes += 2 * align256(B * N * elem) + tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
+        bytes += (g.scheme != HJM_SCHEME_DOUGLAS ? 3 : 2) * align256(B * N * elem) +
+                 tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
     }
     const void* old = ws.block.ptr;
     cudaError_t e = ws.block.ensure(bytes);
@@ -503,6 +533,11 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         p += align256(B * N * elem);
         g.A = p;
         p += align256(B * N * elem);
+        g.Y = nullptr;
+        if (g.scheme != HJM_SCHEME_DOUGLAS) {
+            g.Y = p;
+            p += align256(B * N * elem);
+        }
         g.t.nr = g.nr;
         g.t.nv = g.nv;
         g.t.ny = g.ny;
@@ -896,7 +931,7 @@ static hjm_status time_passes(Group& g, int ns, cudaStream_t s, cudaEvent_t* ev,
     for (int n = -1; n < ns; ++n) {  // n = -1: untimed warm-up step
         const int sn = n < 0 ? 0 : n;
         CU_TRY(cudaEventRecord(ev[0], s));
-        CU_TRY(launch_pass1<T>(P, U, A, sn, g.tile, s));
+        CU_TRY(launch_pass1<T>(P, U, nullptr, A, sn, g.tile, s));
         CU_TRY(cudaEventRecord(ev[1], s));
         if (g.tile.p2_P == 0 && !g.gpos) {
             CU_TRY(cudaEventRecord(ev[2], s));
@@ -1106,10 +1141,13 @@ extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* ins
                                        const void* in2, void* out)
 {
     if (!grid || !inst || !in || !out) return fail(HJM_EINVAL, "null argument");
-    if (pass < 1 || pass > 3) return fail(HJM_EINVAL, "pass must be 1, 2 or 3");
+    if (pass < 1 || pass > 4) return fail(HJM_EINVAL, "pass must be 1, 2, 3 or 4");
     if (pass == 3 && !in2) return fail(HJM_EINVAL, "pass 3 needs U^n");
+    if (pass == 4 && (!in2 || grid->spec.scheme == HJM_SCHEME_DOUGLAS))
+        return fail(HJM_EINVAL, "pass 4 needs Y3 and a Craig-Sneyd-family scheme");
     if (step_n < 0 || step_n >= grid->spec.n_steps) return fail(HJM_EINVAL, "step outside [0, n_steps)");
-    if (pass == 1 && in == out) return fail(HJM_EINVAL, "pass 1 cannot run in place");
+    if ((pass == 1 || pass == 4) && (in == out || in2 == out))
+        return fail(HJM_EINVAL, "pass %d cannot run in place", pass);
     std::lock_guard<std::mutex> lk(g_mu);
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
@@ -1121,13 +1159,17 @@ extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* ins
     cudaStream_t s = grid->stream;
     if (elem == sizeof(float)) {
         const March<float> P = march_args<float>(g.t);
-        if (pass == 1) CU_TRY(launch_pass1<float>(P, (const float*)in, (float*)out, step_n, g.tile, s));
+        if (pass == 1 || pass == 4)
+            CU_TRY(launch_pass1<float>(P, (const float*)in, pass == 4 ? (const float*)in2 : nullptr, (float*)out,
+                                       step_n, g.tile, s));
         if (pass == 2) CU_TRY(launch_pass2<float>(P, (const float*)in, (float*)out, s));
         if (pass == 3)
             CU_TRY(launch_pass3<float>(P, (const float*)in, (const float*)in2, (float*)out, g.gpos, step_n, s));
     } else {
         const March<double> P = march_args<double>(g.t);
-        if (pass == 1) CU_TRY(launch_pass1<double>(P, (const double*)in, (double*)out, step_n, g.tile, s));
+        if (pass == 1 || pass == 4)
+            CU_TRY(launch_pass1<double>(P, (const double*)in, pass == 4 ? (const double*)in2 : nullptr,
+                                        (double*)out, step_n, g.tile, s));
         if (pass == 2) CU_TRY(launch_pass2<double>(P, (const double*)in, (double*)out, s));
         if (pass == 3)
             CU_TRY(launch_pass3<double>(P, (const double*)in, (const double*)in2, (double*)out, g.gpos, step_n, s));
@@ -1168,18 +1210,13 @@ void* g_static_addr[kStaticMaxDevices];  // device address of g_static_scratch, 
 std::mutex g_static_mu;
 
 template <typename T>
-hjm_status static_march(const GroupTables& t, void* U, void* A, int nsteps, bool gpos, const Tile& tile,
-                        cudaStream_t s)
+hjm_status static_march(const GroupTables& t, int scheme, void* U, void* A, void* Y, int nsteps, bool gpos,
+                        const Tile& tile, cudaStream_t s)
 {
     const March<T> P = march_args<T>(t);
     for (int n = 0; n < nsteps; ++n) {
-        CU_TRY(launch_pass1<T>(P, (const T*)U, (T*)A, n, tile, s));
-        if (tile.p2_P == 0 && !gpos) {
-            CU_TRY(launch_pass23<T>(P, (const T*)A, (const T*)U, (T*)U, n, s));
-            continue;
-        }
-        CU_TRY(launch_pass2<T>(P, (const T*)A, (T*)A, s));
-        CU_TRY(launch_pass3<T>(P, (const T*)A, (const T*)U, (T*)U, gpos, n, s));
+        hjm_status st = adi_step<T>(P, scheme, (T*)U, (T*)A, (T*)Y, gpos, tile, n, s, false);
+        if (st != HJM_OK) return st;
     }
     return HJM_OK;
 }
@@ -1196,7 +1233,8 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     if (st != HJM_OK) return st;
     const hjm_grid_spec& g = item->grid;
     const size_t N = (size_t)g.n_r * g.n_v * g.n_y;
-    const size_t need = align256(sizeof(InstParams)) + 2 * align256(N * elem) +
+    const int fields = g.scheme != HJM_SCHEME_DOUGLAS ? 3 : 2;
+    const size_t need = align256(sizeof(InstParams)) + fields * align256(N * elem) +
                         tables_bytes(g.n_r, g.n_v, g.n_y, g.n_steps, 1, elem) + align256(sizeof(double));
     if (need > HJM_STATIC_SCRATCH_BYTES)
         return fail(HJM_ERANGE, "item needs %zu bytes of scratch, the static array holds %u", need,
@@ -1232,6 +1270,11 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     p += align256(N * elem);
     void* A = p;
     p += align256(N * elem);
+    void* Y = nullptr;
+    if (fields == 3) {
+        Y = p;
+        p += align256(N * elem);
+    }
     tables_carve(t, p, elem);
     p += tables_bytes(g.n_r, g.n_v, g.n_y, g.n_steps, 1, elem);
     double* ind = (double*)p;
@@ -1250,8 +1293,8 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     CU_TRY(launch_setup(t, elem, s));
     CU_TRY(launch_terminal(t, U, elem, s));
     const bool gpos = item->model.gamma > 0.0;
-    st = elem == sizeof(float) ? static_march<float>(t, U, A, g.n_steps, gpos, tile, s)
-                               : static_march<double>(t, U, A, g.n_steps, gpos, tile, s);
+    st = elem == sizeof(float) ? static_march<float>(t, g.scheme, U, A, Y, g.n_steps, gpos, tile, s)
+                               : static_march<double>(t, g.scheme, U, A, Y, g.n_steps, gpos, tile, s);
     if (st != HJM_OK) return st;
     CU_TRY(launch_readout(t, U, elem, price_out, ind, nullptr, s));
     return HJM_OK;

@@ -6,7 +6,9 @@
 //   r tables rt[b][RT_N][n_r]         per-node factors of the r operator,
 //   v tables vt[b][VT_N][n_v]         with the grid spacings of the centred
 //   y tables yt[b][YT_N][n_y]         differences folded in (see k_setup)
-//   scalars  sc[b][SC_N]              dt, theta*dt, 1/h per axis
+//   scalars  sc[b][SC_N]              dt, theta*dt, 1/h per axis, and the
+//                                     weights of the Craig-Sneyd correction
+//                                     stage (see SC_C1 ..)
 //   steps    st[b][n_steps][2]        a(t) = df(0,t)/dt + kappa f(0,t) for
 //                                     the explicit and the implicit stage
 //   faces    dir[b][n_steps][2][n_y]  Dirichlet data at t^{n+1}, r_min/r_max
@@ -40,6 +42,7 @@ struct InstParams {
     int center_on_strike;
     double theta_adi;
     int yorder, midpoint;
+    int scheme;  // hjm_scheme
     int kind;
     double T, TM, K;
     int atm_rel;
@@ -61,7 +64,14 @@ constexpr double kIndicatorC = 8.0;
 enum { RT_R, RT_IJ, RT_C1, RT_C4V, RT_C4B, RT_C3, RT_CY, RT_N };
 enum { VT_V, VT_IJ, VT_G2, VT_G5, VT_FV, VT_N };
 enum { YT_Y, YT_IJ, YT_KY, YT_N };
-enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_N };
+// Correction stage of the Craig-Sneyd family (all explicit operators at
+// t^{n+1/2}, E = Y3 - U^n the first stage's increment):
+//   Z0 - B = dt (A_0 (U + E/2) + A_dir (U + c1 E)) - he E,
+// with A_dir = A_r + A_v + A_y; c1 = 0 (CS), 1/2 - theta (MCS), 1/2 (HV);
+// he = 1 for HV (B = Y3), 0 otherwise (B = U^n). SC_CX = 1/2 - c1 is the
+// extra weight of the mixed term; on Dirichlet nodes Z0 - B = kd (g - U -
+// c1 E) with kd = (1 - he) / (1 - c1) (there E = g - U^n).
+enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_C1, SC_CX, SC_HE, SC_KD, SC_N };
 enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_RI0, FL_RK0, FL_PAD, FL_N };
 
 template <typename T>
@@ -170,9 +180,12 @@ bool pass23_valid(int nr, int nv, int ny, int p2, size_t elem);
 template <typename T>
 cudaError_t launch_pass23(const March<T>& P, const T* in, const T* Un, T* out, int n, cudaStream_t s);
 
-// The three Douglas passes of step n (in/out as documented in hjm.h).
+// The three Douglas passes of step n (in/out as documented in hjm.h). Pass 1
+// with Y == nullptr: dU1 from dt F(U^n); with Y = Y3 of a Craig-Sneyd-family
+// step: Z1 - B of its correction stage (never the staged kernel).
 template <typename T>
-cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s);
+cudaError_t launch_pass1(const March<T>& P, const T* U, const T* Y, T* out, int n, const Tile& t,
+                         cudaStream_t s);
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s);
 template <typename T>

@@ -3,6 +3,9 @@
 //   metric form of Section 4.3, centred differences of Section 5, the r-v
 //   mixed term A_0 explicit only)
 // fused with the r-line solve (I - theta dt A_r(t^{n+1/2})) dU1 = dU0.
+// The same kernel, given the first stage's result Y3, forms the correction
+// stage of the Craig-Sneyd family (right-hand side from U^n and Y3, the
+// weights in the scalar table; see SC_C1 in hjm_kernels.cuh).
 //
 // r lines are contiguous in memory. A line is owned by a segment of S lanes
 // of a warp (S = 8, 16 or 32; 32/S lines per warp side by side); lane l of
@@ -256,9 +259,12 @@ struct P1Inst {
     const T* vt;
     const T* yt;
     const T* dir;  // Dirichlet data of this step: [2][n_y]
+    // correction stage of the Craig-Sneyd family only (SC_C1 ..)
+    T c1, cx, kd;
+    bool hv;
 };
 
-template <typename T>
+template <typename T, bool ST2 = false>
 __device__ __forceinline__ P1Inst<T> p1_inst(const March<T>& P, int b, int n)
 {
     P1Inst<T> I;
@@ -277,6 +283,15 @@ __device__ __forceinline__ P1Inst<T> p1_inst(const March<T>& P, int b, int n)
     I.vt = P.vt + (size_t)b * VT_N * P.nv;
     I.yt = P.yt + (size_t)b * YT_N * P.ny;
     I.dir = P.dir + (((size_t)b * P.nsteps + n) * 2) * P.ny;
+    if constexpr (ST2) {
+        I.c1 = sc[SC_C1];
+        I.cx = sc[SC_CX];
+        I.kd = sc[SC_KD];
+        I.hv = sc[SC_HE] != T(0);
+    } else {
+        I.c1 = I.cx = I.kd = T(0);
+        I.hv = false;
+    }
     return I;
 }
 
@@ -289,10 +304,14 @@ __device__ __forceinline__ P1Inst<T> p1_inst(const March<T>& P, int b, int n)
 //      line's (v, y) (the input rows are dead by then, which bounds the
 //      registers at about 6 M + scalars);
 //   3. the partition solve. d returns dU1 on the lane's nodes.
-template <typename T, int S, int M>
+// ST2 (correction stage of the Craig-Sneyd family): the rows hold
+// U + c1 E and xx the extra term: the mixed-term rows' weighted difference
+// cx (E_{v,b} - E_{v,a}) (CS, MCS) or -E (HV, added to the right-hand
+// side); Dirichlet nodes take kd (g - U - c1 E).
+template <typename T, int S, int M, bool ST2 = false>
 __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl, int k, int j, const T (&uc)[M],
                                         const T (&ua)[M], const T (&ub)[M], const T (&ya)[M], const T (&yb)[M],
-                                        T (&d)[M])
+                                        const T (&xx)[M], T (&d)[M])
 {
     constexpr int W = P1Layout<T, M>::W, MP = P1Layout<T, M>::MP;
     const int nr = I.nr, nv = I.nv, ny = I.ny, e0 = sl * M;
@@ -320,8 +339,15 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     // mixed term, wd = U_{v,b} - U_{v,a}.
     const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
     const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
-    const T wd_prev = __shfl_up_sync(0xffffffffu, ub[M - 1] - ua[M - 1], 1, S);
-    const T wd_next = __shfl_down_sync(0xffffffffu, ub[0] - ua[0], 1, S);
+    T wl = ub[M - 1] - ua[M - 1], wf = ub[0] - ua[0];
+    if constexpr (ST2) {
+        if (!I.hv) {
+            wl += xx[M - 1];
+            wf += xx[0];
+        }
+    }
+    const T wd_prev = __shfl_up_sync(0xffffffffu, wl, 1, S);
+    const T wd_next = __shfl_down_sync(0xffffffffu, wf, 1, S);
 
 #define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
     // 1. right-hand side, every node as if interior in r. Nodes are taken
@@ -331,8 +357,11 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     using PV = typename Two<T>::V;
     constexpr int H = M / 2;
     // rolling shifted pairs (current and next), built just in time
+    // ST2: weights of xx in the mixed-term difference and in the right-hand side
+    const PV xw2 = Two<T>::splat(ST2 && !I.hv ? T(1) : T(0)), xr2 = Two<T>::splat(ST2 && I.hv ? T(1) : T(0));
     PV shc = Two<T>::mk(uc_prev, uc[0]);
     PV wdc = Two<T>::sub(Two<T>::mk(ub[0], ub[1]), Two<T>::mk(ua[0], ua[1]));
+    if constexpr (ST2) wdc = Two<T>::fma(xw2, Two<T>::mk(xx[0], xx[1]), wdc);
     PV twc = Two<T>::mk(wd_prev, Two<T>::x(wdc));
     const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v), aFy2 = Two<T>::splat(aFy);
     const PV vq2 = Two<T>::splat(vq), cA2 = Two<T>::splat(cA), cB2 = Two<T>::splat(cB);
@@ -355,6 +384,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             if (h + 1 < H) {
                 shn = Two<T>::mk(uc[m + 1], uc[m + 2]);
                 wdn = Two<T>::sub(Two<T>::mk(ub[m + 2], ub[m + 3]), Two<T>::mk(ua[m + 2], ua[m + 3]));
+                if constexpr (ST2) wdn = Two<T>::fma(xw2, Two<T>::mk(xx[m + 2], xx[m + 3]), wdn);
                 twn = Two<T>::mk(Two<T>::y(wdc), Two<T>::x(wdn));
             } else {
                 shn = Two<T>::mk(uc[M - 1], uc_next);
@@ -376,7 +406,8 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             const PV yy = Two<T>::fma(yA2, Two<T>::sub(Two<T>::mk(ya[m], ya[m + 1]), u),
                                       Two<T>::mul(yB2, Two<T>::sub(Two<T>::mk(yb[m], yb[m + 1]), u)));
             f = Two<T>::fma(g6, yy, f);
-            const PV r = Two<T>::mul(dt2, f);
+            PV r = Two<T>::mul(dt2, f);
+            if constexpr (ST2) r = Two<T>::fma(xr2, Two<T>::mk(xx[m], xx[m + 1]), r);
             d[m] = Two<T>::x(r);
             d[m + 1] = Two<T>::y(r);
             shc = shn;
@@ -387,7 +418,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const T gLo = I.dir[j], gHi = I.dir[ny + j];
     if (sl == 0) {
         if (I.rlo) {
-            d[0] = gLo - uc[0];
+            d[0] = ST2 ? I.kd * (gLo - uc[0]) : gLo - uc[0];
         } else {
             // gamma > 0: r = 0 face, one-sided first derivative, zeta_rr = 0
             // and no mixed term (Section 7.3).
@@ -398,13 +429,16 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             const T g6 = tl[RT_CY * S * MP] * vy + kyy;
             f += g6 * (yA * (ya[0] - u) + yB * (yb[0] - u));
             d[0] = dt * f;
+            if constexpr (ST2) {
+                if (I.hv) d[0] += xx[0];
+            }
         }
     }
     if (e0 + M > nr - 1) {  // only lanes holding r_max or padding
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             const int e = e0 + m;
-            if (e >= nr - 1) d[m] = e == nr - 1 ? gHi - uc[m] : T(0);
+            if (e >= nr - 1) d[m] = e == nr - 1 ? (ST2 ? I.kd * (gHi - uc[m]) : gHi - uc[m]) : T(0);
         }
     }
 
@@ -494,10 +528,12 @@ __device__ __forceinline__ void p1_neighbours(int k, int j, int nv, int ny, int&
 // Pass 1, rows from global memory: one CTA = 4 warps = 4 * (32/S) segments;
 // each segment processes R lines of one instrument (line index k + n_v j),
 // all segments of a warp advancing together so the width-S shuffles always
-// see full warps.
-template <typename T, int S, int M>
+// see full warps. ST2: the correction stage of the Craig-Sneyd family, which
+// also reads the rows of the first stage's result Y.
+template <typename T, int S, int M, bool ST2>
 __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __restrict__ U,
-                                               T* __restrict__ out, const int n, const int R)
+                                               const T* __restrict__ Y, T* __restrict__ out, const int n,
+                                               const int R)
 {
     constexpr int G = 32 / S;
     constexpr int MP = P1Layout<T, M>::MP;
@@ -509,8 +545,9 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
     const int bpi = (L + lpc - 1) / lpc;
     const int b = blockIdx.x / bpi, cb = blockIdx.x % bpi;
     const T* __restrict__ Ub = U + (long long)b * P.N;
+    const T* __restrict__ Yb = ST2 ? Y + (long long)b * P.N : nullptr;
     T* __restrict__ Ob = out + (long long)b * P.N;
-    const P1Inst<T> I = p1_inst(P, b, n);
+    const P1Inst<T> I = p1_inst<T, ST2>(P, b, n);
     const int e0 = sl * M;
     __shared__ __align__(16) T tsm[RT_N * S * MP];
     p1_tables<T, S, M>(P, b, tsm);
@@ -519,7 +556,8 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
     // 16-byte row access for every row when n_r is a multiple of the vector
     // width and the fields are 16-byte aligned (uniform, checked once).
     const bool vec = nr % (16 / (int)sizeof(T)) == 0 &&
-                     ((reinterpret_cast<uintptr_t>(Ub) | reinterpret_cast<uintptr_t>(Ob)) & 15) == 0;
+                     ((reinterpret_cast<uintptr_t>(Ub) | reinterpret_cast<uintptr_t>(Ob) |
+                       reinterpret_cast<uintptr_t>(Yb)) & 15) == 0;
     // Lines of this segment: line0, line0 + G, ...; (k, j) advanced without
     // divisions. Element offsets within an instrument fit in 32 bits.
     const int line0 = cb * lpc + warp * R * G + seg;
@@ -530,13 +568,44 @@ __global__ void __launch_bounds__(128) k_pass1(const March<T> P, const T* __rest
         int ka, kb, ja, jb;
         p1_neighbours(kk, jj, nv, ny, ka, kb, ja, jb);
         const int off = (jj * nv + kk) * nr;
-        T uc[M], ua[M], ub[M], ya[M], yb[M], d[M];
+        T uc[M], ua[M], ub[M], ya[M], yb[M], d[M], xx[M];
         p1_load<T, M>(Ub + off, e0, nr, uc, vec);
         p1_load<T, M>(Ub + off + (ka - kk) * nr, e0, nr, ua, vec);
         p1_load<T, M>(Ub + off + (kb - kk) * nr, e0, nr, ub, vec);
         p1_load<T, M>(Ub + off + (ja - jj) * nv * nr, e0, nr, ya, vec);
         p1_load<T, M>(Ub + off + (jb - jj) * nv * nr, e0, nr, yb, vec);
-        p1_line<T, S, M>(I, tl, sl, kk, jj, uc, ua, ub, ya, yb, d);
+        if constexpr (ST2) {
+            // rows of U + c1 E with E = Y - U, and the extra term xx
+            T e[M];
+            p1_load<T, M>(Yb + off, e0, nr, e, vec);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                e[m] -= uc[m];
+                xx[m] = I.hv ? -e[m] : T(0);
+                uc[m] = fma(I.c1, e[m], uc[m]);
+            }
+            p1_load<T, M>(Yb + off + (ka - kk) * nr, e0, nr, e, vec);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                e[m] -= ua[m];
+                if (!I.hv) xx[m] = -I.cx * e[m];
+                ua[m] = fma(I.c1, e[m], ua[m]);
+            }
+            p1_load<T, M>(Yb + off + (kb - kk) * nr, e0, nr, e, vec);
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                e[m] -= ub[m];
+                if (!I.hv) xx[m] = fma(I.cx, e[m], xx[m]);
+                ub[m] = fma(I.c1, e[m], ub[m]);
+            }
+            p1_load<T, M>(Yb + off + (ja - jj) * nv * nr, e0, nr, e, vec);
+#pragma unroll
+            for (int m = 0; m < M; ++m) ya[m] = fma(I.c1, e[m] - ya[m], ya[m]);
+            p1_load<T, M>(Yb + off + (jb - jj) * nv * nr, e0, nr, e, vec);
+#pragma unroll
+            for (int m = 0; m < M; ++m) yb[m] = fma(I.c1, e[m] - yb[m], yb[m]);
+        }
+        p1_line<T, S, M, ST2>(I, tl, sl, kk, jj, uc, ua, ub, ya, yb, xx, d);
         if (valid) p1_store<T, M>(Ob + off, e0, nr, d, vec);
         k += G;
         while (k >= nv) {
@@ -664,7 +733,7 @@ __global__ void __launch_bounds__(128, 4) k_pass1s(const March<T> P, const T* __
                 p1s_row<T, M>(ring + (jb & 3) * SLOT + (k - klo) * RS, e0, yb);
             else
                 p1_load<T, M>(Ub + ((long long)jb * nv + k) * nr, e0, nr, yb);
-            p1_line<T, S, M>(I, tl, sl, k, j, uc, ua, ub, ya, yb, d);
+            p1_line<T, S, M>(I, tl, sl, k, j, uc, ua, ub, ya, yb, uc, d);
             if (valid) p1_store<T, M>(Ob + ((long long)j * nv + k) * nr, e0, nr, d);
         }
     }
@@ -733,10 +802,11 @@ int pass1_chunk(int nr)
 }
 
 template <typename T, int S, int M>
-static cudaError_t p1_launch(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s)
+static cudaError_t p1_launch(const March<T>& P, const T* U, const T* Y, T* out, int n, const Tile& t,
+                             cudaStream_t s)
 {
     const bool aligned = ((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
-    if (t.p1_stage == 1 && aligned) {
+    if (Y == nullptr && t.p1_stage == 1 && aligned) {
         const int KB = 4 * (32 / S) * t.p1_R;
         const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
         const size_t smem = p1s_smem(P.nr, S, M, t.p1_R, sizeof(T));
@@ -746,7 +816,10 @@ static cudaError_t p1_launch(const March<T>& P, const T* U, T* out, int n, const
     }
     const int lpc = 4 * (32 / S) * t.p1_R;
     const int bpi = (P.nv * P.ny + lpc - 1) / lpc;
-    k_pass1<T, S, M><<<(unsigned)(bpi * P.B), 128, 0, s>>>(P, U, out, n, t.p1_R);
+    if (Y)
+        k_pass1<T, S, M, true><<<(unsigned)(bpi * P.B), 128, 0, s>>>(P, U, Y, out, n, t.p1_R);
+    else
+        k_pass1<T, S, M, false><<<(unsigned)(bpi * P.B), 128, 0, s>>>(P, U, nullptr, out, n, t.p1_R);
     return cudaGetLastError();
 }
 
@@ -773,12 +846,13 @@ cudaError_t init_pass1()
 }
 
 template <typename T>
-cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, const Tile& t, cudaStream_t s)
+cudaError_t launch_pass1(const March<T>& P, const T* U, const T* Y, T* out, int n, const Tile& t,
+                         cudaStream_t s)
 {
     if (!tile_valid(t, P.nr, P.nv, P.ny, sizeof(T))) return cudaErrorInvalidValue;
     const int S = t.p1_S, M = t.p1_M;
 #define P1_CASE(T_, S_, M_) \
-    if (S == S_ && M == M_) return p1_launch<T, S_, M_>(P, U, out, n, t, s);
+    if (S == S_ && M == M_) return p1_launch<T, S_, M_>(P, U, Y, out, n, t, s);
     if constexpr (sizeof(T) == 4) {
         P1_SHAPES_F32(P1_CASE)
     } else {
@@ -788,9 +862,9 @@ cudaError_t launch_pass1(const March<T>& P, const T* U, T* out, int n, const Til
     return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_pass1<float>(const March<float>&, const float*, float*, int, const Tile&,
-                                         cudaStream_t);
-template cudaError_t launch_pass1<double>(const March<double>&, const double*, double*, int, const Tile&,
-                                          cudaStream_t);
+template cudaError_t launch_pass1<float>(const March<float>&, const float*, const float*, float*, int,
+                                         const Tile&, cudaStream_t);
+template cudaError_t launch_pass1<double>(const March<double>&, const double*, const double*, double*, int,
+                                          const Tile&, cudaStream_t);
 
 }  // namespace hjm

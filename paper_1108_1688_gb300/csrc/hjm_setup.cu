@@ -181,6 +181,12 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         sc[SC_IHR] = (T)(nr - 1);
         sc[SC_IHV] = (T)(nv - 1);
         sc[SC_IHY] = (T)(ny - 1);
+        const double c1 = p.scheme == HJM_SCHEME_MCS ? 0.5 - p.theta_adi : (p.scheme == HJM_SCHEME_HV ? 0.5 : 0.0);
+        const double he = p.scheme == HJM_SCHEME_HV ? 1.0 : 0.0;
+        sc[SC_C1] = (T)c1;
+        sc[SC_CX] = (T)(0.5 - c1);
+        sc[SC_HE] = (T)he;
+        sc[SC_KD] = (T)((1.0 - he) / (1.0 - c1));
         int* fl = g.fl + (size_t)b * FL_N;
         fl[FL_RLO_DIR] = p.gamma == 0.0;
         fl[FL_YORDER] = p.yorder;
@@ -192,11 +198,13 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         fl[FL_PAD] = 0;
     }
     for (int n = tid; n < ns; n += nth) g.acc[(size_t)b * ns + n] = 0.0f;
-    // a(t) = df(0,t)/dt + kappa f(0,t): F at t^n (or t^{n+1/2}), implicit
-    // operators at t^{n+1/2} (Section 5, delta form).
+    // a(t) = df(0,t)/dt + kappa f(0,t): F at t^n (or t^{n+1/2}, always for
+    // the Craig-Sneyd family), implicit operators at t^{n+1/2} (Section 5,
+    // delta form).
     T* st = (T*)g.st + (size_t)b * ns * 2;
+    const bool mid = p.midpoint || p.scheme != HJM_SCHEME_DOUGLAS;
     for (int n = tid; n < ns; n += nth) {
-        const double tF = p.T - (p.midpoint ? n + 0.5 : (double)n) * D.dt;
+        const double tF = p.T - (mid ? n + 0.5 : (double)n) * D.dt;
         const double tI = p.T - (n + 0.5) * D.dt;
         st[2 * n] = (T)(fwd_slope(p, tF) + p.kappa * fwd(p, tF));
         st[2 * n + 1] = (T)(fwd_slope(p, tI) + p.kappa * fwd(p, tI));

@@ -44,7 +44,7 @@ class hjm_grid_spec(C.Structure):
                 ("v_max", C.c_double), ("alpha_r", C.c_double), ("alpha_y", C.c_double),
                 ("alpha_v", C.c_double), ("k_r", C.c_double), ("k_v", C.c_double),
                 ("center_r_on_strike", C.c_int), ("theta_adi", C.c_double),
-                ("y_boundary_order", C.c_int), ("explicit_midpoint", C.c_int)]
+                ("y_boundary_order", C.c_int), ("explicit_midpoint", C.c_int), ("scheme", C.c_int)]
 
 
 class hjm_instrument(C.Structure):

@@ -50,6 +50,16 @@ def test_workload_sizes():
     assert len(items) == 256
 
 
+@pytest.mark.parametrize("scheme,code", [("cs", 1), ("mcs", 2), ("hv", 3)])
+def test_workload_scheme_option(scheme, code):
+    items, desc = bench.workload_items("config2", instruments=3, march_steps=10, scheme=scheme)
+    assert all(x["grid"]["scheme"] == code for x in items)
+    assert abs(items[0]["grid"]["theta_adi"] - bench.SCHEMES[scheme][1]) == 0.0
+    assert scheme.upper() + " scheme" in desc
+    plain, _ = bench.workload_items("config2", instruments=3, march_steps=10)
+    assert all(x["grid"]["scheme"] == 0 and x["grid"]["theta_adi"] == 0.5 for x in plain)
+
+
 def test_reference_arm_prints_one_line():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
                         "--steps", "1", "--warmup", "0", "--workload", "config1",
