@@ -79,6 +79,9 @@ def _workload_items(name, instruments=None, march_steps=None):
         return W.config3_batch(), "256 caplets, expiries 1..10y, uneven grids 64..256 x n/2 x n/2, 2n steps"
     if name == "config1":
         return [W.config1()], "5y zero-coupon bond, flat 3%, 40x20x20, 100 steps"
+    if name == "paper63":
+        return (W.paper_timing_set(),
+                "the 3 caplets of the paper's timing table (1y, 10y, 19y into 1y, ATM), 100x50x50, 12 steps/yr")
     raise SystemExit("unknown workload %s" % name)
 
 
@@ -561,7 +564,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2",
-                    choices=["config1", "config2", "config3", "config4", "config5"])
+                    choices=["config1", "config2", "config3", "config4", "config5", "paper63"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--scheme", default="douglas", choices=list(SCHEMES),
                     help="ADI scheme: the paper's Douglas, or Craig-Sneyd / modified CS / Hundsdorfer-Verwer")

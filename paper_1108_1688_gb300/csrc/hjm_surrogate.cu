@@ -197,6 +197,10 @@ struct hjm_surrogate {
     DBuf<unsigned> cnt;
     DBuf<double> dtmp;
     DBuf<unsigned char> rej;
+    // march fallback of hjm_surrogate_infer (grow-only, kept between calls)
+    DBuf<float> fb_x;
+    DBuf<double> fb_q;
+    DBuf<int> fb_idx;
     std::mutex mu;
 };
 
@@ -473,6 +477,9 @@ extern "C" hjm_status hjm_surrogate_destroy(hjm_surrogate* s)
     s->cnt.release();
     s->dtmp.release();
     s->rej.release();
+    s->fb_x.release();
+    s->fb_q.release();
+    s->fb_idx.release();
     delete s;
     return HJM_OK;
 }
@@ -653,22 +660,17 @@ extern "C" hjm_status hjm_surrogate_infer(hjm_surrogate* s, const float* x, size
     std::vector<float> sx((size_t)m * kIn);
     for (int q = 0; q < m; ++q)
         for (int k = 0; k < kIn; ++k) sx[(size_t)q * kIn + k] = hx[(size_t)idx[q] * kIn + k];
-    DBuf<float> dsx;
-    DBuf<double> dq;
-    DBuf<int> didx;
-    if (dsx.ensure((size_t)m * kIn) || dq.ensure(m) || didx.ensure(m)) return fail(HJM_ENOMEM, "fallback buffers");
+    if (s->fb_x.ensure((size_t)m * kIn) || s->fb_q.ensure(m) || s->fb_idx.ensure(m))
+        return fail(HJM_ENOMEM, "fallback buffers");
     hjm_status r = HJM_OK;
-    if (cudaMemcpyAsync(dsx.p, sx.data(), sx.size() * sizeof(float), cudaMemcpyHostToDevice, st) ||
-        cudaMemcpyAsync(didx.p, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice, st))
+    if (cudaMemcpyAsync(s->fb_x.p, sx.data(), sx.size() * sizeof(float), cudaMemcpyHostToDevice, st) ||
+        cudaMemcpyAsync(s->fb_idx.p, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice, st))
         r = fail(HJM_ECUDA, "fallback upload");
-    if (r == HJM_OK) r = pde_targets(s, sx, m, dsx.p, nullptr, dq.p, 0, st);
+    if (r == HJM_OK) r = pde_targets(s, sx, m, s->fb_x.p, nullptr, s->fb_q.p, 0, st);
     if (r == HJM_OK) {
-        k_scatter_d<<<(m + 127) / 128, 128, 0, st>>>(m, didx.p, dq.p, price_out, nullptr);
+        k_scatter_d<<<(m + 127) / 128, 128, 0, st>>>(m, s->fb_idx.p, s->fb_q.p, price_out, nullptr);
         if (cudaGetLastError() || cudaStreamSynchronize(st)) r = fail(HJM_ECUDA, "fallback scatter");
     }
-    dsx.release();
-    dq.release();
-    didx.release();
     return r;
 }
 

@@ -180,6 +180,20 @@ def paper_2007_set(n_r=40, n_y=20, n_v=20, n_steps=100, T=5.0):
     return item(c, m, g, bond(T))
 
 
+def paper_timing_set():
+    """The caplets of the paper's computation-time table (Section 6.3): expiry
+    Tc = 1, 10, 19 years into a one-year period (TMc = Tc + 1), ATM, on a
+    100 x 50 x 50 (r x y x v) mesh with 12 steps per year; the model is the
+    2007 market set of Section 3.3 (the table does not name one)."""
+    out = []
+    for Tc in (1, 10, 19):
+        x = paper_2007_set(n_r=100, n_y=50, n_v=50, n_steps=12 * Tc, T=float(Tc))
+        x["inst"] = caplet(float(Tc), float(Tc + 1))
+        x["grid"] = default_grid(x["curve"], x["model"], float(Tc), 100, 50, 50, 12 * Tc, y_boundary_order=1)
+        out.append(x)
+    return out
+
+
 def with_grid(it, **kw):
     """Copy of an item with some grid fields replaced."""
     out = copy.deepcopy(it)

@@ -203,53 +203,138 @@ def test_train_gate_checkpoint_and_resume(env, tmp_path):
         H.hjm_surrogate_destroy(h)
 
 
-def test_trained_surrogate_error_coverage_and_gain(env):
-    # A network trained on 2^16 PDE labels (64 x 32 x 32, 128 steps), judged
-    # by the PDE on fresh draws (5% out of the box): every answered row within
-    # 1e-4 of the PDE forward premium, the rest priced by the PDE; then the
-    # speed-up of surrogate pricing over the march alone on 65,536 rows.
+TRAINED_LABEL = dict(n_r=64, n_y=32, n_v=32, n_steps=128)
+
+
+@pytest.fixture(scope="module")
+def trained(env):
+    # A network trained on 2^16 PDE labels (64 x 32 x 32, 128 steps), shared
+    # by the tests below.
     torch, H = env
-    label = W.surrogate_label_grid(64, 32, 32, 128)
+    label = W.surrogate_label_grid(**TRAINED_LABEL)
     t0 = time.time()
     h = H.hjm_surrogate_train(H.surrogate_cfg(1 << 16, 120, 1024, 3e-3, 2024, W.SURROGATE_BOX_LO,
                                               W.SURROGATE_BOX_HI, label, None))
-    train_s = time.time() - t0
+    yield h, label, time.time() - t0
+    H.hjm_surrogate_destroy(h)
+
+
+def test_trained_surrogate_error_coverage_and_gain(env, trained):
+    # The trained network judged by the PDE on fresh draws (5% out of the
+    # box): every answered row within 1e-4 of the PDE forward premium, the
+    # rest priced by the PDE; then the speed-up of surrogate pricing over the
+    # march alone on 65,536 rows.
+    torch, H = env
+    h, label, train_s = trained
     table = H.hjm_surrogate_error_table(h)
     print("surrogate: held-out bin errors min %.2e median %.2e max %.2e, bins under 5e-5: %d/72"
           % (table.min(), np.median(table), table.max(), int((table <= 5e-5).sum())))
-    try:
-        x = W.surrogate_draws(2048, seed=31, out_of_box=0.05)
-        out = torch.empty(2048, dtype=torch.float64, device="cuda")
-        used = torch.zeros(2048, dtype=torch.uint8, device="cuda")
-        H.hjm_surrogate_infer(h, torch.tensor(x).cuda(), out, used)
-        torch.cuda.synchronize()
-        got = out.cpu().numpy()
-        u = used.cpu().numpy().astype(bool)
-        want = _pde_forward_premium(H, x, label)
-        err = np.abs(got - want)
-        coverage = 1.0 - u.mean()
-        print("surrogate: train %.1fs coverage %.3f max err answered %.2e median %.2e"
-              % (train_s, coverage, err[~u].max() if (~u).any() else 0, np.median(err[~u]) if (~u).any() else 0))
-        assert np.all(err[u] <= 1e-12 + 1e-12 * np.abs(want[u]))  # fallback rows are the PDE
-        assert np.all(err[~u] <= 1e-4)
-        assert coverage > 0.5
-        # gain: 65,536 rows through the network vs the march on a 256-row sample
-        xb = torch.tensor(W.surrogate_draws(65536, seed=32)).cuda()
-        yb = torch.empty(65536, dtype=torch.float32, device="cuda")
+    x = W.surrogate_draws(2048, seed=31, out_of_box=0.05)
+    out = torch.empty(2048, dtype=torch.float64, device="cuda")
+    used = torch.zeros(2048, dtype=torch.uint8, device="cuda")
+    H.hjm_surrogate_infer(h, torch.tensor(x).cuda(), out, used)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    u = used.cpu().numpy().astype(bool)
+    want = _pde_forward_premium(H, x, label)
+    err = np.abs(got - want)
+    coverage = 1.0 - u.mean()
+    print("surrogate: train %.1fs coverage %.3f max err answered %.2e median %.2e"
+          % (train_s, coverage, err[~u].max() if (~u).any() else 0, np.median(err[~u]) if (~u).any() else 0))
+    assert np.all(err[u] <= 1e-12 + 1e-12 * np.abs(want[u]))  # fallback rows are the PDE
+    assert np.all(err[~u] <= 1e-4)
+    assert coverage > 0.5
+    # gain: 65,536 rows through the network vs the march on a 256-row sample
+    xb = torch.tensor(W.surrogate_draws(65536, seed=32)).cuda()
+    yb = torch.empty(65536, dtype=torch.float32, device="cuda")
+    H.hjm_surrogate_forward(h, xb, yb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
         H.hjm_surrogate_forward(h, xb, yb)
+    torch.cuda.synchronize()
+    net_per_row = (time.perf_counter() - t0) / 5 / 65536
+    xs = W.surrogate_draws(256, seed=33)
+    items = [W.surrogate_item(r, label) for r in xs]
+    H.hjm_price_batch(items, "fp32")
+    t0 = time.perf_counter()
+    H.hjm_price_batch(items, "fp32")
+    pde_per_row = (time.perf_counter() - t0) / 256
+    print("surrogate: %.3g s/row vs march %.3g s/row: %.0fx" % (net_per_row, pde_per_row, pde_per_row / net_per_row))
+    assert pde_per_row / net_per_row > 100
+
+
+def test_calibration_with_the_surrogate(env, trained):
+    # The use the surrogate is built for: fit (lambda, epsilon, rho) to a
+    # strip of caplet prices made by the PDE (8 expiries x 5 strikes, flat
+    # curve) with one least-squares solver and start, four ways: the march in
+    # the loop; the network in the loop (hjm_surrogate_forward); the gated
+    # network (hjm_surrogate_infer, untrusted rows priced by the march); then
+    # the march again, started from the network's answer (the final PDE
+    # confirmation).
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    torch, H = env
+    h, label, _ = trained
+    F, dl = 0.04, 0.5
+    kap, th = 0.1, 1.0
+    true = np.array([0.011, 0.35, -0.3])
+    rows = []
+    for T in range(1, 9):
+        for dk in (-0.015, -0.0075, 0.0, 0.0075, 0.015):
+            rows.append([kap, 0.0, th, 0.0, 0.0, float(T), dl, F + dk, F])
+    rows = np.array(rows, dtype=np.float32)
+
+    def with_params(p):
+        x = rows.copy()
+        x[:, 1], x[:, 3], x[:, 4] = p[0], p[1], p[2]
+        return x
+
+    target = _pde_forward_premium(H, with_params(true), label)
+    n = len(rows)
+    xd = torch.empty((n, 9), dtype=torch.float32, device="cuda")
+    yd = torch.empty(n, dtype=torch.float32, device="cuda")
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    used = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    fallback = []
+    # unknowns q = (lambda / 0.01, epsilon, rho), all of order one, so that
+    # the solver's relative finite-difference steps suit each of them
+    S = np.array([0.01, 1.0, 1.0])
+
+    def resid_net(q):
+        xd.copy_(torch.from_numpy(with_params(q * S)))
+        H.hjm_surrogate_forward(h, xd, yd)
+        return (yd.cpu().numpy().astype(np.float64) * (dl * 0.01) - target) / 1e-4
+
+    def resid_gated(q):
+        xd.copy_(torch.from_numpy(with_params(q * S)))
+        H.hjm_surrogate_infer(h, xd, out, used)
+        fallback.append(int(used.sum().item()))
+        return (out.cpu().numpy() - target) / 1e-4
+
+    def resid_pde(q):
+        return (_pde_forward_premium(H, with_params(q * S), label) - target) / 1e-4
+
+    kw = dict(bounds=(np.array([0.005, 0.1, -0.7]) / S, np.array([0.015, 0.6, 0.3]) / S), diff_step=1e-2,
+              xtol=1e-10, ftol=1e-10, max_nfev=100)
+    start = np.array([0.008, 0.2, 0.0]) / S
+    res = {}
+    for name, fun in (("pde", resid_pde), ("net", resid_net), ("gated", resid_gated), ("confirm", resid_pde)):
+        x0 = res["net"][0] / S if name == "confirm" else start
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(5):
-            H.hjm_surrogate_forward(h, xb, yb)
-        torch.cuda.synchronize()
-        net_per_row = (time.perf_counter() - t0) / 5 / 65536
-        xs = W.surrogate_draws(256, seed=33)
-        items = [W.surrogate_item(r, label) for r in xs]
-        H.hjm_price_batch(items, "fp32")
-        t0 = time.perf_counter()
-        H.hjm_price_batch(items, "fp32")
-        pde_per_row = (time.perf_counter() - t0) / 256
-        print("surrogate: %.3g s/row vs march %.3g s/row: %.0fx" % (net_per_row, pde_per_row, pde_per_row / net_per_row))
-        assert pde_per_row / net_per_row > 100
-    finally:
-        H.hjm_surrogate_destroy(h)
+        r = scipy_opt.least_squares(fun, x0, **kw)
+        res[name] = (r.x * S, time.perf_counter() - t0, r.nfev)
+    for name, (x, secs, nfev) in res.items():
+        print("calibration %s: lambda %.5f eps %.4f rho %.4f (true %s) in %.3f s, %d evaluations"
+              % (name, x[0], x[1], x[2], true, secs, nfev))
+    print("calibration gated: %d of %d rows priced by the march over %d evaluations"
+          % (sum(fallback), n * len(fallback), len(fallback)))
+    # the march recovers its own parameters, from the plain start and from
+    # the network's answer; the network gets lambda to within its price
+    # error, far faster than the march
+    for name in ("pde", "confirm"):
+        x = res[name][0]
+        assert abs(x[0] / true[0] - 1) < 1e-3 and abs(x[1] - true[1]) < 0.02 and abs(x[2] - true[2]) < 0.05, name
+    for name in ("net", "gated"):
+        assert abs(res[name][0][0] / true[0] - 1) < 0.05, name
+    assert res["pde"][1] > 5 * res["net"][1]

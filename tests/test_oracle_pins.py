@@ -537,11 +537,42 @@ def test_bond_reproduces_curve_for_any_volatility(orc, lam, eps, rho):
     assert abs(p - math.exp(-0.15)) < 1e-5
 
 
+def _golden():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_printed_values.json")) as f:
+        return json.load(f)
+
+
+def test_golden_market_set_is_the_workload(orc):
+    # The 2007 market set as the paper prints it (Section 3.3) is the one the
+    # workloads use: the model constants and p(0,T) = 1.04^-T (a flat
+    # forward ln 1.04).
+    g = _golden()["market_set_2007"]
+    it = W.paper_2007_set()
+    m = it["model"]
+    for key, name in (("kappa", "kappa"), ("lambda", "lambda_"), ("gamma", "gamma"), ("epsilon", "epsilon"),
+                      ("theta", "theta"), ("rho", "rho")):
+        assert m[name] == g[key], key
+    for T in (1.0, 5.0, 19.0):
+        assert abs(orc.curve_P(it["curve"], T) - g["discount_base"] ** -T) < 1e-15
+
+
+def test_golden_computation_time_table_is_consistent():
+    # Section 6.3's table: Ntotal = 12 steps per year x Tc, TMc = Tc + 1 (the
+    # derived grid-point-steps/s quoted as context are 250,000 x Ntotal / time).
+    g = _golden()["computation_time"]
+    for TMc, Tc, Ntot, secs in g["rows"]:
+        assert Ntot == g["steps_per_year"] * Tc and TMc == Tc + 1 and secs > 0
+
+
 def test_bond_gamma_09_paper_set(orc):
-    # Section 3.3's 2007 parameters (gamma = 0.9, r >= 0, p(0,T) = 1.04^-T).
+    # Section 3.3's 2007 parameters (gamma = 0.9, r >= 0, p(0,T) = 1.04^-T):
+    # the bond within Section 6.1's printed accuracy of the exact price.
+    g = _golden()
     it = W.paper_2007_set()
     p = orc.price(it)
-    assert abs(p - 1.04 ** -5.0) < 1e-5
+    assert abs(p - g["market_set_2007"]["discount_base"] ** -5.0) < g["bond_accuracy"]["max_abs_error"]
 
 
 def test_bond_field_converges_to_exact(orc):
