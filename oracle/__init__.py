@@ -28,9 +28,13 @@ _lock = threading.Lock()
 _lib = None
 
 
+MAX_KNOTS = 32
+
+
 class Curve(C.Structure):
     _fields_ = [("kind", C.c_int), ("flat_rate", C.c_double), ("beta0", C.c_double),
-                ("beta1", C.c_double), ("beta2", C.c_double), ("tau", C.c_double)]
+                ("beta1", C.c_double), ("beta2", C.c_double), ("tau", C.c_double),
+                ("n_knots", C.c_int), ("knot_t", C.c_double * MAX_KNOTS), ("knot_P", C.c_double * MAX_KNOTS)]
 
 
 class Model(C.Structure):
@@ -55,8 +59,14 @@ class Inst(C.Structure):
 
 def _fill(struct_t, d):
     s = struct_t()
-    for name, _ in struct_t._fields_:
-        setattr(s, name, d[name])
+    for name, typ in struct_t._fields_:
+        if hasattr(typ, "_length_"):  # fixed-size array: the given values, zero-padded
+            vals = [float(v) for v in d.get(name, ())]
+            getattr(s, name)[:len(vals)] = vals
+        elif name == "n_knots":
+            setattr(s, name, int(d.get(name, 0)))
+        else:
+            setattr(s, name, d[name])
     return s
 
 

@@ -52,6 +52,11 @@
  *       r integral is closed form, the y integral 8-point Gauss-Legendre.
  *   R12 r^gamma is taken as 1 when gamma == 0 (any r), so negative rates are
  *       allowed in the Gaussian case only.
+ *   R14 Discrete initial curve (Section 6.1): the paper smooths the discount
+ *       factors with splines so that df(0,T)/dT is continuous; here a natural
+ *       cubic spline of ln P(0,t) through (0, 0) and the knots (zero second
+ *       derivative at both ends), f = -(ln P)', df/dt = -(ln P)''; past the
+ *       last knot ln P continues linearly (flat forward).
  *   R13 Craig-Sneyd family: a second explicit stage and a second sweep of
  *       the three line solves, as In 't Hout and Welfert define CS, modified
  *       CS and Hundsdorfer-Verwer. Every explicit operator of such a step is
@@ -68,8 +73,17 @@
 
 static const double ORC_PI = 3.14159265358979323846;
 
+/* Natural cubic spline of ln P(0,t) of a discrete curve (R14). */
+typedef struct {
+    int m;                                 /* nodes: the origin and the knots */
+    double tau[ORC_MAX_KNOTS + 1];         /* node times */
+    double y[ORC_MAX_KNOTS + 1];           /* ln P(0, tau) */
+    double M[ORC_MAX_KNOTS + 1];           /* second derivatives */
+} orc_knot_spline;
+
 struct orc_ctx {
     orc_curve c;
+    orc_knot_spline sp;  /* the discrete curve's spline (kind 2) */
     orc_model m;
     orc_grid g;
     orc_inst in;
@@ -85,10 +99,81 @@ struct orc_ctx {
 
 /* ------------------------------------------------------------------ curve */
 
+/* Natural cubic spline of ln P(0,t) through (0, 0) and the knots (R14):
+ * nodes tau_0 = 0 < tau_1 < ... < tau_{m-1}, values y_i = ln P(0, tau_i),
+ * second derivatives M_i with M_0 = M_{m-1} = 0 and, inside, continuity of
+ * the first derivative:
+ *   h_{i-1} M_{i-1} + 2 (h_{i-1} + h_i) M_i + h_i M_{i+1}
+ *       = 6 ((y_{i+1} - y_i) / h_i - (y_i - y_{i-1}) / h_{i-1}). */
+static void knot_spline_build(const orc_curve* c, orc_knot_spline* sp)
+{
+    int m = c->n_knots + 1;
+    sp->m = m;
+    sp->tau[0] = 0.0;
+    sp->y[0] = 0.0;
+    for (int i = 1; i < m; ++i) {
+        sp->tau[i] = c->knot_t[i - 1];
+        sp->y[i] = log(c->knot_P[i - 1]);
+    }
+    for (int i = 0; i < m; ++i) sp->M[i] = 0.0;
+    if (m < 3) return;
+    /* Thomas on the interior unknowns M_1 .. M_{m-2} */
+    double cp[ORC_MAX_KNOTS + 1], dp[ORC_MAX_KNOTS + 1];
+    for (int i = 1; i <= m - 2; ++i) {
+        double hl = sp->tau[i] - sp->tau[i - 1], hr = sp->tau[i + 1] - sp->tau[i];
+        double a = hl, b = 2.0 * (hl + hr), cc = hr;
+        double d = 6.0 * ((sp->y[i + 1] - sp->y[i]) / hr - (sp->y[i] - sp->y[i - 1]) / hl);
+        if (i == 1) {
+            cp[i] = cc / b;
+            dp[i] = d / b;
+        } else {
+            double piv = b - a * cp[i - 1];
+            cp[i] = cc / piv;
+            dp[i] = (d - a * dp[i - 1]) / piv;
+        }
+    }
+    sp->M[m - 2] = dp[m - 2];
+    for (int i = m - 3; i >= 1; --i) sp->M[i] = dp[i] - cp[i] * sp->M[i + 1];
+}
+
+/* ln P(0,t) and its first two derivatives from the spline. */
+static void knot_spline_eval(const orc_knot_spline* sp, double t, double* s, double* ds, double* d2s)
+{
+    int m = sp->m;
+    if (t >= sp->tau[m - 1]) {
+        /* slope at the last node from the last piece (b = 1, a = 0) */
+        double h = sp->tau[m - 1] - sp->tau[m - 2];
+        double slope = (sp->y[m - 1] - sp->y[m - 2]) / h + h / 6.0 * (sp->M[m - 2] + 2.0 * sp->M[m - 1]);
+        *s = sp->y[m - 1] + slope * (t - sp->tau[m - 1]);
+        *ds = slope;
+        *d2s = 0.0;
+        return;
+    }
+    int i = 0;
+    while (i < m - 2 && t >= sp->tau[i + 1]) ++i;
+    double h = sp->tau[i + 1] - sp->tau[i];
+    double a = (sp->tau[i + 1] - t) / h, b = (t - sp->tau[i]) / h;
+    *s = a * sp->y[i] + b * sp->y[i + 1] + ((a * a * a - a) * sp->M[i] + (b * b * b - b) * sp->M[i + 1]) * h * h / 6.0;
+    *ds = (sp->y[i + 1] - sp->y[i]) / h + (-(3.0 * a * a - 1.0) * sp->M[i] + (3.0 * b * b - 1.0) * sp->M[i + 1]) * h / 6.0;
+    *d2s = a * sp->M[i] + b * sp->M[i + 1];
+}
+
+static void knot_curve_at(const orc_curve* c, double t, double* s, double* ds, double* d2s)
+{
+    orc_knot_spline sp;
+    knot_spline_build(c, &sp);
+    knot_spline_eval(&sp, t, s, ds, d2s);
+}
+
 /* Initial forward curve f(0,t), Section 2 (f = -d ln p / dT). */
 double orc_curve_f(const orc_curve* c, double t)
 {
     if (c->kind == 0) return c->flat_rate;
+    if (c->kind == 2) {
+        double s, ds, d2s;
+        knot_curve_at(c, t, &s, &ds, &d2s);
+        return -ds;
+    }
     double e = exp(-t / c->tau);
     return c->beta0 + c->beta1 * e + c->beta2 * (t / c->tau) * e;
 }
@@ -96,6 +181,11 @@ double orc_curve_f(const orc_curve* c, double t)
 double orc_curve_dfdt(const orc_curve* c, double t)
 {
     if (c->kind == 0) return 0.0;
+    if (c->kind == 2) {
+        double s, ds, d2s;
+        knot_curve_at(c, t, &s, &ds, &d2s);
+        return -d2s;
+    }
     double e = exp(-t / c->tau);
     return -c->beta1 / c->tau * e + c->beta2 / c->tau * e * (1.0 - t / c->tau);
 }
@@ -104,6 +194,11 @@ double orc_curve_dfdt(const orc_curve* c, double t)
 double orc_curve_P(const orc_curve* c, double t)
 {
     if (c->kind == 0) return exp(-c->flat_rate * t);
+    if (c->kind == 2) {
+        double s, ds, d2s;
+        knot_curve_at(c, t, &s, &ds, &d2s);
+        return exp(s);
+    }
     double e = exp(-t / c->tau);
     double integral = c->beta0 * t + c->beta1 * c->tau * (1.0 - e)
                     + c->beta2 * (c->tau * (1.0 - e) - t * e);
@@ -212,8 +307,15 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
                     g->r_min, g->r_max, g->y_max, g->v_max, g->alpha_r, g->alpha_y,
                     g->alpha_v, g->k_r, g->k_v, g->theta_adi, in->T, in->TM, in->K};
     if (!finite_all(chk, (int)(sizeof chk / sizeof chk[0]))) return 1;
-    if (c->kind != 0 && c->kind != 1) return 1;
+    if (c->kind != 0 && c->kind != 1 && c->kind != 2) return 1;
     if (c->kind == 1 && !(c->tau > 0.0)) return 1;
+    if (c->kind == 2) {
+        if (c->n_knots < 1 || c->n_knots > ORC_MAX_KNOTS) return 1;
+        for (int i = 0; i < c->n_knots; ++i) {
+            if (!isfinite(c->knot_t[i]) || !isfinite(c->knot_P[i]) || !(c->knot_P[i] > 0.0)) return 1;
+            if (!(c->knot_t[i] > (i ? c->knot_t[i - 1] : 0.0))) return 1;
+        }
+    }
     if (g->n_r < 5 || g->n_v < 5 || g->n_y < 5 || g->n_steps < 1) return 1;
     if (!(g->r_max > g->r_min) || !(g->y_max > 0.0) || !(g->v_max > 0.0)) return 1;
     if (m->gamma < 0.0 || m->gamma > 1.0) return 1;
@@ -233,6 +335,7 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
     orc_ctx* x = (orc_ctx*)calloc(1, sizeof *x);
     if (!x) return 1;
     x->c = *c;
+    if (c->kind == 2) knot_spline_build(c, &x->sp);
     x->m = *m;
     x->g = *g;
     x->in = *in;
@@ -317,7 +420,17 @@ static coeffs coeffs_at(const orc_ctx* x, int i, int k, int j, double t)
     q.zrr = 0.5 * m->lambda * m->lambda * r2g * v;
     q.zvv = 0.5 * m->epsilon * m->epsilon * v;
     q.zrv = m->lambda * rg * m->epsilon * m->rho * v;
-    q.mur = orc_curve_dfdt(&x->c, t) - m->kappa * (r - orc_curve_f(&x->c, t)) + y;
+    double f0, df0;
+    if (x->c.kind == 2) {
+        double s, ds, d2s;
+        knot_spline_eval(&x->sp, t, &s, &ds, &d2s);
+        f0 = -ds;
+        df0 = -d2s;
+    } else {
+        f0 = orc_curve_f(&x->c, t);
+        df0 = orc_curve_dfdt(&x->c, t);
+    }
+    q.mur = df0 - m->kappa * (r - f0) + y;
     q.muv = m->theta * (1.0 - v);
     q.muy = m->lambda * m->lambda * r2g * v - 2.0 * m->kappa * y;
     q.r = r;

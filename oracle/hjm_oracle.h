@@ -30,10 +30,18 @@ extern "C" {
 
 /* Initial forward curve f(0,t). kind 0: flat f(0,t)=flat_rate.
  * kind 1: Nelson-Siegel in instantaneous-forward form
- *   f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}. */
+ *   f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}.
+ * kind 2: discrete curve (Section 6.1): discount factors knot_P[i] at
+ *   maturities knot_t[i] (0 < knot_t[0] < ... , 1 <= n_knots <= ORC_MAX_KNOTS),
+ *   smoothed by a natural cubic spline of ln P(0,t) through (0, 0) and the
+ *   knots; ln P continues linearly past the last knot. */
+#define ORC_MAX_KNOTS 32
 typedef struct {
     int kind;
     double flat_rate, beta0, beta1, beta2, tau;
+    int n_knots;
+    double knot_t[ORC_MAX_KNOTS];
+    double knot_P[ORC_MAX_KNOTS];
 } orc_curve;
 
 /* Model parameters of Section 3.1, constant in time. */

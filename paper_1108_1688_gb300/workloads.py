@@ -54,6 +54,35 @@ def ns_curve(beta0, beta1, beta2, tau):
                 beta2=float(beta2), tau=float(tau))
 
 
+MAX_KNOTS = 32
+
+
+def knot_curve(knot_t, knot_P):
+    """Discrete initial curve (Section 6.1): discount factors knot_P at
+    maturities knot_t (increasing, > 0, at most MAX_KNOTS)."""
+    knot_t, knot_P = [float(v) for v in knot_t], [float(v) for v in knot_P]
+    return dict(kind=2, flat_rate=0.0, beta0=0.0, beta1=0.0, beta2=0.0, tau=1.0,
+                n_knots=len(knot_t), knot_t=knot_t, knot_P=knot_P)
+
+
+# Maturities of a typical market discount curve: 3 and 6 months, 1 to 10
+# years yearly, then 12, 15, 20, 25 and 30 years.
+MARKET_KNOT_TIMES = (0.25, 0.5) + tuple(float(y) for y in range(1, 11)) + (12.0, 15.0, 20.0, 25.0, 30.0)
+
+
+def synthetic_knot_curve(seed, times=MARKET_KNOT_TIMES, bump_bp=5.0):
+    """A seeded discrete curve: continuously compounded zero rates at market
+    maturities, z(t) = z0 + s (1 - e^{-t/5}) with z0 U[0.01, 0.035] and s
+    U[-0.01, 0.025] (upward or inverted curves), each moved by up to bump_bp
+    basis points of quote noise so the knots are not a smooth family;
+    P = e^{-z t}."""
+    rng = np.random.default_rng(seed)
+    z0, sl = rng.uniform(0.01, 0.035), rng.uniform(-0.01, 0.025)
+    Ps = [math.exp(-(z0 + sl * -math.expm1(-t / 5.0) + rng.uniform(-1.0, 1.0) * bump_bp * 1e-4) * t)
+          for t in times]
+    return knot_curve(times, Ps)
+
+
 def model(kappa, lambda_, gamma, theta, epsilon, rho, v0=1.0):
     return dict(kappa=float(kappa), lambda_=float(lambda_), gamma=float(gamma),
                 theta=float(theta), epsilon=float(epsilon), rho=float(rho), v0=float(v0))
@@ -69,9 +98,16 @@ def caplet(T, TM, K=0.0, atm_relative=True):
 
 
 def curve_level_bound(curve):
-    """An upper bound on |f(0,t)| read off the parameters (x e^{-x} <= 1/e)."""
+    """An upper bound on |f(0,t)| read off the parameters (x e^{-x} <= 1/e);
+    for a discrete curve a rough scale: twice the largest zero rate or
+    forward between knots (the spline's forward can overshoot them)."""
     if curve["kind"] == 0:
         return abs(curve["flat_rate"])
+    if curve["kind"] == 2:
+        ts = [0.0] + list(curve["knot_t"][:curve["n_knots"]])
+        ls = [0.0] + [math.log(p) for p in curve["knot_P"][:curve["n_knots"]]]
+        fwd = [abs((ls[i] - ls[i + 1]) / (ts[i + 1] - ts[i])) for i in range(len(ts) - 1)]
+        return 2.0 * max(fwd)
     return abs(curve["beta0"]) + abs(curve["beta1"]) + abs(curve["beta2"]) / math.e
 
 

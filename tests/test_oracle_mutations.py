@@ -64,6 +64,15 @@ MUTATIONS = [
      "if (sch == 4)\n        for (long p = 0; p < N; ++p) z[p] -= a[p];"),
     ("CS family explicit operators at t^n", "int mid = x->g.explicit_midpoint || x->g.scheme != 0;",
      "int mid = x->g.explicit_midpoint;"),
+    ("spline right-hand side halved", "double d = 6.0 * ((sp->y[i + 1] - sp->y[i]) / hr",
+     "double d = 3.0 * ((sp->y[i + 1] - sp->y[i]) / hr"),
+    ("spline end slope sign", "+ h / 6.0 * (sp->M[m - 2] + 2.0 * sp->M[m - 1]);",
+     "- h / 6.0 * (sp->M[m - 2] + 2.0 * sp->M[m - 1]);"),
+    ("spline last interval never used", "while (i < m - 2 && t >= sp->tau[i + 1]) ++i;",
+     "while (i < m - 3 && t >= sp->tau[i + 1]) ++i;"),
+    ("knot forward sign", "        knot_curve_at(c, t, &s, &ds, &d2s);\n        return -ds;",
+     "        knot_curve_at(c, t, &s, &ds, &d2s);\n        return ds;"),
+    ("knot drift curvature sign in the PDE", "        df0 = -d2s;", "        df0 = d2s;"),
 ]
 
 
@@ -102,6 +111,11 @@ def _pins(orc):
     yield lambda: P.test_config1_bond_price(orc)
     yield lambda: P.test_bond_ns_curve_converges(orc)
     yield lambda: P.test_gaussian_limit_converges_to_closed_form(orc, P.W.flat_curve(0.03))
+    yield lambda: P.test_knot_curve_interpolates_the_knots(orc)
+    yield lambda: P.test_knot_curve_of_a_flat_curve_is_flat(orc)
+    yield lambda: P.test_knot_curve_is_the_natural_cubic_spline_of_ln_p(orc)
+    yield lambda: P.test_knot_curve_continues_flat_past_the_last_knot(orc)
+    yield lambda: P.test_knot_curve_bond_reprices_the_curve(orc)
     yield lambda: P.test_craig_sneyd_reductions(orc)
     for sch in range(4):
         yield lambda sch=sch: P.test_craig_sneyd_family_time_order(orc, sch)

@@ -88,17 +88,112 @@ def fields(X):
 # ------------------------------------------------------- curve and closed forms
 
 @pytest.mark.parametrize("curve", [W.flat_curve(0.03), W.ns_curve(0.03, -0.01, 0.015, 2.0),
-                                   W.ns_curve(0.045, 0.02, -0.02, 4.5)])
+                                   W.ns_curve(0.045, 0.02, -0.02, 4.5), W.synthetic_knot_curve(5)])
 def test_discount_is_exp_minus_integral_of_forward(orc, curve):
-    # Section 2: p(0,T) = exp(-int_0^T f(0,s) ds), f = -d ln p / dT.
-    for T in (0.5, 3.0, 10.0):
-        I, _ = integrate.quad(lambda s: orc.curve_f(curve, s), 0.0, T, epsabs=1e-14)
+    # Section 2: p(0,T) = exp(-int_0^T f(0,s) ds), f = -d ln p / dT (for the
+    # knot curve between knots: df/dt has kinks at the knots).
+    for T in ((0.5, 3.0, 10.0) if curve["kind"] != 2 else (0.6, 3.3, 10.5)):
+        kinks = [t for t in curve.get("knot_t", []) if t < T] or None
+        I, _ = integrate.quad(lambda s: orc.curve_f(curve, s), 0.0, T, epsabs=1e-14, points=kinks)
         assert orc.curve_P(curve, T) == pytest.approx(math.exp(-I), rel=1e-12)
         h = 1e-5
         fd = -(math.log(orc.curve_P(curve, T + h)) - math.log(orc.curve_P(curve, T - h))) / (2 * h)
         assert fd == pytest.approx(orc.curve_f(curve, T), abs=1e-9)
         dfd = (orc.curve_f(curve, T + h) - orc.curve_f(curve, T - h)) / (2 * h)
         assert orc.curve_dfdt(curve, T) == pytest.approx(dfd, abs=1e-9)
+
+
+# --------------------------------------------------- discrete (knot) curve
+
+KNOT_CURVES = [W.synthetic_knot_curve(s) for s in (1, 2, 3)]
+
+
+def test_knot_curve_interpolates_the_knots(orc):
+    # Section 6.1: the smoothed curve passes through the discrete discount
+    # factors, and P(0,0) = 1.
+    for c in KNOT_CURVES:
+        assert orc.curve_P(c, 0.0) == 1.0
+        for t, P in zip(c["knot_t"], c["knot_P"]):
+            assert orc.curve_P(c, t) == pytest.approx(P, rel=1e-14)
+
+
+def test_knot_curve_of_a_flat_curve_is_flat(orc):
+    # Knots of a flat curve: ln P is linear, which the natural spline
+    # reproduces exactly: f = r and df/dt = 0 everywhere, past the last knot too.
+    r = 0.037
+    c = W.knot_curve(W.MARKET_KNOT_TIMES, [math.exp(-r * t) for t in W.MARKET_KNOT_TIMES])
+    for t in np.linspace(0.0, 40.0, 81):
+        assert orc.curve_f(c, t) == pytest.approx(r, abs=1e-13)
+        assert abs(orc.curve_dfdt(c, t)) < 1e-12
+        assert orc.curve_P(c, t) == pytest.approx(math.exp(-r * t), rel=1e-12)
+
+
+def test_knot_curve_is_the_natural_cubic_spline_of_ln_p(orc):
+    # The reading of Section 6.1's smoothing: the textbook natural cubic
+    # spline of ln P through (0, 0) and the knots (scipy's CubicSpline with
+    # bc_type="natural"); f = -(ln P)', df/dt = -(ln P)''.
+    from scipy.interpolate import CubicSpline
+    for c in KNOT_CURVES:
+        tau = np.array([0.0] + c["knot_t"])
+        sp = CubicSpline(tau, np.log(np.array([1.0] + c["knot_P"])), bc_type="natural")
+        for t in np.concatenate([np.linspace(0.0, tau[-1], 301), tau]):
+            assert math.log(orc.curve_P(c, t)) == pytest.approx(float(sp(t)), abs=1e-13)
+            assert orc.curve_f(c, t) == pytest.approx(-float(sp(t, 1)), abs=1e-11)
+            assert orc.curve_dfdt(c, t) == pytest.approx(-float(sp(t, 2)), abs=1e-10)
+
+
+def test_knot_curve_continues_flat_past_the_last_knot(orc):
+    # Past the last knot ln P continues with the spline's end slope (the
+    # natural end has zero curvature): f is continuous there and constant
+    # after, df/dt = 0.
+    for c in KNOT_CURVES:
+        tl = c["knot_t"][-1]
+        fl = orc.curve_f(c, tl - 1e-9)
+        for t in (tl, tl + 0.5, tl + 7.0):
+            assert orc.curve_f(c, t) == pytest.approx(fl, abs=1e-9)
+            assert orc.curve_dfdt(c, t) == 0.0
+            assert orc.curve_P(c, t) == pytest.approx(c["knot_P"][-1] * math.exp(-fl * (t - tl)), rel=1e-9)
+
+
+def test_knot_curve_converges_to_the_sampled_curve(orc):
+    # Knots sampled from a smooth curve (Nelson-Siegel) at spacing h: the
+    # spline's forward converges to the curve's forward at second order away
+    # from the ends (the natural end conditions are first order at t = 0).
+    ns = W.ns_curve(0.035, -0.015, 0.02, 2.5)
+    errs = []
+    for h in (1.0, 0.5, 0.25):
+        ts = np.arange(h, 8.0 + 1e-9, h)  # 8, 16, 32 knots
+        c = W.knot_curve(ts, [orc.curve_P(ns, t) for t in ts])
+        errs.append(max(abs(orc.curve_f(c, t) - orc.curve_f(ns, t)) for t in np.linspace(1.5, 6.5, 21)))
+    assert errs[1] < errs[0] / 3.0 and errs[2] < errs[1] / 3.0, errs
+
+
+def test_knot_curve_bond_reprices_the_curve(orc):
+    # Section 6.1: with the smoothed discrete curve the bond still converges
+    # to P(0,T), O(1e-5) on moderate meshes, more refinement needed below.
+    m = W.model(**W.CONFIG1_MODEL)
+    errs = []
+    c = KNOT_CURVES[0]
+    for n in (24, 48):
+        it = W.item(c, m, W.default_grid(c, m, 5.0, n, n // 2, n // 2, 2 * n + 2, explicit_midpoint=1), W.bond(5.0))
+        errs.append(abs(orc.price(it) - orc.curve_P(c, 5.0)))
+    assert errs[1] < 1e-4 and errs[0] > 3.0 * errs[1], errs
+    c = KNOT_CURVES[1]
+    it = W.item(c, m, W.default_grid(c, m, 5.0, 40, 20, 20, 100, explicit_midpoint=1), W.bond(5.0))
+    assert abs(orc.price(it) - orc.curve_P(c, 5.0)) < 1e-5
+
+
+def test_knot_curve_rejects_bad_knots(orc):
+    good = W.synthetic_knot_curve(4)
+    for mutate in (lambda c: c.update(n_knots=0), lambda c: c.update(n_knots=33),
+                   lambda c: c["knot_t"].__setitem__(3, c["knot_t"][2]),
+                   lambda c: c["knot_P"].__setitem__(1, -0.5), lambda c: c["knot_t"].__setitem__(0, 0.0)):
+        c = {k: (list(v) if isinstance(v, list) else v) for k, v in good.items()}
+        mutate(c)
+        it = W.with_grid(W.config1(), n_steps=2)
+        it["curve"] = c
+        with pytest.raises(orc.OracleError):
+            orc.price(it)
 
 
 def test_G_is_integral_of_decay(orc):
