@@ -52,12 +52,23 @@ typedef enum { HJM_FP64 = 0, HJM_FP32 = 1, HJM_MIXED = 2 } hjm_precision;
 
 /* Initial forward curve f(0,t) (Section 2: p(0,T) = exp(-int_0^T f(0,s) ds)).
  * FLAT: f = flat_rate. NELSON_SIEGEL (instantaneous-forward form):
- * f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}, tau > 0. */
-typedef enum { HJM_CURVE_FLAT = 0, HJM_CURVE_NELSON_SIEGEL = 1 } hjm_curve_kind;
+ * f(0,t) = beta0 + beta1 e^{-t/tau} + beta2 (t/tau) e^{-t/tau}, tau > 0.
+ * KNOTS (the discrete curve of Section 6.1): discount factors knot_P[i] > 0
+ * at maturities 0 < knot_t[0] < knot_t[1] < ..., 1 <= n_knots <=
+ * HJM_MAX_KNOTS, smoothed by the natural cubic spline of ln P(0,t) through
+ * (0, 0) and the knots (f = -(ln P)', df/dt = -(ln P)'' continuous; the
+ * spline is built on the device by the set-up); past the last knot ln P
+ * continues linearly (flat forward). The knot fields are ignored for the
+ * other kinds. */
+typedef enum { HJM_CURVE_FLAT = 0, HJM_CURVE_NELSON_SIEGEL = 1, HJM_CURVE_KNOTS = 2 } hjm_curve_kind;
+#define HJM_MAX_KNOTS 32
 typedef struct {
     int kind;                 /* hjm_curve_kind */
     double flat_rate;
     double beta0, beta1, beta2, tau;
+    int n_knots;
+    double knot_t[HJM_MAX_KNOTS];
+    double knot_P[HJM_MAX_KNOTS];
 } hjm_curve;
 
 /* Model of Section 3.1, constant in time: mean reversion kappa >= 0,

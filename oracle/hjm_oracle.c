@@ -52,11 +52,6 @@
  *       r integral is closed form, the y integral 8-point Gauss-Legendre.
  *   R12 r^gamma is taken as 1 when gamma == 0 (any r), so negative rates are
  *       allowed in the Gaussian case only.
- *   R14 Discrete initial curve (Section 6.1): the paper smooths the discount
- *       factors with splines so that df(0,T)/dT is continuous; here a natural
- *       cubic spline of ln P(0,t) through (0, 0) and the knots (zero second
- *       derivative at both ends), f = -(ln P)', df/dt = -(ln P)''; past the
- *       last knot ln P continues linearly (flat forward).
  *   R13 Craig-Sneyd family: a second explicit stage and a second sweep of
  *       the three line solves, as In 't Hout and Welfert define CS, modified
  *       CS and Hundsdorfer-Verwer. Every explicit operator of such a step is
@@ -64,6 +59,11 @@
  *       explicit_midpoint says), which keeps the schemes second order with
  *       the time-dependent drift; the implicit stages use the same line
  *       operators as the Douglas stages (R5, R6, R8).
+ *   R14 Discrete initial curve (Section 6.1): the paper smooths the discount
+ *       factors with splines so that df(0,T)/dT is continuous; here a natural
+ *       cubic spline of ln P(0,t) through (0, 0) and the knots (zero second
+ *       derivative at both ends), f = -(ln P)', df/dt = -(ln P)''; past the
+ *       last knot ln P continues linearly (flat forward).
  */
 #include "hjm_oracle.h"
 

@@ -80,10 +80,29 @@ static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const 
                      m.theta, m.epsilon, m.rho, m.v0, g.r_min, g.r_max, g.y_max, g.v_max, g.alpha_r,
                      g.alpha_y, g.alpha_v, g.k_r, g.k_v, g.theta_adi}))
         return fail(HJM_EINVAL, "non-finite curve, model or grid parameter");
-    if (c.kind != HJM_CURVE_FLAT && c.kind != HJM_CURVE_NELSON_SIEGEL)
+    if (c.kind != HJM_CURVE_FLAT && c.kind != HJM_CURVE_NELSON_SIEGEL && c.kind != HJM_CURVE_KNOTS)
         return fail(HJM_EINVAL, "unknown curve kind %d", c.kind);
     if (c.kind == HJM_CURVE_NELSON_SIEGEL && !(c.tau > 0.0))
         return fail(HJM_EINVAL, "Nelson-Siegel tau must be > 0");
+    double r00 = c.kind == HJM_CURVE_FLAT ? c.flat_rate : c.beta0 + c.beta1;  // f(0,0)
+    if (c.kind == HJM_CURVE_KNOTS) {
+        if (c.n_knots < 1 || c.n_knots > HJM_MAX_KNOTS)
+            return fail(HJM_EINVAL, "n_knots must be in [1, %d]", HJM_MAX_KNOTS);
+        for (int i = 0; i < c.n_knots; ++i) {
+            if (!isfinite(c.knot_t[i]) || !isfinite(c.knot_P[i]) || !(c.knot_P[i] > 0.0))
+                return fail(HJM_EINVAL, "knot %d: non-finite maturity or non-positive discount factor", i);
+            if (!(c.knot_t[i] > (i ? c.knot_t[i - 1] : 0.0)))
+                return fail(HJM_EINVAL, "knot maturities must be positive and increasing");
+        }
+        KnotCurve kc;
+        kc.n = c.n_knots;
+        memcpy(kc.t, c.knot_t, sizeof kc.t);
+        memcpy(kc.P, c.knot_P, sizeof kc.P);
+        knot_build(kc);
+        double s0, ds0, d2s0;
+        knot_eval(kc, 0.0, s0, ds0, d2s0);
+        r00 = -ds0;
+    }
     if (g.n_r < 5 || g.n_v < 5 || g.n_y < 5) return fail(HJM_EINVAL, "each axis needs >= 5 nodes");
     if ((long long)g.n_r * g.n_v * g.n_y > 0x7fffffffLL)
         return fail(HJM_ERANGE, "n_r * n_v * n_y above 2^31 - 1 nodes");  // 32-bit offsets in the kernels
@@ -103,8 +122,7 @@ static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const 
         return fail(HJM_EINVAL, "explicit_midpoint must be 0 or 1");
     if (g.scheme < HJM_SCHEME_DOUGLAS || g.scheme > HJM_SCHEME_HV)
         return fail(HJM_EINVAL, "unknown scheme %d", g.scheme);
-    const double r00 = c.kind == HJM_CURVE_FLAT ? c.flat_rate : c.beta0 + c.beta1;  // f(0,0)
-    if (r00 < g.r_min || r00 > g.r_max) return fail(HJM_EINVAL, "f(0,0) outside [r_min, r_max]");
+    if (!(r00 >= g.r_min && r00 <= g.r_max)) return fail(HJM_EINVAL, "f(0,0) outside [r_min, r_max]");
     if (pass1_chunk(g.n_r) == 0) return fail(HJM_ERANGE, "n_r = %d above 512", g.n_r);
     if (elem) {
         const int lim = max_strided_len(elem, m.gamma > 0.0);
@@ -133,6 +151,9 @@ static InstParams to_params(const hjm_batch_item& it)
     p.b1 = it.curve.beta1;
     p.b2 = it.curve.beta2;
     p.tau = it.curve.tau;
+    p.kc.n = it.curve.kind == HJM_CURVE_KNOTS ? it.curve.n_knots : 0;
+    memcpy(p.kc.t, it.curve.knot_t, sizeof p.kc.t);
+    memcpy(p.kc.P, it.curve.knot_P, sizeof p.kc.P);
     p.kappa = it.model.kappa;
     p.lambda = it.model.lambda;
     p.gamma = it.model.gamma;

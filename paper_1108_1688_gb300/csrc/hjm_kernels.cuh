@@ -29,6 +29,7 @@
 #include <stdint.h>
 
 #include "hjm.h"
+#include "hjm_curve.cuh"
 
 namespace hjm {
 
@@ -36,6 +37,7 @@ namespace hjm {
 struct InstParams {
     int ckind;
     double flat, b0, b1, b2, tau;
+    KnotCurve kc;  // HJM_CURVE_KNOTS: knots as given, spline built by the set-up
     double kappa, lambda, gamma, theta, eps, rho, v0;
     int nr, nv, ny, nsteps;
     double rmin, rmax, ymax, vmax, ar, ay, av, kr, kv;

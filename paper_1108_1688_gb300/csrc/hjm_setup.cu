@@ -14,10 +14,16 @@ namespace hjm {
 
 // ----------------------------------------------------------- curve, bonds
 
-// f(0,t) of the initial curve (flat or Nelson-Siegel forward form).
+// f(0,t) of the initial curve (flat, Nelson-Siegel forward form, or the
+// spline of a discrete curve, Section 6.1).
 __device__ double fwd(const InstParams& p, double t)
 {
     if (p.ckind == HJM_CURVE_FLAT) return p.flat;
+    if (p.ckind == HJM_CURVE_KNOTS) {
+        double s, ds, d2s;
+        knot_eval(p.kc, t, s, ds, d2s);
+        return -ds;
+    }
     const double x = t / p.tau, e = exp(-x);
     return p.b0 + e * (p.b1 + p.b2 * x);
 }
@@ -25,6 +31,11 @@ __device__ double fwd(const InstParams& p, double t)
 __device__ double fwd_slope(const InstParams& p, double t)
 {
     if (p.ckind == HJM_CURVE_FLAT) return 0.0;
+    if (p.ckind == HJM_CURVE_KNOTS) {
+        double s, ds, d2s;
+        knot_eval(p.kc, t, s, ds, d2s);
+        return -d2s;
+    }
     const double x = t / p.tau, e = exp(-x);
     return e * (p.b2 * (1.0 - x) - p.b1) / p.tau;
 }
@@ -33,6 +44,11 @@ __device__ double fwd_slope(const InstParams& p, double t)
 __device__ double discount(const InstParams& p, double t)
 {
     if (p.ckind == HJM_CURVE_FLAT) return exp(-p.flat * t);
+    if (p.ckind == HJM_CURVE_KNOTS) {
+        double s, ds, d2s;
+        knot_eval(p.kc, t, s, ds, d2s);
+        return exp(s);
+    }
     const double x = t / p.tau, e = exp(-x), one_m_e = -expm1(-x);
     return exp(-(p.b0 * t + (p.b1 + p.b2) * p.tau * one_m_e - p.b2 * t * e));
 }
@@ -100,7 +116,11 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
 {
     const int b = blockIdx.x, tid = threadIdx.x, nth = blockDim.x;
     const int nr = g.nr, nv = g.nv, ny = g.ny, ns = g.nsteps;
-    const InstParams p = g.params[b];
+    // The discrete curve's spline, rebuilt from the knots at every set-up;
+    // the later kernels read it from the parameters.
+    if (tid == 0 && g.params[b].ckind == HJM_CURVE_KNOTS) knot_build(g.params[b].kc);
+    __syncthreads();
+    const InstParams& p = g.params[b];
     __shared__ InstDerived D;
     if (tid == 0) {
         double K = 0.0, DM = 1.0;
@@ -343,7 +363,7 @@ __global__ void __launch_bounds__(32) k_split(GroupTables g, int axis, int P)
     const int nv = g.nv, ny = g.ny;
     const int b = axis == 0 ? blockIdx.x : blockIdx.x / nv;
     const int k = axis == 0 ? 0 : blockIdx.x % nv;
-    const InstParams p = g.params[b];
+    const InstParams& p = g.params[b];
     if (axis == 1 && p.gamma != 0.0) return;
     const double w = p.theta_adi * g.derived[b].dt;
     const double* axv = g.axv + (size_t)b * 3 * nv;
@@ -574,7 +594,7 @@ __global__ void k_readout(GroupTables g, const T* U, double* prices, double* ind
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.B) return;
-    const InstParams p = g.params[b];
+    const InstParams& p = g.params[b];
     const InstDerived D = g.derived[b];
     const int nr = g.nr, nv = g.nv;
     double sr, sv;

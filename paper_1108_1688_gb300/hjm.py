@@ -20,16 +20,22 @@ LIB_PATH = os.path.join(_HERE, "_build", "libhjm.so")
 
 HJM_OK, HJM_EINVAL, HJM_ENOMEM, HJM_ECUDA, HJM_ETOL, HJM_ETIMEOUT, HJM_ENUMERIC, HJM_ERANGE = range(8)
 HJM_FP64, HJM_FP32, HJM_MIXED = 0, 1, 2
-HJM_CURVE_FLAT, HJM_CURVE_NELSON_SIEGEL = 0, 1
+HJM_CURVE_FLAT, HJM_CURVE_NELSON_SIEGEL, HJM_CURVE_KNOTS = 0, 1, 2
+HJM_SCHEME_DOUGLAS, HJM_SCHEME_CS, HJM_SCHEME_MCS, HJM_SCHEME_HV = 0, 1, 2, 3
 HJM_ZCB, HJM_CAPLET = 0, 1
 
 PRECISIONS = {"fp64": HJM_FP64, "fp32": HJM_FP32, "mixed": HJM_MIXED,
               HJM_FP64: HJM_FP64, HJM_FP32: HJM_FP32, HJM_MIXED: HJM_MIXED}
 
 
+HJM_MAX_KNOTS = 32
+
+
 class hjm_curve(C.Structure):
     _fields_ = [("kind", C.c_int), ("flat_rate", C.c_double), ("beta0", C.c_double),
-                ("beta1", C.c_double), ("beta2", C.c_double), ("tau", C.c_double)]
+                ("beta1", C.c_double), ("beta2", C.c_double), ("tau", C.c_double),
+                ("n_knots", C.c_int), ("knot_t", C.c_double * HJM_MAX_KNOTS),
+                ("knot_P", C.c_double * HJM_MAX_KNOTS)]
 
 
 class hjm_model_params(C.Structure):
@@ -162,9 +168,17 @@ def _check(status):
 
 def _struct(t, d, rename=None):
     s = t()
-    for name, _ in t._fields_:
+    for name, typ in t._fields_:
         key = (rename or {}).get(name, name)
-        setattr(s, name, d[key])
+        if hasattr(typ, "_length_"):  # fixed-size array: the given values, zero-padded
+            vals = [float(v) for v in d.get(key, ())]
+            if len(vals) > typ._length_:
+                raise ValueError("%s holds at most %d values" % (key, typ._length_))
+            getattr(s, name)[:len(vals)] = vals
+        elif name == "n_knots":
+            setattr(s, name, int(d.get(key, 0)))
+        else:
+            setattr(s, name, d[key])
     return s
 
 
