@@ -179,8 +179,9 @@ hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_precision p
                      double tol_rel, double* price_out, hjm_price_info* info_out);
 
 /* Price n independent instruments, each with its own curve, model and grid,
- * in one call. Items of equal grid shape march together in the same kernel
- * launches. prices_out: n doubles, host or device memory (detected).
+ * in one call. Items of equal grid shape (and scheme) march together in the
+ * same kernel launches; a batch of the same make-up seen again is replayed
+ * as one CUDA graph in which the shape groups run concurrently. prices_out: n doubles, host or device memory (detected).
  * infos_out: n host structs or NULL. Asynchronous on cuda_stream when both
  * outputs are device/NULL; otherwise synchronises before returning. */
 typedef struct {

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <map>
+#include <set>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -217,10 +218,12 @@ struct Buffer {
 struct Workspace {
     Buffer block;                     // fields + tables of all groups
     std::map<std::string, cudaGraphExec_t> graphs;
+    std::set<std::string> seen;       // batch keys launched once without a graph
     void drop_graphs()
     {
         for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
         graphs.clear();
+        seen.clear();
     }
     void release()
     {
@@ -408,8 +411,9 @@ hjm_status group_sequence(const Group& g, size_t elem, cudaStream_t s)
 
 // The whole batch as one CUDA-graph launch: every shape group is a branch of
 // the graph (fork from one node, join into one), so groups of different
-// sizes run concurrently and fill the GPU together. Captured once per set of
-// shapes and buffers, then replayed.
+// sizes run concurrently and fill the GPU together. Captured the second time
+// a set of shapes, launch shapes and buffers is seen, then replayed (the
+// first time the launches go straight to the stream).
 hjm_status batch_graph(Workspace& ws, const std::vector<Group>& groups, size_t elem, cudaStream_t s)
 {
     std::string key = std::to_string(elem);
@@ -421,6 +425,19 @@ hjm_status batch_graph(Workspace& ws, const std::vector<Group>& groups, size_t e
         key += buf;
     }
     auto it = ws.graphs.find(key);
+    if (it == ws.graphs.end() && ws.seen.insert(key).second) {
+        // First sighting of this batch: launch it directly (groups one after
+        // another on s). Capturing and instantiating a graph costs more than
+        // one launch sequence, and a batch whose make-up changes on every
+        // call (the surrogate's fallback rows, calibration loops) would pay
+        // that each time; a batch seen again is captured and replayed.
+        if (ws.seen.size() > 1024) ws.seen.clear();
+        for (const auto& g : groups) {
+            hjm_status st = group_sequence(g, elem, s);
+            if (st != HJM_OK) return st;
+        }
+        return HJM_OK;
+    }
     if (it == ws.graphs.end()) {
         if (ws.graphs.size() > 64) ws.drop_graphs();
         while (g_events.size() < groups.size() + 1) {
