@@ -243,6 +243,51 @@ def test_full_size_config2_bench_batch(H, orc, torch_mod):
     assert np.all(p64 > 0.0)
 
 
+def test_full_size_config4_first_step_and_march(H, orc, torch_mod):
+    # The 512 x 256 x 256 caplet of the benchmark, in the launch shape the
+    # autotuner picks for it (32,16,8,8,8): the whole field after the first
+    # step against the oracle element by element (FP32 and FP64), then the
+    # full 1000-step FP32 price against the FP64 GPU march (the oracle cannot
+    # run 3.4e10 point-steps; the FP64 path is pinned to it above).
+    torch = torch_mod
+    it = W.config4()
+    g = it["grid"]
+    H.hjm_tile_set(g["n_r"], g["n_v"], g["n_y"], "fp32", (32, 16, 8, 8, 8, 0, 0))
+    try:
+        with orc.Ctx(it) as X:
+            want = X.step(0, X.terminal())
+        scale = np.max(np.abs(want))
+        with H.Grid(it) as gr:
+            for prec, tol in (("fp32", field32_tol(1)), ("fp64", 1e-10)):
+                out = torch.empty(gr.shape, dtype=_ptype(torch, prec), device="cuda")
+                gr.field(prec, 1, out)
+                got = out.double().cpu().numpy()
+                assert np.max(np.abs(got - want)) <= tol * scale, prec
+                del out
+            p32, p64 = gr.price("fp32"), gr.price("fp64")
+        assert abs(p32 - p64) <= max(1e-4 * abs(p64), 1e-6), (p32, p64)
+    finally:
+        H.hjm_tile_set(g["n_r"], g["n_v"], g["n_y"], "fp32", None)
+
+
+def test_full_size_config3_batch(H, orc):
+    # The 256 uneven caplets of the benchmark in one call after the
+    # benchmark's autotuning: FP32 against the FP64 GPU march for all, and
+    # both against the oracle on the caplets of the smallest grid (64 x 32 x
+    # 32, 128 steps).
+    items = W.config3_batch()
+    H.hjm_autotune(items, "fp32", steps=4)
+    p32 = H.hjm_price_batch(items, "fp32")
+    p64 = H.hjm_price_batch(items, "fp64")
+    assert np.all(np.abs(p32 - p64) <= np.maximum(1e-4 * np.abs(p64), 1e-6))
+    small = [i for i, x in enumerate(items) if x["grid"]["n_r"] == 64][:3]
+    want = _oracle_prices_parallel(orc, [items[i] for i in small], workers=3)
+    assert np.all(np.abs(p64[small] - want) <= 1e-10 * np.abs(want)), (p64[small], want)
+    assert np.all(np.abs(p32[small] - want) <= np.maximum(1e-4 * np.abs(want), 1e-6))
+    for x in items:
+        H.hjm_tile_set(x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], "fp32", None)
+
+
 def test_size_limits(H):
     it = _caplet_case(512, 5, 5, 2)
     with H.Grid(it) as g:
