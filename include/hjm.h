@@ -59,7 +59,10 @@ typedef enum { HJM_FP64 = 0, HJM_FP32 = 1, HJM_MIXED = 2 } hjm_precision;
  * (0, 0) and the knots (f = -(ln P)', df/dt = -(ln P)'' continuous; the
  * spline is built on the device by the set-up); past the last knot ln P
  * continues linearly (flat forward). The knot fields are ignored for the
- * other kinds. */
+ * other kinds. Calls taking a curve return HJM_EINVAL for an unknown kind,
+ * tau <= 0 (Nelson-Siegel), n_knots outside [1, HJM_MAX_KNOTS], maturities
+ * not positive and increasing, a discount factor not finite and positive, or
+ * f(0,0) outside [r_min, r_max]. */
 typedef enum { HJM_CURVE_FLAT = 0, HJM_CURVE_NELSON_SIEGEL = 1, HJM_CURVE_KNOTS = 2 } hjm_curve_kind;
 #define HJM_MAX_KNOTS 32
 typedef struct {
@@ -98,7 +101,9 @@ typedef struct {
  *                  solves once more) that makes the step second order in time
  *                  with the mixed term; they take every explicit operator at
  *                  t^{n+1/2}, whatever explicit_midpoint says. Usual theta:
- *                  CS 1/2, MCS 1/3, HV 1/2 + sqrt(3)/6.
+ *                  CS 1/2, MCS 1/3, HV 1/2 + sqrt(3)/6. Another value:
+ *                  HJM_EINVAL. A scheme of the family needs a third field
+ *                  of the grid's size on the device.
  * Boundary rule: r = r_max, and r = r_min when gamma == 0, carry Dirichlet
  * data (exact bond; caplet max(P(t,T) - Delta_M P(t,T_M), 0)); the v and y
  * faces (and r = 0 when gamma > 0) drop the normal second derivative and the
