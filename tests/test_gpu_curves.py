@@ -47,6 +47,7 @@ CASES = {
     "caplet_5y_past_the_last_knot_3y": lambda: _item(5, W.caplet(5.0, 6.0), 33, 9, 9, 8,
                                                      times=(0.25, 0.5, 1.0, 2.0, 3.0)),
     "caplet_5y_hv": lambda: _item(6, W.caplet(5.0, 5.5), 37, 11, 13, 12, scheme=3, theta_adi=0.5 + 3 ** 0.5 / 6),
+    "bond_one_knot": lambda: _item(9, W.bond(5.0), 24, 8, 8, 10, times=(7.0,)),
 }
 
 

@@ -128,6 +128,17 @@ def test_knot_curve_of_a_flat_curve_is_flat(orc):
         assert orc.curve_P(c, t) == pytest.approx(math.exp(-r * t), rel=1e-12)
 
 
+def test_knot_curve_with_one_knot_is_flat(orc):
+    # One knot: the natural spline through (0, 0) and (t1, ln P1) is the
+    # straight line, a flat forward -ln(P1)/t1 everywhere.
+    c = W.knot_curve([4.0], [0.88])
+    r = -math.log(0.88) / 4.0
+    for t in (0.0, 1.0, 4.0, 9.0):
+        assert orc.curve_f(c, t) == pytest.approx(r, abs=1e-15)
+        assert orc.curve_dfdt(c, t) == 0.0
+        assert orc.curve_P(c, t) == pytest.approx(math.exp(-r * t), rel=1e-14)
+
+
 def test_knot_curve_is_the_natural_cubic_spline_of_ln_p(orc):
     # The reading of Section 6.1's smoothing: the textbook natural cubic
     # spline of ln P through (0, 0) and the knots (scipy's CubicSpline with
