@@ -1,6 +1,7 @@
 // C ABI of libhjm (declared in include/hjm.h): argument validation, grouping
-// of batch items by grid shape, device workspaces, CUDA-graph capture of the
-// time march, read-out and error reporting.
+// of batch items by grid shape and scheme, device workspaces, the step
+// sequence of each scheme (Douglas; the Craig-Sneyd family's two stages),
+// CUDA-graph capture of the time march, read-out and error reporting.
 //
 // Host code here validates and marshals only; every arithmetic step of the
 // method (set-up tables, terminal field, the march, the read-out) runs in the

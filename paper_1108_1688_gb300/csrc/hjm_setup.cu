@@ -1,7 +1,8 @@
-// FP64 set-up and read-out kernels of the Douglas ADI march.
+// FP64 set-up and read-out kernels of the ADI march.
 //
 // Everything here runs once per price (not per step): the curve and bond
-// functions of Sections 2 and 3.1, the sinh metric of Sections 4.3 / 7.1, the
+// functions of Sections 2 and 3.1 (with the spline of a discrete curve,
+// Section 6.1, built by k_setup), the sinh metric of Sections 4.3 / 7.1, the
 // coefficient tables of the operator of Eq. (1) in the metric form of Section
 // 4.3, the per-step scalars and Dirichlet data, the Thomas factors of the
 // line-invariant v and y systems, the softened terminal field of Section 7.2
