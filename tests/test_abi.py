@@ -46,6 +46,7 @@ def test_status_strings(H):
     ("grid", "n_r", 4, 1), ("grid", "n_r", 600, 7), ("grid", "n_v", 4000, 7),
     ("grid", "y_boundary_order", 0, 1), ("model", "rho", -1.5, 1), ("model", "gamma", 2.0, 1),
     ("inst", "T", -1.0, 1), ("curve", "kind", 7, 1), ("grid", "theta_adi", float("inf"), 1),
+    ("grid", "scheme", 4, 1), ("grid", "scheme", -1, 1),
 ])
 def test_batch_validation_rejects_bad_items(H, part, key, val, status):
     items = W.config2_draws(3, n_r=16, n_y=8, n_v=8, n_steps=4)
@@ -54,6 +55,22 @@ def test_batch_validation_rejects_bad_items(H, part, key, val, status):
         H.hjm_price_batch(items, H.HJM_FP32)
     assert ei.value.status == status
     assert "item 1" in str(ei.value)
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda c: c.update(n_knots=0), lambda c: c.update(n_knots=33),
+    lambda c: c["knot_t"].__setitem__(2, c["knot_t"][1]), lambda c: c["knot_P"].__setitem__(0, -0.1),
+    lambda c: c["knot_t"].__setitem__(0, 0.0), lambda c: c["knot_P"].__setitem__(4, float("nan")),
+])
+def test_batch_validation_rejects_bad_knots(H, mutate):
+    # the host-side checks of a discrete curve (no device is touched)
+    items = W.config2_draws(2, n_r=16, n_y=8, n_v=8, n_steps=4)
+    c = W.synthetic_knot_curve(3)
+    mutate(c)
+    items[1]["curve"] = c
+    with pytest.raises(H.HJMError) as ei:
+        H.hjm_price_batch(items, H.HJM_FP32)
+    assert ei.value.status == H.HJM_EINVAL and "item 1" in str(ei.value)
 
 
 def test_gamma_positive_needs_rmin_zero(H):
