@@ -90,3 +90,22 @@ def test_single_price_mixed(H):
 def torch_dev():
     import torch
     return torch
+
+
+def test_non_finite_price_is_reported(H, orc):
+    # A valid but absurd input (lambda = 30: the domain reaches |r| ~ 1000
+    # and the Dirichlet bond prices overflow) gives a non-finite price, as in
+    # the oracle; every precision reports HJM_ENUMERIC for that item instead
+    # of returning it (MIXED after its FP64 re-run). No device fault: IEEE
+    # infinities and NaNs only.
+    c = W.flat_curve(0.03)
+    m = W.model(0.1, 30.0, 0.0, 1.0, 0.3, -0.3)
+    bad = W.item(c, m, W.default_grid(c, m, 5.0, 16, 8, 8, 4), W.bond(5.0))
+    assert not np.isfinite(orc.price(bad))
+    items = [W.config1(), bad]
+    for prec in ("fp32", "fp64", "mixed"):
+        with pytest.raises(H.HJMError) as ei:
+            H.hjm_price_batch(items, prec)
+        assert ei.value.status == H.HJM_ENUMERIC and "item 1" in str(ei.value), prec
+    # the library stays usable
+    assert abs(H.hjm_price_batch([W.config1()], "fp64")[0] - orc.price(W.config1())) < 1e-12
