@@ -335,84 +335,96 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const T yB = yin ? T(1) : (yord == 1 ? T(0) : (j == 0 ? T(-1) : T(1)));
     const T dt = I.dt, w = I.w;
 
-    // Neighbours across lanes by shuffles: U at the chunk's ends and, for the
-    // mixed term, wd = U_{v,b} - U_{v,a}.
-    const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
-    const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
-    T wl = ub[M - 1] - ua[M - 1], wf = ub[0] - ua[0];
-    if constexpr (ST2) {
-        if (!I.hv) {
-            wl += xx[M - 1];
-            wf += xx[0];
-        }
-    }
-    const T wd_prev = __shfl_up_sync(0xffffffffu, wl, 1, S);
-    const T wd_next = __shfl_down_sync(0xffffffffu, wf, 1, S);
-
 #define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
-    // 1. right-hand side, every node as if interior in r. Nodes are taken
-    // in pairs (m, m+1) so the FP32 march runs on the paired FP32 pipe (two
-    // lanes of arithmetic per instruction); sh[h] = (U_{2h-1}, U_{2h}) and
-    // tw[h] = (wd_{2h-1}, wd_{2h}) are the pairs shifted by one node.
+    // 1. right-hand side, every node as if interior in r, in two sweeps over
+    // node pairs (m, m+1) (so the FP32 march runs on the paired FP32 pipe,
+    // two lanes of arithmetic per instruction): (a) the v and y parts and the
+    // mixed-term row differences wd = U_{v,b} - U_{v,a}, after which the four
+    // neighbour rows are dead; (b) the r part, the reaction and the mixed
+    // term from U and wd. Splitting the sweep keeps the registers of the
+    // rows, the tables and the pair constants from being live together.
     using PV = typename Two<T>::V;
     constexpr int H = M / 2;
-    // rolling shifted pairs (current and next), built just in time
     // ST2: weights of xx in the mixed-term difference and in the right-hand side
     const PV xw2 = Two<T>::splat(ST2 && !I.hv ? T(1) : T(0)), xr2 = Two<T>::splat(ST2 && I.hv ? T(1) : T(0));
-    PV shc = Two<T>::mk(uc_prev, uc[0]);
-    PV wdc = Two<T>::sub(Two<T>::mk(ub[0], ub[1]), Two<T>::mk(ua[0], ua[1]));
-    if constexpr (ST2) wdc = Two<T>::fma(xw2, Two<T>::mk(xx[0], xx[1]), wdc);
-    PV twc = Two<T>::mk(wd_prev, Two<T>::x(wdc));
-    const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v), aFy2 = Two<T>::splat(aFy);
-    const PV vq2 = Two<T>::splat(vq), cA2 = Two<T>::splat(cA), cB2 = Two<T>::splat(cB);
-    const PV vy2 = Two<T>::splat(vy), kyy2 = Two<T>::splat(kyy), yA2 = Two<T>::splat(yA), yB2 = Two<T>::splat(yB);
-    const PV dt2 = Two<T>::splat(dt);
+    T wd[M];
+    {
+        const PV cA2 = Two<T>::splat(cA), cB2 = Two<T>::splat(cB);
+        const PV vy2 = Two<T>::splat(vy), kyy2 = Two<T>::splat(kyy), yA2 = Two<T>::splat(yA), yB2 = Two<T>::splat(yB);
 #pragma unroll
-    for (int m0 = 0; m0 < M; m0 += W) {
-        T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W], tC3[W], tCY[W];
-        TABV(RT_R, m0, tR);
-        TABV(RT_IJ, m0, tIJ);
-        TABV(RT_C1, m0, tC1);
-        TABV(RT_C4V, m0, tC4V);
-        TABV(RT_C4B, m0, tC4B);
-        TABV(RT_C3, m0, tC3);
-        TABV(RT_CY, m0, tCY);
+        for (int m0 = 0; m0 < M; m0 += W) {
+            T tCY[W];
+            TABV(RT_CY, m0, tCY);
 #pragma unroll
-        for (int q = 0; q < W; q += 2) {
-            const int m = m0 + q, h = m / 2;
-            PV shn, twn, wdn = wdc;
-            if (h + 1 < H) {
-                shn = Two<T>::mk(uc[m + 1], uc[m + 2]);
-                wdn = Two<T>::sub(Two<T>::mk(ub[m + 2], ub[m + 3]), Two<T>::mk(ua[m + 2], ua[m + 3]));
-                if constexpr (ST2) wdn = Two<T>::fma(xw2, Two<T>::mk(xx[m + 2], xx[m + 3]), wdn);
-                twn = Two<T>::mk(Two<T>::y(wdc), Two<T>::x(wdn));
-            } else {
-                shn = Two<T>::mk(uc[M - 1], uc_next);
-                twn = Two<T>::mk(Two<T>::y(wdc), wd_next);
+            for (int q = 0; q < W; q += 2) {
+                const int m = m0 + q;
+                const PV u = Two<T>::mk(uc[m], uc[m + 1]);
+                const PV va = Two<T>::mk(ua[m], ua[m + 1]), vb = Two<T>::mk(ub[m], ub[m + 1]);
+                const PV g6 = Two<T>::fma(Two<T>::mk(tCY[q], tCY[q + 1]), vy2, kyy2);
+                const PV yy = Two<T>::fma(yA2, Two<T>::sub(Two<T>::mk(ya[m], ya[m + 1]), u),
+                                          Two<T>::mul(yB2, Two<T>::sub(Two<T>::mk(yb[m], yb[m + 1]), u)));
+                PV f = Two<T>::mul(g6, yy);
+                f = Two<T>::fma(cA2, Two<T>::sub(va, u), f);
+                f = Two<T>::fma(cB2, Two<T>::sub(vb, u), f);
+                d[m] = Two<T>::x(f);
+                d[m + 1] = Two<T>::y(f);
+                PV wv = Two<T>::sub(vb, va);
+                if constexpr (ST2) wv = Two<T>::fma(xw2, Two<T>::mk(xx[m], xx[m + 1]), wv);
+                wd[m] = Two<T>::x(wv);
+                wd[m + 1] = Two<T>::y(wv);
             }
-            const PV u = Two<T>::mk(uc[m], uc[m + 1]);
-            const PV Dp = Two<T>::sub(shn, u);  // U_{m+1} - U_m
-            const PV Dm = Two<T>::sub(u, shc);  // U_m - U_{m-1}
-            const PV g1 = Two<T>::mul(Two<T>::mk(tC1[q], tC1[q + 1]), v2);  // zeta_rr / (J^2 h^2)
-            const PV g4F = Two<T>::fma(aFy2, Two<T>::mk(tIJ[q], tIJ[q + 1]),
-                                       Two<T>::fma(nv2, Two<T>::mk(tC4V[q], tC4V[q + 1]),
-                                                   Two<T>::mk(tC4B[q], tC4B[q + 1])));  // g4 / (2h) at t^n
-            PV f = Two<T>::fma(g1, Two<T>::sub(Dp, Dm), Two<T>::mul(g4F, Two<T>::add(Dp, Dm)));
-            f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
-            f = Two<T>::fma(Two<T>::mul(Two<T>::mk(tC3[q], tC3[q + 1]), vq2), Two<T>::sub(twn, twc), f);
-            f = Two<T>::fma(cA2, Two<T>::sub(Two<T>::mk(ua[m], ua[m + 1]), u), f);
-            f = Two<T>::fma(cB2, Two<T>::sub(Two<T>::mk(ub[m], ub[m + 1]), u), f);
-            const PV g6 = Two<T>::fma(Two<T>::mk(tCY[q], tCY[q + 1]), vy2, kyy2);
-            const PV yy = Two<T>::fma(yA2, Two<T>::sub(Two<T>::mk(ya[m], ya[m + 1]), u),
-                                      Two<T>::mul(yB2, Two<T>::sub(Two<T>::mk(yb[m], yb[m + 1]), u)));
-            f = Two<T>::fma(g6, yy, f);
-            PV r = Two<T>::mul(dt2, f);
-            if constexpr (ST2) r = Two<T>::fma(xr2, Two<T>::mk(xx[m], xx[m + 1]), r);
-            d[m] = Two<T>::x(r);
-            d[m + 1] = Two<T>::y(r);
-            shc = shn;
-            twc = twn;
-            wdc = wdn;
+        }
+    }
+    const T f1_0 = d[0];  // v and y parts at the lane's first node (r = 0 face)
+    // Neighbours across lanes by shuffles: U and wd at the chunk's ends.
+    const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
+    const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
+    const T wd_prev = __shfl_up_sync(0xffffffffu, wd[M - 1], 1, S);
+    const T wd_next = __shfl_down_sync(0xffffffffu, wd[0], 1, S);
+    {
+        // shifted pairs sh = (U_{m-1}, U_m), tw = (wd_{m-1}, wd_m), rolled
+        PV shc = Two<T>::mk(uc_prev, uc[0]);
+        PV twc = Two<T>::mk(wd_prev, wd[0]);
+        const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v), aFy2 = Two<T>::splat(aFy);
+        const PV vq2 = Two<T>::splat(vq), dt2 = Two<T>::splat(dt);
+#pragma unroll
+        for (int m0 = 0; m0 < M; m0 += W) {
+            T tR[W], tIJ[W], tC1[W], tC4V[W], tC4B[W], tC3[W];
+            TABV(RT_R, m0, tR);
+            TABV(RT_IJ, m0, tIJ);
+            TABV(RT_C1, m0, tC1);
+            TABV(RT_C4V, m0, tC4V);
+            TABV(RT_C4B, m0, tC4B);
+            TABV(RT_C3, m0, tC3);
+#pragma unroll
+            for (int q = 0; q < W; q += 2) {
+                const int m = m0 + q, h = m / 2;
+                PV shn, twn;
+                if (h + 1 < H) {
+                    shn = Two<T>::mk(uc[m + 1], uc[m + 2]);
+                    twn = Two<T>::mk(wd[m + 1], wd[m + 2]);
+                } else {
+                    shn = Two<T>::mk(uc[M - 1], uc_next);
+                    twn = Two<T>::mk(wd[M - 1], wd_next);
+                }
+                const PV u = Two<T>::mk(uc[m], uc[m + 1]);
+                const PV Dp = Two<T>::sub(shn, u);  // U_{m+1} - U_m
+                const PV Dm = Two<T>::sub(u, shc);  // U_m - U_{m-1}
+                const PV g1 = Two<T>::mul(Two<T>::mk(tC1[q], tC1[q + 1]), v2);  // zeta_rr / (J^2 h^2)
+                const PV g4F = Two<T>::fma(aFy2, Two<T>::mk(tIJ[q], tIJ[q + 1]),
+                                           Two<T>::fma(nv2, Two<T>::mk(tC4V[q], tC4V[q + 1]),
+                                                       Two<T>::mk(tC4B[q], tC4B[q + 1])));  // g4 / (2h) at t^n
+                PV f = Two<T>::fma(g1, Two<T>::sub(Dp, Dm), Two<T>::mul(g4F, Two<T>::add(Dp, Dm)));
+                f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
+                f = Two<T>::fma(Two<T>::mul(Two<T>::mk(tC3[q], tC3[q + 1]), vq2), Two<T>::sub(twn, twc), f);
+                f = Two<T>::add(f, Two<T>::mk(d[m], d[m + 1]));
+                PV r = Two<T>::mul(dt2, f);
+                if constexpr (ST2) r = Two<T>::fma(xr2, Two<T>::mk(xx[m], xx[m + 1]), r);
+                d[m] = Two<T>::x(r);
+                d[m + 1] = Two<T>::y(r);
+                shc = shn;
+                twc = twn;
+            }
         }
     }
     const T gLo = I.dir[j], gHi = I.dir[ny + j];
@@ -425,9 +437,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             const T u = uc[0], u1 = uc[1], u2 = M >= 3 ? uc[M >= 3 ? 2 : 1] : uc_next;
             const T fr = aFy * tl[RT_IJ * S * MP] + tl[RT_C4B * S * MP];  // mu_r / (2 h J) at t^n
             T f = fr * (T(-3) * u + T(4) * u1 - u2) - tl[RT_R * S * MP] * u;
-            f += cA * (ua[0] - u) + cB * (ub[0] - u);
-            const T g6 = tl[RT_CY * S * MP] * vy + kyy;
-            f += g6 * (yA * (ya[0] - u) + yB * (yb[0] - u));
+            f += f1_0;  // v and y parts
             d[0] = dt * f;
             if constexpr (ST2) {
                 if (I.hv) d[0] += xx[0];
@@ -446,6 +456,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     T a[M], bb[M], c[M];
     {
         const PV aIy2 = Two<T>::splat(aIy), nw2 = Two<T>::splat(-w), w2 = Two<T>::splat(w);
+        const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v);
         const PV one2 = Two<T>::splat(T(1)), two2 = Two<T>::splat(T(2));
 #pragma unroll
         for (int m0 = 0; m0 < M; m0 += W) {
