@@ -228,9 +228,9 @@ def recorded_traffic(kernel, workload, points_per_launch, tile=None):
     if d.get("source_digest") != source_digest():
         return None
     w = d.get("workloads", {}).get(workload)
-    if not w or (tile is not None and w.get("tile") != tile):
+    if not w or tile is None:
         return None
-    rec = w.get("kernels", {}).get(kernel)
+    rec = w.get("tiles", {}).get(tile, {}).get("kernels", {}).get(kernel)
     if not rec:
         return None
     return rec["dram_bytes_per_point"] * points_per_launch

@@ -281,10 +281,13 @@ hjm_status hjm_tile_get(int n_r, int n_v, int n_y, hjm_precision precision, hjm_
  * n_r. */
 hjm_status hjm_tile_set(int n_r, int n_v, int n_y, hjm_precision precision, const hjm_tile* tile);
 /* Autotuner: for every grid shape among the items, march the items of that
- * shape for `steps` Douglas steps (1..1000) with each candidate launch shape
- * (timed with CUDA events on cuda_stream, best of two), and keep the fastest
- * for later calls. Prices are not computed; synchronous; the items are
- * validated as in hjm_price_batch. */
+ * shape for `steps` steps (1..1000) with each candidate launch shape (timed
+ * with CUDA events on cuda_stream, best of two), and keep the fastest for
+ * later calls. For items of the Craig-Sneyd family the pass-1 time includes
+ * the correction stage's pass 1, which never uses the staged row feed. One
+ * shape is kept per grid shape and precision, whatever the scheme: tune
+ * with the items (and scheme) that will be priced. Prices are not computed;
+ * synchronous; the items are validated as in hjm_price_batch. */
 hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_precision precision, int steps,
                         void* cuda_stream);
 

@@ -966,11 +966,19 @@ static hjm_status time_passes(Group& g, int ns, cudaStream_t s, cudaEvent_t* ev,
     const March<T> P = march_args<T>(g.t);
     T* U = (T*)g.U;
     T* A = (T*)g.A;
+    // A Craig-Sneyd-family group also runs the correction-stage pass 1 (from
+    // U^n and Y3; Y3 = U^n here, the values do not change the timing), so
+    // its pass-1 time is that of both kinds of launch.
+    T* Y = g.scheme != HJM_SCHEME_DOUGLAS ? (T*)g.Y : nullptr;
+    if (Y)
+        CU_TRY(cudaMemcpyAsync(Y, U, (size_t)g.t.B * g.nr * g.nv * g.ny * sizeof(T), cudaMemcpyDeviceToDevice,
+                               s));
     ms[0] = ms[1] = ms[2] = 0.f;
     for (int n = -1; n < ns; ++n) {  // n = -1: untimed warm-up step
         const int sn = n < 0 ? 0 : n;
         CU_TRY(cudaEventRecord(ev[0], s));
         CU_TRY(launch_pass1<T>(P, U, nullptr, A, sn, g.tile, s));
+        if (Y) CU_TRY(launch_pass1<T>(P, U, Y, A, sn, g.tile, s));
         CU_TRY(cudaEventRecord(ev[1], s));
         if (g.tile.p2_P == 0 && !g.gpos) {
             CU_TRY(cudaEventRecord(ev[2], s));
