@@ -213,3 +213,18 @@ def test_unknown_scheme_rejected(H):
     with pytest.raises(H.HJMError) as ei:
         H.hjm_price_batch([it], "fp32")
     assert ei.value.status == H.HJM_EINVAL
+
+
+def test_mixed_precision_with_the_schemes(H, orc):
+    # MIXED on Craig-Sneyd-family items: FP32 marches, the rounding bound of
+    # each (both stages feed the indicator), FP64 re-runs where it misses:
+    # every price within the tolerance of the oracle and every reported
+    # bound within it; an escalated item carries the FP64 price.
+    items = [_caplet(37, 11, 13, 10, s, seed=30 + s) for s in SCHEMES]
+    want = np.array([orc.price(x) for x in items])
+    p, infos = H.hjm_price_batch(items, "mixed", tol_rel=1e-4, infos=True)
+    assert np.all(np.abs(p - want) <= np.maximum(1e-4 * np.abs(want), 1e-6))
+    for i, inf in enumerate(infos):
+        assert inf.err_estimate <= max(1e-4 * abs(p[i]), 1e-6)
+        if inf.escalated:
+            assert abs(p[i] - want[i]) <= 1e-10 * max(abs(want[i]), 1e-3)
