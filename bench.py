@@ -202,13 +202,15 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_name(kind, tile):
+def kernel_name(kind, tile, prec="fp32", scheme=0):
     """The kernel that runs a pass under a launch shape (7-tuple as from
     hjm_tile_get), for the roofline line."""
     if tile is None:
         return "k_" + kind
     if kind == "pass1":
-        return "k_pass1s" if tile[5] == 1 else "k_pass1"
+        if tile[5] == 1:
+            return "k_pass1s"
+        return "k_pass1_r96" if prec == "fp32" and tile[1] == 8 and not scheme else "k_pass1"
     if kind == "pass3" and tile[3] == 0:
         return "k_pass23"
     if kind in ("pass2", "pass3"):
@@ -497,7 +499,7 @@ def run_ours(args):
         alg = (WORDS_PER_POINT_CS if scheme else WORDS_PER_POINT)[dom] * elem * pts_launch
         peak, peak_kind = measured_peaks()
         achieved = alg / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": kernel_name(dom, tile_used), "achieved": achieved, "peak": peak,
+        roof = {"bound": "hbm", "kernel": kernel_name(dom, tile_used, prec, scheme), "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                 "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
                 "traffic": recorded_traffic(dom, "%s-%s%s" % (args.workload, prec, "-" + args.scheme if scheme else ""),
