@@ -76,3 +76,28 @@ def test_reference_arm_prints_one_line():
 def test_source_digest_is_stable():
     assert bench.source_digest() == bench.source_digest()
     assert len(bench.source_digest()) == 16
+
+
+def test_kernel_names_of_launch_shapes():
+    # the roofline line names the kernel a launch shape runs
+    assert bench.kernel_name("pass1", (16, 8, 8, 1, 4, 0, 0)) == "k_pass1_r96"
+    assert bench.kernel_name("pass1", (16, 8, 8, 1, 4, 0, 0), "fp64") == "k_pass1"
+    assert bench.kernel_name("pass1", (16, 8, 8, 1, 4, 0, 0), "fp32", 3) == "k_pass1"
+    assert bench.kernel_name("pass1", (32, 16, 8, 8, 8, 0, 0)) == "k_pass1"
+    assert bench.kernel_name("pass1", (8, 16, 1, 1, 4, 1, 16)) == "k_pass1s"
+    assert bench.kernel_name("pass2", (16, 8, 8, 1, 4, 0, 0)) == "k_pass2"
+    assert bench.kernel_name("pass3", (16, 8, 8, 1, 4, 0, 0)) == "k_split_lines"
+    assert bench.kernel_name("pass3", (16, 8, 8, 0, 1, 0, 0)) == "k_pass23"
+
+
+def test_recorded_traffic_is_keyed_by_sources_and_launch_shape():
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    shapes = d["workloads"]["config2-fp32"]["tiles"]
+    tile = sorted(shapes)[0]
+    assert bench.recorded_traffic("pass1", "config2-fp32", 1000, "1,2,3,4,5,6,7") is None
+    assert bench.recorded_traffic("pass1", "no-such-workload", 1000, tile) is None
+    got = bench.recorded_traffic("pass1", "config2-fp32", 1000, tile)
+    if d["source_digest"] == bench.source_digest():
+        assert got == shapes[tile]["kernels"]["pass1"]["dram_bytes_per_point"] * 1000
+    else:  # counters taken on other kernel sources are not reported
+        assert got is None
