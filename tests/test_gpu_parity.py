@@ -319,3 +319,38 @@ def test_greeks_match_oracle(H, orc, name, prec):
     rel = 1e-9 if prec == "fp64" else 2e-4
     assert abs(got_r - want_r) <= rel * sr, (got_r, want_r, sr)
     assert abs(got_v - want_v) <= rel * sv, (got_v, want_v, sv)
+
+
+def test_concurrent_callers_on_their_own_streams(H, torch_mod):
+    # Two host threads price different batches on their own CUDA streams at
+    # the same time (the library serialises its host state, each stream has
+    # its own workspace); every result equals the single-threaded one.
+    import threading
+    torch = torch_mod
+    batches = [W.config2_draws(6, seed=41, n_r=48, n_y=12, n_v=10, n_steps=20),
+               W.config2_draws(5, seed=42, n_r=33, n_y=9, n_v=11, n_steps=15) + [W.config1()]]
+    want = [H.hjm_price_batch(b, "fp32") for b in batches]
+    got = [[None] * 3 for _ in batches]
+    errors = []
+
+    def worker(q):
+        try:
+            s = torch.cuda.Stream()
+            out = torch.empty(len(batches[q]), dtype=torch.float64, device="cuda")
+            for r in range(3):
+                with torch.cuda.stream(s):
+                    H.hjm_price_batch(batches[q], "fp32", out=out, stream=s)
+                s.synchronize()
+                got[q][r] = out.cpu().numpy().copy()
+        except Exception as e:  # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(q,)) for q in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join(timeout=300)
+    assert not errors, errors
+    for q in range(2):
+        for r in range(3):
+            assert np.array_equal(got[q][r], want[q]), (q, r)
