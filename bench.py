@@ -209,7 +209,7 @@ def kernel_name(kind, tile, prec="fp32", scheme=0):
         return "k_" + kind
     if kind == "pass1":
         if tile[5] == 1:
-            return "k_pass1s"
+            return "k_pass1s_r96" if prec == "fp32" and tile[1] <= 8 else "k_pass1s"
         return "k_pass1_r96" if prec == "fp32" and tile[1] == 8 and not scheme else "k_pass1"
     if kind == "pass3" and tile[3] == 0:
         return "k_pass23"

@@ -691,9 +691,11 @@ __host__ __device__ inline int p1s_row_stride(int nr, int SM, int V)
     return ((ch + 7) & ~7) * V;
 }
 
+// Body of k_pass1s and k_pass1s_r96 (which differ only in their register
+// budget).
 template <typename T, int S, int M>
-__global__ void __launch_bounds__(128, 4) k_pass1s(const March<T> P, const T* __restrict__ U,
-                                                T* __restrict__ out, const int n, const int RK, const int JC)
+__device__ __forceinline__ void pass1_staged(const March<T>& P, const T* __restrict__ U, T* __restrict__ out,
+                                             const int n, const int RK, const int JC)
 {
     constexpr int G = 32 / S;
     constexpr int MP = P1Layout<T, M>::MP;
@@ -772,6 +774,23 @@ __global__ void __launch_bounds__(128, 4) k_pass1s(const March<T> P, const T* __
     cp_async_wait16<0>();
 }
 
+template <typename T, int S, int M>
+__global__ void __launch_bounds__(128, 4) k_pass1s(const March<T> P, const T* __restrict__ U,
+                                                T* __restrict__ out, const int n, const int RK, const int JC)
+{
+    pass1_staged<T, S, M>(P, U, out, n, RK, JC);
+}
+
+// The FP32 staged shapes with at most 8 nodes per lane, held to 96 registers
+// (5 CTAs per SM) like k_pass1_r96; they fit without spills.
+template <typename T, int S, int M>
+__global__ void __launch_bounds__(128, 5) k_pass1s_r96(const March<T> P, const T* __restrict__ U,
+                                                     T* __restrict__ out, const int n, const int RK,
+                                                     const int JC)
+{
+    pass1_staged<T, S, M>(P, U, out, n, RK, JC);
+}
+
 // Pass-1 shapes compiled for each element type: (S, M) with S lanes per r
 // line and M nodes per lane.
 static bool p1_compiled(size_t elem, int S, int M)
@@ -842,8 +861,11 @@ static cudaError_t p1_launch(const March<T>& P, const T* U, const T* Y, T* out, 
         const int KB = 4 * (32 / S) * t.p1_R;
         const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
         const size_t smem = p1s_smem(P.nr, S, M, t.p1_R, sizeof(T));
-        k_pass1s<T, S, M><<<(unsigned)((long long)P.B * strips * runs), 128, smem, s>>>(P, U, out, n, t.p1_R,
-                                                                                       t.p1_J);
+        const unsigned grid = (unsigned)((long long)P.B * strips * runs);
+        if constexpr (sizeof(T) == 4 && M <= 8)
+            k_pass1s_r96<T, S, M><<<grid, 128, smem, s>>>(P, U, out, n, t.p1_R, t.p1_J);
+        else
+            k_pass1s<T, S, M><<<grid, 128, smem, s>>>(P, U, out, n, t.p1_R, t.p1_J);
         return cudaGetLastError();
     }
     const int lpc = 4 * (32 / S) * t.p1_R;
@@ -862,6 +884,18 @@ static cudaError_t p1_launch(const March<T>& P, const T* U, const T* Y, T* out, 
 #define P1_SHAPES_F64(X) X(double, 16, 2) X(double, 16, 4) X(double, 16, 8) X(double, 32, 2) X(double, 32, 4) \
     X(double, 32, 8) X(double, 32, 16)
 
+// The shared-memory limit of the register-capped staged kernel of a shape
+// (only the FP32 shapes with at most 8 nodes per lane have one).
+template <typename T, int S, int M>
+static cudaError_t p1s_r96_attr()
+{
+    if constexpr (sizeof(T) == 4 && M <= 8)
+        return cudaFuncSetAttribute(k_pass1s_r96<T, S, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kP1SmemLimit);
+    else
+        return cudaSuccess;
+}
+
 // Lets the staged kernels use up to kP1SmemLimit bytes of dynamic shared
 // memory (once per device, before launches or captures).
 cudaError_t init_pass1()
@@ -871,6 +905,7 @@ cudaError_t init_pass1()
     if (e == cudaSuccess)                                                                                    \
         e = cudaFuncSetAttribute(k_pass1s<T_, S_, M_>, cudaFuncAttributeMaxDynamicSharedMemorySize,          \
                                  (int)kP1SmemLimit);                                                         \
+    if (e == cudaSuccess) e = p1s_r96_attr<T_, S_, M_>();                                                   \
                                                          \
 
     P1_SHAPES_F32(P1_ATTR)

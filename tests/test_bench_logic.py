@@ -85,6 +85,7 @@ def test_kernel_names_of_launch_shapes():
     assert bench.kernel_name("pass1", (16, 8, 8, 1, 4, 0, 0), "fp32", 3) == "k_pass1"
     assert bench.kernel_name("pass1", (32, 16, 8, 8, 8, 0, 0)) == "k_pass1"
     assert bench.kernel_name("pass1", (8, 16, 1, 1, 4, 1, 16)) == "k_pass1s"
+    assert bench.kernel_name("pass1", (16, 8, 1, 1, 4, 1, 16)) == "k_pass1s_r96"
     assert bench.kernel_name("pass2", (16, 8, 8, 1, 4, 0, 0)) == "k_pass2"
     assert bench.kernel_name("pass3", (16, 8, 8, 1, 4, 0, 0)) == "k_split_lines"
     assert bench.kernel_name("pass3", (16, 8, 8, 0, 1, 0, 0)) == "k_pass23"
