@@ -62,7 +62,17 @@ CASES = {
     "bond_gamma09_nr13": lambda: _bond_gamma(13, 7, 9, 20),
     "bond_gamma09_nr64": lambda: _bond_gamma(64, 10, 12, 15),
     "caplet_uniform_5x5x5": lambda: _caplet_case(5, 5, 5, 7, seed=5, alpha_r=0.0, alpha_v=0.0, alpha_y=0.0),
+    "caplet_kappa0_rho_minus1": lambda: _degenerate(dict(kappa=0.0, rho=-1.0), W.caplet(3.0, 3.5)),
+    "bond_eps0_theta0": lambda: _degenerate(dict(epsilon=0.0, theta=0.0), W.bond(4.0)),
 }
+
+
+def _degenerate(model_kw, inst):
+    # the model's limiting cases: kappa = 0 (G(s) = s), perfect correlation,
+    # a variance that neither diffuses nor reverts (A_v = 0)
+    c = W.ns_curve(0.03, -0.01, 0.015, 2.0)
+    m = W.model(**dict(W.CONFIG1_MODEL, **model_kw))
+    return W.item(c, m, W.default_grid(c, m, inst["T"], 29, 9, 11, 10), inst)
 PRECS = ["fp64", "fp32"]
 
 
@@ -286,6 +296,22 @@ def test_full_size_config3_batch(H, orc):
     assert np.all(np.abs(p32[small] - want) <= np.maximum(1e-4 * np.abs(want), 1e-6))
     for x in items:
         H.hjm_tile_set(x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], "fp32", None)
+
+
+@pytest.mark.parametrize("prec,lim", [("fp32", 908), ("fp64", 454)])
+def test_strided_line_length_limits(H, orc, prec, lim):
+    # The longest v and y lines the one-lane-per-line kernels hold in shared
+    # memory (two columns of 32 lines for pass 3), priced against the
+    # oracle; one node more is refused.
+    tol = (lambda p, w: abs(p - w) <= 1e-10 * max(abs(w), 1e-3)) if prec == "fp64" else \
+          (lambda p, w: abs(p - w) <= max(1e-4 * abs(w), 1e-6))
+    for nv, ny in ((lim, 6), (6, lim)):
+        it = _caplet_case(6, ny, nv, 3, seed=7)
+        assert tol(H.hjm_price_batch([it], prec)[0], orc.price(it)), (nv, ny)
+    for nv, ny in ((lim + 1, 6), (6, lim + 1)):
+        with pytest.raises(H.HJMError) as ei:
+            H.hjm_price_batch([_caplet_case(6, ny, nv, 3, seed=7)], prec)
+        assert ei.value.status == H.HJM_ERANGE
 
 
 def test_size_limits(H):
