@@ -102,3 +102,16 @@ def test_recorded_traffic_is_keyed_by_sources_and_launch_shape():
         assert got == shapes[tile]["kernels"]["pass1"]["dram_bytes_per_point"] * 1000
     else:  # counters taken on other kernel sources are not reported
         assert got is None
+
+
+def test_pass1_fp64_operation_count():
+    # 16 lanes of 8 nodes: 15 + 20 + 13 per point and, per lane,
+    # 8 + 54 + 25 + 9 + 10 + 4 * 14 + 6 + 24 = 192 for the solve, 24 a point
+    assert bench.pass1_flops_per_point(16, 8) == 72
+    # two-node chunks: no backward elimination, no first-row reduction
+    assert bench.pass1_flops_per_point(1, 2) == 48 + (8 + 10 + 6) / 2
+    # more lanes per line add parallel-cyclic-reduction levels, longer
+    # chunks amortise them
+    assert bench.pass1_flops_per_point(32, 8) > bench.pass1_flops_per_point(16, 8)
+    assert bench.pass1_flops_per_point(16, 16) < bench.pass1_flops_per_point(16, 8)
+    assert abs(bench.FP64_PEAK_TFLOPS - 1.259) < 1e-3
