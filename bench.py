@@ -227,7 +227,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 def pass1_flops_per_point(S, M):
     """FP64 operations per grid point that pass 1 performs, counted from its
-    arithmetic (a fused multiply-add counts 2, a reciprocal 1; face rows,
+    arithmetic (a fused multiply-add counts 2, a division 1; face rows,
     a few per line, left out), for S lanes of M nodes per r line:
     the explicit operator's first sweep (v and y parts, mixed-term row
     difference: 15) and second sweep (r part, reaction, mixed term, scaling
