@@ -39,11 +39,16 @@
  *   R8  Boundary faces: r = r_max always, and r = r_min when gamma == 0, are
  *       Dirichlet with data g(t, r, y): the exact bond for a bond and
  *       max(P(t,T) - Delta_M P(t,T_M), 0) for a caplet. Every other face
- *       (v = 0, v = v_max, y = 0, y = y_max, r = 0 when gamma > 0) drops the
- *       normal second derivative and the mixed term and takes the normal first
- *       derivative one-sided into the domain: second order in F (first order
- *       on y faces when y_boundary_order == 1), first order in the implicit
- *       operators so that they stay tridiagonal. Dirichlet wins on edges.
+ *       (v = 0, v = v_max, y = 0, y = y_max, r = 0 when gamma > 0) drops its
+ *       own normal second derivative and takes the normal first derivative
+ *       one-sided into the domain: second order in F (first order on y faces
+ *       when y_boundary_order == 1), first order in the implicit operators so
+ *       that they stay tridiagonal. The r-v mixed term is dropped only where
+ *       its centred stencil leaves the grid, i.e. on the v faces and the
+ *       non-Dirichlet r face; the y faces keep it, because y has no diffusion
+ *       and no y-mixed term, so Eq. (1) of Section 3.2 holds unchanged in the
+ *       r-v directions on y = 0 (the plane the price is read from) and on
+ *       y = y_max. Dirichlet wins on edges.
  *   R9  Node counts include both boundaries; nodes xi_i = i/(n-1).
  *   R10 State at the readout: r = f(0,0), v = v0, y = 0; tensor-product
  *       cubic Lagrange interpolation in (xi_r, xi_v) on the y = 0 plane.

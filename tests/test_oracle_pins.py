@@ -316,9 +316,11 @@ def poly_cases():
 def test_operator_exact_on_quadratics(orc, gamma, name):
     # Section 5: centred differences are exact on polynomials of degree <= 2 on a
     # uniform grid, so each split operator must equal Eq. (1)'s terms applied
-    # analytically. Degenerate faces (reading R8): physical second derivative
-    # and mixed term dropped, second-order one-sided first derivative (exact
-    # for degree <= 2).
+    # analytically. Degenerate faces (reading R8): the face's own normal second
+    # derivative dropped, second-order one-sided first derivative (exact for
+    # degree <= 2); the r-v mixed term dropped only where its stencil leaves
+    # the grid (v faces, non-Dirichlet r face) and kept on the y faces, where
+    # Eq. (1) holds unchanged in r and v (hence r_int & v_int and no y mask).
     it = small_item(n_r=9, n_y=8, n_v=7, gamma=gamma, uniform=True)
     Uf, dU = poly_cases()[name]
     with orc.Ctx(it) as X:
@@ -796,7 +798,7 @@ def test_craig_sneyd_reductions(orc):
     assert abs(p_cs - p_do) > 1e-9  # the mixed term does make them differ
 
 
-def _time_errors(orc, curve, scheme, midpoint, steps=(8, 16, 32), ref_steps=512):
+def _time_errors(orc, curve, scheme, midpoint, steps=(16, 32, 64), ref_steps=1024):
     m = W.model(0.1, 0.02, 0.0, 1.0, 1.0, -0.9)
     th = SCHEME_THETA[scheme]
     it = lambda ns: W.item(curve, m, W.default_grid(curve, m, 2.0, 24, 16, 16, ns, theta_adi=th, scheme=scheme,
@@ -808,28 +810,32 @@ def _time_errors(orc, curve, scheme, midpoint, steps=(8, 16, 32), ref_steps=512)
 @pytest.mark.parametrize("scheme", [0, 1, 2, 3])
 def test_craig_sneyd_family_time_order(orc, scheme):
     # Strong correlation (rho = -0.9, epsilon = 1) on a fixed spatial grid,
-    # flat curve, errors against 512 steps: Douglas with the explicit mixed
-    # term is first order in time (error ratio about 2 per halving), CS,
-    # modified CS (theta = 1/3) and Hundsdorfer-Verwer (theta = 1/2 + sqrt(3)/6)
-    # are second order (ratio about 4).
-    # (measured: Douglas 2.3, 2.2; CS 4.1, 4.5; MCS 4.6, 5.1; HV 3.3, 3.6)
+    # flat curve, errors at 16, 32 and 64 steps against 1024 steps (the
+    # asymptotic range: every error is far above the reference's own):
+    # Douglas with the explicit mixed term is first order in time (error
+    # ratio about 2 per halving), CS, modified CS (theta = 1/3) and
+    # Hundsdorfer-Verwer (theta = 1/2 + sqrt(3)/6) are second order, as
+    # In 't Hout and Welfert prove for these schemes (ratio -> 4; the bound
+    # 3.4 was fixed before the ladder was run).
+    # (measured: Douglas 2.15, 2.13; CS 4.5, 5.4; MCS 5.2, 8.3; HV 3.6, 3.8)
     e = _time_errors(orc, W.flat_curve(0.03), scheme, 1)
     ratios = [e[i] / e[i + 1] for i in range(len(e) - 1)]
     if scheme == 0:
         assert all(1.6 < r < 2.8 for r in ratios), (e, ratios)
     else:
-        assert all(r > 3.0 for r in ratios), (e, ratios)
+        assert all(r >= 3.4 for r in ratios), (e, ratios)
 
 
-@pytest.mark.parametrize("scheme", [1, 3])
+@pytest.mark.parametrize("scheme", [1, 2, 3])
 def test_craig_sneyd_family_second_order_with_time_dependent_drift(orc, scheme):
     # Nelson-Siegel curve (time-dependent drift a(t) in mu_r) with the grid's
     # explicit_midpoint = 0: the CS family still takes its explicit operators
     # at t^{n+1/2} and stays second order, where Douglas with F at t^n is
-    # first order.
+    # first order. (measured: CS 4.02, 4.02; MCS 3.99, 4.01; HV 5.1, 4.8;
+    # Douglas 1.99, 2.05)
     c = W.ns_curve(0.03, -0.02, 0.02, 1.5)
     e = _time_errors(orc, c, scheme, 0)
-    assert all(e[i] / e[i + 1] > 3.0 for i in range(len(e) - 1)), e
+    assert all(e[i] / e[i + 1] >= 3.4 for i in range(len(e) - 1)), e
     d = _time_errors(orc, c, 0, 0)
     assert all(d[i] / d[i + 1] < 2.8 for i in range(len(d) - 1)), d
 
