@@ -91,10 +91,12 @@ def forward(p, x, lo, hi, bf16_round=True, keep=False):
     return y
 
 
-def loss_and_grad(p, x, t, lo, hi, bf16_round=True):
+def loss_and_grad(p, x, t, lo, hi, bf16_round=True, keep=False):
     """Mean squared error and its gradient with respect to p (flattened).
     With bf16_round the backward pass rounds the back-propagated signal of
-    the 256 x 256 layers to bfloat16 where the kernels do."""
+    the 256 x 256 layers to bfloat16 where the kernels do. With keep, also
+    the forward intermediates (z, pre, h) and the back-propagated signals
+    {"dy": dL/dy, "dz0".."dz3": dL/dpre of each hidden layer}."""
     P = unpack(p)
     r = bf16 if bf16_round else (lambda a: np.asarray(a, dtype=np.float64))
     y, (z, pre, h) = forward(p, x, lo, hi, bf16_round, keep=True)
@@ -104,12 +106,16 @@ def loss_and_grad(p, x, t, lo, hi, bf16_round=True):
     g["W4"] = h[3].T @ dy
     g["b4"] = np.array([dy.sum()])
     dz = np.outer(dy, P["W4"]) * silu_grad(pre[3])
+    sig = {"dy": dy, "dz3": dz}
     for l in (3, 2, 1):
         g["W%d" % l] = r(dz).T @ h[l - 1]
         g["b%d" % l] = dz.sum(axis=0)
         dh = r(dz) @ r(P["W%d" % l])
         dz = dh * silu_grad(pre[l - 1])
+        sig["dz%d" % (l - 1)] = dz
     g["W0"] = dz.T @ z
     g["b0"] = dz.sum(axis=0)
     grad = np.concatenate([g[name].reshape(-1) for name, _, _ in LAYOUT])
+    if keep:
+        return float(np.mean((y - t) ** 2)), grad, (z, pre, h), sig
     return float(np.mean((y - t) ** 2)), grad

@@ -60,8 +60,14 @@ def _features(x):
 
 
 def test_loss_gradient_matches_fp64_reference(env):
+    # Element by element against the CPU FP64 reference with the kernels'
+    # bfloat16 roundings replayed (bf16_round=True); the per-element tolerance
+    # is one bfloat16 unit of each element's magnitude scale (tests/mlp_bounds.py:
+    # the rounding decisions that FP32 arithmetic may take the other way).
+    # The relative norm of each block is kept only as a summary.
     torch, H = env
     from oracle import mlp_oracle as M
+    from tests import mlp_bounds as B
     h = H.hjm_surrogate_create(_cfg(H))
     try:
         p = H.hjm_surrogate_get_params(h).astype(np.float64)
@@ -72,20 +78,25 @@ def test_loss_gradient_matches_fp64_reference(env):
         loss = H.hjm_surrogate_loss_grad(h, torch.tensor(x).cuda(), torch.tensor(t).cuda(), g)
         torch.cuda.synchronize()
         lo, hi = np.array(W.SURROGATE_BOX_LO), np.array(W.SURROGATE_BOX_HI)
-        lref, gref = M.loss_and_grad(p, _features(x), t.astype(np.float64), lo, hi, bf16_round=True)
+        f, t64 = _features(x), t.astype(np.float64)
+        lref, gref = M.loss_and_grad(p, f, t64, lo, hi, bf16_round=True)
         assert abs(loss - lref) <= 1e-4 * abs(lref)
         gg = g.cpu().numpy().astype(np.float64)
+        scale = B.grad_scale(p, f, t64, lo, hi)
         for name, shape, off in M.LAYOUT:
             n = int(np.prod(shape))
-            a, b = gg[off:off + n], gref[off:off + n]
-            rel = np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
-            assert rel < 5e-3, (name, rel)
-        # forward agrees as well
+            sl = slice(off, off + n)
+            excess, i = B.elementwise_excess(gg[sl], gref[sl], scale[sl])
+            assert excess <= 1.0, (name, i, gg[off + i], gref[off + i], scale[off + i])
+            rel = np.linalg.norm(gg[sl] - gref[sl]) / max(np.linalg.norm(gref[sl]), 1e-30)
+            assert rel < 5e-3, (name, rel)  # summary
+        # forward pass, row by row
         y = torch.empty(192, dtype=torch.float32, device="cuda")
         H.hjm_surrogate_forward(h, torch.tensor(x).cuda(), y)
         torch.cuda.synchronize()
-        yref = M.forward(p, _features(x), lo, hi, bf16_round=True)
-        assert np.max(np.abs(y.cpu().numpy() - yref)) <= 2e-3 * max(1.0, np.max(np.abs(yref)))
+        yref = M.forward(p, f, lo, hi, bf16_round=True)
+        excess, i = B.elementwise_excess(y.cpu().numpy(), yref, B.forward_scale(p, f, lo, hi))
+        assert excess <= 1.0, (i, excess)
     finally:
         H.hjm_surrogate_destroy(h)
 
