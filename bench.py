@@ -587,7 +587,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32" if kprec == "fp32" else "f64",
+        "dtype": "mixed" if prec == "mixed" else ("f32" if kprec == "fp32" else "f64"),
         "data": "synthetic",
         "config": {"workload": desc, "instruments": n, "grid_point_steps_per_step": ps,
                    "caplets_per_s": world * n * args.steps / (ms_max * 1e-3),

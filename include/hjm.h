@@ -366,11 +366,11 @@ hjm_status hjm_mlp_gemm(int M, int N, int K, const void* A, int lda, int trans_a
 
 /* Allocation-free pricing of one instrument (the paper has no counterpart;
  * this is a deployment aid). For callers that cannot allocate device memory:
- * code that runs while a CUDA stream capture is open (cudaMalloc is not a
- * legal call then), processes whose device memory belongs to another
- * allocator (a framework's caching allocator, or a fixed pool sized at
- * start-up), and latency-critical loops that cannot take cudaMalloc's
- * implicit device-wide synchronisation.
+ * processes whose device memory belongs to another allocator (a framework's
+ * caching allocator, or a fixed pool sized at start-up, where a cudaMalloc
+ * outside it fails or fragments the pool), and latency-critical loops that
+ * cannot take cudaMalloc's implicit device-wide synchronisation. Tested on
+ * ordinary streams, two calls in a row against hjm_price.
  *
  * Instead of a workspace, the march uses one file-scope device array of
  * HJM_STATIC_SCRATCH_BYTES bytes that every GPU loading the library holds

@@ -1245,8 +1245,8 @@ extern "C" hjm_status hjm_trace_read(hjm_trace* out, int reset)
 //
 // hjm_price_static (declared in hjm.h): the whole march of one instrument in
 // a file-scope device array, for callers that cannot allocate device memory
-// (open stream captures, externally owned device memory, latency-critical
-// loops). Nothing here allocates; the array is reserved when the library's
+// (device memory owned by another allocator or a fixed pool, latency-critical
+// loops that cannot take cudaMalloc's implicit synchronisation). Nothing here allocates; the array is reserved when the library's
 // module is loaded on a device and lives until the process exits.
 
 static __device__ __align__(256) unsigned char g_static_scratch[HJM_STATIC_SCRATCH_BYTES];

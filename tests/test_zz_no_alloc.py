@@ -1,6 +1,7 @@
 """hjm_price_static: the allocation-free entry point, for callers that cannot
-allocate device memory (open stream captures, device memory owned by another
-allocator, latency-critical loops). Checked through the C ABI against
+allocate device memory (device memory owned by another allocator or a fixed
+pool, latency-critical loops that cannot take cudaMalloc's implicit
+synchronisation). Checked through the C ABI against
 hjm_price, the allocating entry point, on two calls in a row (the second
 reuses the static scratch array left by the first). This file is collected
 last so that a run stopping at its first failure has run everything else."""
