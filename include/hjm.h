@@ -260,8 +260,14 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * copies the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v nodes
  * into a shared-memory ring and marches over p1_planes (1..4096) y nodes
  * (p1_planes = 0 unless staged; staged needs n_r * element size a multiple
- * of 16 and the ring within the shared memory of a CTA). A shape changes speed and the rounding of the line
- * solves, nothing else.
+ * of 16 and the ring within the shared memory of a CTA), 2 the same march
+ * with each y plane's strip copied by the Tensor Memory Accelerator (one
+ * box copy per plane, FP32, n_r a multiple of 32, v strips of at least 3
+ * nodes or a multiple of the strip; shapes (p1_lanes: p1_nodes) (4: 16),
+ * (8: 8, 12, 16), (16: 12, 16), (32: 16); lines of r nodes at the Section
+ * 5.1 Douglas stage only: the Craig-Sneyd correction stage and groups with
+ * gamma > 0 or theta_adi = 0 fall back to the default shape of pass 1). A
+ * shape changes speed and the rounding of the line solves, nothing else.
  * tile_cfg in hjm_price_info packs p1_lanes | p1_nodes << 8 | p1_lines << 14
  * | p2_warps << 21 | p3_warps << 25 | p1_staged << 29. */
 typedef struct {
@@ -394,6 +400,20 @@ hjm_status hjm_mlp_gemm(int M, int N, int K, const void* A, int lda, int trans_a
 #define HJM_STATIC_SCRATCH_BYTES (8u << 20)
 hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision precision, double* price_out,
                             void* cuda_stream);
+
+/* Bounded device-side waits (no counterpart in the paper). The TMA-fed pass
+ * 1 (p1_staged = 2) waits on a barrier for each y plane it copies; a CTA
+ * whose wait runs out of polls (the copy never arrived) stops without
+ * writing the rest of its planes and is counted. hjm_wait_status
+ * synchronises the current device and returns HJM_ETIMEOUT when any CTA has
+ * given up since the last reset (reset != 0 clears the count), HJM_OK
+ * otherwise; hjm_price and hjm_price_batch with host outputs check it
+ * themselves. hjm_test_drop_plane is a test hook: from the next launch on,
+ * the copy of y plane `plane` (0 .. n_y - 1 of every instrument) is never
+ * started and each wait gives up after `polls` polls; plane = -1 and polls
+ * = 0 restore normal operation. */
+hjm_status hjm_wait_status(int reset);
+hjm_status hjm_test_drop_plane(int plane, unsigned polls);
 
 const char* hjm_status_string(hjm_status status);
 const char* hjm_last_error(void);

@@ -271,6 +271,7 @@ struct Group {
     int scheme = HJM_SCHEME_DOUGLAS;  // the same for every instrument of the group
     std::vector<size_t> idx;  // positions in the caller's item array
     bool gpos = false;
+    bool theta0 = false;  // some instrument has theta = 0 (no TMA-fed pass 1)
     Tile tile{};
     GroupTables t{};
     void* U = nullptr;
@@ -533,6 +534,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         if (gr.idx.empty()) gr.tile = tile_for(gr.nr, gr.nv, gr.ny, elem);
         gr.idx.push_back(i);
         gr.gpos = gr.gpos || items[i].model.gamma > 0.0;
+        gr.theta0 = gr.theta0 || !(items[i].grid.theta_adi > 0.0);
     }
     size_t bytes = align256(n * sizeof(InstParams)) + align256(n * sizeof(long long)) +
                    4 * align256(n * sizeof(double)) + 2 * align256(2 * n * sizeof(double));
@@ -584,6 +586,7 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         g.t.B = (int)B;
         g.t.p2P = g.tile.p2_P;
         g.t.p3P = g.tile.p3_P;
+        g.t.tma_ok = !g.gpos && !g.theta0;
         g.t.params = *d_params + off;
         g.prices = group_prices + off;
         g.ind = group_ind + off;
@@ -655,6 +658,17 @@ hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, siz
     return HJM_OK;
 }
 
+// HJM_ETIMEOUT (and the count cleared) when a bounded device-side wait of
+// the march gave up since the last check.
+static hjm_status check_waits()
+{
+    unsigned n = 0;
+    CU_TRY(pass1t_timeouts(&n, false));
+    if (n == 0) return HJM_OK;
+    CU_TRY(pass1t_timeouts(&n, true));
+    return fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n);
+}
+
 // Core of hjm_price_batch (caller holds g_mu, items validated).
 //  FP32 / FP64: one march in that precision.
 //  MIXED: the FP32 march; every instrument whose rounding indicator exceeds
@@ -688,6 +702,8 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
         CU_TRY(cudaMemcpyAsync(hi.data(), d_ind, n * sizeof(double), cudaMemcpyDeviceToHost, s));
         CU_TRY(cudaStreamSynchronize(s));
         if (g_trace_on) trace_collect();
+        st = check_waits();
+        if (st != HJM_OK) return st;
     }
     if (prec == HJM_MIXED) {
         std::vector<hjm_batch_item> redo;
@@ -945,6 +961,33 @@ static std::vector<Tile> pass1_candidates(int nr, int nv, int ny, size_t elem, c
                     t.p1_M = M;
                     t.p1_R = R;
                     t.p1_stage = 1;
+                    t.p1_J = J;
+                    if (tile_valid(t, nr, nv, ny, elem)) out.push_back(t);
+                }
+        }
+    // y planes staged by TMA (FP32; the launcher falls back to the default
+    // rows-from-memory shape for groups the kernel does not cover)
+    int cover2 = 1 << 30;
+    for (int S : {4, 8, 16, 32})
+        for (int M : {8, 12, 16}) {
+            Tile t = base;
+            t.p1_S = S;
+            t.p1_M = M;
+            t.p1_R = 1;
+            t.p1_stage = 2;
+            t.p1_J = 8;
+            if (tile_valid(t, nr, nv, ny, elem)) cover2 = std::min(cover2, S * M);
+        }
+    for (int S : {4, 8, 16, 32})
+        for (int M : {8, 12, 16}) {
+            if (S * M > std::max(nr + nr / 4, cover2)) continue;
+            for (int R : {1, 2})
+                for (int J : {8, 16, 32}) {
+                    Tile t = base;
+                    t.p1_S = S;
+                    t.p1_M = M;
+                    t.p1_R = R;
+                    t.p1_stage = 2;
                     t.p1_J = J;
                     if (tile_valid(t, nr, nv, ny, elem)) out.push_back(t);
                 }
@@ -1225,6 +1268,28 @@ extern "C" hjm_status hjm_douglas_pass(hjm_grid* grid, const hjm_instrument* ins
     return HJM_OK;
 }
 
+extern "C" hjm_status hjm_wait_status(int reset)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    CU_TRY(cudaDeviceSynchronize());
+    unsigned n = 0;
+    CU_TRY(pass1t_timeouts(&n, reset != 0));
+    return n ? fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n) : HJM_OK;
+}
+
+extern "C" hjm_status hjm_test_drop_plane(int plane, unsigned polls)
+{
+    if (plane < -1) return fail(HJM_EINVAL, "plane must be >= -1");
+    std::lock_guard<std::mutex> lk(g_mu);
+    hjm_status st = ensure_init();
+    if (st != HJM_OK) return st;
+    CU_TRY(cudaDeviceSynchronize());
+    CU_TRY(pass1t_test_drop(plane, plane < 0 || polls == 0 ? (1u << 22) : polls));
+    return HJM_OK;
+}
+
 extern "C" hjm_status hjm_trace_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -1332,6 +1397,7 @@ extern "C" hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision
     }
     t.p2P = tile.p2_P;
     t.p3P = tile.p3_P;
+    t.tma_ok = item->model.gamma == 0.0 && item->grid.theta_adi > 0.0;
     // Every region above is fully rewritten by the kernels below before it
     // is read (the set-up kernel also zeroes the rounding indicator), so no
     // clearing is needed between calls.

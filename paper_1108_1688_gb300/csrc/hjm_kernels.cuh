@@ -18,6 +18,9 @@
 //   v split  vp[b][sys]               factors of the v system split into
 //   y split  yp[b][n_v][sys]          p2P (p3P) chunks, one warp per chunk
 //                                     (see part_sys_size; y: gamma == 0)
+//   r folded r2[b][R2_N][n_r]         the r tables recombined for the TMA-fed
+//                                     pass 1 (dt and 1/theta folded in, the
+//                                     Dirichlet nodes zeroed; see R2_L ..)
 //   flags    fl[b][FL_N]              r_min Dirichlet, y face order, y LU
 //                                     present, read-out stencil corner (i, k)
 //   indicator acc[b][n_steps] (float) max |dU3| of each step over the 4 x 4
@@ -64,6 +67,21 @@ struct InstDerived {
 constexpr double kIndicatorC = 8.0;
 
 enum { RT_R, RT_IJ, RT_C1, RT_C4V, RT_C4B, RT_C3, RT_CY, RT_N };
+// Folded r tables of the TMA-fed pass 1 (gamma = 0 groups). With C1, C4V,
+// IJ, C4B, C3, CY the RT_ factors above, z the node's rate, dt the step and
+// theta the ADI weight, the kernel solves the r system divided by theta,
+//   a x_{i-1} + b x_i + c x_{i+1} = dt F / theta,
+//   a = s_I - v L,  c = -(v U + s_I),  b = B + 2 v E1,  s_I = (a_I + y) P + Q
+// (a_I = a(t^{n+1/2})), and forms the explicit r part from the undivided
+// second and first differences of U^n (no cancelling sums of large terms):
+//   (dt/theta) A_r U = g1 d2U + g4 d1U + RT U,
+//   g1 = (v/theta) E1,  g4 = (a_F + y)/theta P + QT - (v/theta) E4.
+// So L = dt (C1 + C4V), U = dt (C1 - C4V), P = dt IJ, Q = dt C4B,
+// B = 1/theta + dt z, E1 = dt C1, E4 = dt C4V, QT = Q / theta,
+// RT = -dt z / theta; X and Y are the mixed-term and y-drift factors times
+// dt. The Dirichlet nodes (i = 0 and i = n_r - 1 when gamma = 0) carry zeros
+// and B = 1, so their rows are identity rows without a branch per node.
+enum { R2_L, R2_U, R2_P, R2_Q, R2_B, R2_E1, R2_E4, R2_QT, R2_RT, R2_X, R2_Y, R2_N };
 enum { VT_V, VT_IJ, VT_G2, VT_G5, VT_FV, VT_N };
 enum { YT_Y, YT_IJ, YT_KY, YT_N };
 // Correction stage of the Craig-Sneyd family (all explicit operators at
@@ -73,7 +91,8 @@ enum { YT_Y, YT_IJ, YT_KY, YT_N };
 // he = 1 for HV (B = Y3), 0 otherwise (B = U^n). SC_CX = 1/2 - c1 is the
 // extra weight of the mixed term; on Dirichlet nodes Z0 - B = kd (g - U -
 // c1 E) with kd = (1 - he) / (1 - c1) (there E = g - U^n).
-enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_C1, SC_CX, SC_HE, SC_KD, SC_N };
+// SC_ITH = 1 / theta (0 when theta = 0).
+enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_C1, SC_CX, SC_HE, SC_KD, SC_ITH, SC_N };
 enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_RI0, FL_RK0, FL_PAD, FL_N };
 
 template <typename T>
@@ -81,6 +100,7 @@ struct March {
     int nr, nv, ny, nsteps, B;
     long long N;  // nr * nv * ny
     const T* rt;
+    const T* r2;
     const T* vt;
     const T* yt;
     const T* sc;
@@ -93,6 +113,8 @@ struct March {
     const T* vp;
     const T* yp;
     int p2P, p3P;  // chunks per v line / y line (1: one thread per line)
+    int tma_ok;    // every instrument has gamma = 0 and theta > 0 (the TMA-fed
+                   // pass 1 applies)
 };
 
 // Largest number of chunks a strided line is split into, and the largest
@@ -131,6 +153,7 @@ struct GroupTables {
     double* axv;          // [B][3][nv]
     double* axy;          // [B][3][ny]
     void* rt;
+    void* r2;
     void* vt;
     void* yt;
     void* sc;
@@ -143,6 +166,7 @@ struct GroupTables {
     void* vp;             // split factors (sized for kMaxSplit chunks)
     void* yp;
     int p2P, p3P;         // chunks per v / y line used by set-up and march
+    int tma_ok = 0;       // gamma = 0 and theta > 0 for every instrument
 };
 
 // Bytes of the march-type tables of a group.
@@ -168,7 +192,8 @@ struct Tile {
     int p1_R;  // pass 1: lines per lane segment per CTA
     int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8); 0: passes 2 and 3 fused
     int p3_P;  // pass 3: warps sharing each y line (1, 2, 4, 8)
-    int p1_stage;  // pass 1: 0 rows from global memory, 1 staged y planes
+    int p1_stage;  // pass 1: 0 rows from global memory, 1 staged y planes,
+                   // 2 y planes staged by TMA (k_pass1t, FP32, gamma = 0)
     int p1_J;      // pass 1 staged: y planes marched per CTA (0 when not staged)
 };
 Tile default_tile(int nr, int nv, int ny, size_t elem);
@@ -202,6 +227,20 @@ cudaError_t init_pass1();
 int pass1_chunk(int nr);
 // Largest line length pass 2 / pass 3 accept for this element size.
 int max_strided_len(size_t elem, bool gamma_pos);
+
+// TMA-fed pass 1 (hjm_pass1t.cu): whether it covers the shape (FP32, gamma =
+// 0, n_r a multiple of 32, a compiled (S, M)), its launch, the one-time
+// attribute set-up and the count of its bounded waits that ran out.
+bool pass1t_valid(const Tile& t, int nr, int nv, int ny, size_t elem);
+cudaError_t launch_pass1t(const March<float>& P, const float* U, float* out, int n, const Tile& t,
+                          cudaStream_t s);
+cudaError_t init_pass1t();
+// Reads (and with reset clears) the number of CTAs of the TMA-fed pass 1 that
+// gave up a wait on a plane copy; synchronises the device.
+cudaError_t pass1t_timeouts(unsigned* count, bool reset);
+// Test hook: plane index that the next launches never copy (-1: off), so
+// the waits for it run out; wait limit in polls.
+cudaError_t pass1t_test_drop(int plane, unsigned limit);
 
 template <typename T>
 March<T> march_args(const GroupTables& g);

@@ -837,9 +837,10 @@ Tile default_tile(int nr, int nv, int ny, size_t elem)
 
 bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
 {
-    if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
     if (!(split_valid(nv, t.p2_P) || pass23_valid(nr, nv, ny, t.p2_P, elem)) || !split_valid(ny, t.p3_P))
         return false;
+    if (t.p1_stage == 2) return pass1t_valid(t, nr, nv, ny, elem);
+    if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
     if (t.p1_stage == 0) return t.p1_J == 0;
     // staged rows are copied in 16-byte pieces
     if ((nr * (int)elem) % 16 != 0) return false;
@@ -911,6 +912,7 @@ cudaError_t init_pass1()
     P1_SHAPES_F32(P1_ATTR)
     P1_SHAPES_F64(P1_ATTR)
 #undef P1_ATTR
+    if (e == cudaSuccess) e = init_pass1t();
     return e;
 }
 
@@ -919,6 +921,17 @@ cudaError_t launch_pass1(const March<T>& P, const T* U, const T* Y, T* out, int 
                          cudaStream_t s)
 {
     if (!tile_valid(t, P.nr, P.nv, P.ny, sizeof(T))) return cudaErrorInvalidValue;
+    if (t.p1_stage == 2) {
+        // TMA-fed pass 1; the correction stage of the Craig-Sneyd family and
+        // groups with gamma > 0 or theta = 0 run the default rows-from-memory
+        // shape instead
+        if constexpr (sizeof(T) == 4)
+            if (Y == nullptr && P.tma_ok) return launch_pass1t(P, U, out, n, t, s);
+        Tile t0 = default_tile(P.nr, P.nv, P.ny, sizeof(T));
+        t0.p2_P = t.p2_P;
+        t0.p3_P = t.p3_P;
+        return launch_pass1<T>(P, U, Y, out, n, t0, s);
+    }
     const int S = t.p1_S, M = t.p1_M;
 #define P1_CASE(T_, S_, M_) \
     if (S == S_ && M == M_) return p1_launch<T, S_, M_>(P, U, Y, out, n, t, s);

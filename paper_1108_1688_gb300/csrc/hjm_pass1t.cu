@@ -1,0 +1,685 @@
+// Pass 1 of a Douglas ADI step (Section 5.1) for FP32 groups whose
+// instruments all have gamma = 0 and theta > 0, with the rows of U^n moved
+// into shared memory by the Tensor Memory Accelerator. It computes what
+// k_pass1 (hjm_pass1.cu) computes,
+//   dU0 = dt F(U^n; t^n)  (Eq. (1) in the metric form of Section 4.3, the
+//                          centred differences of Section 5, the r-v mixed
+//                          term explicit)
+//   (I - theta dt A_r(t^{n+1/2})) dU1 = dU0,
+// with less work per grid point:
+//  - the r factors are recombined per node once per instrument (the R2_
+//    tables: dt and 1/theta folded in, Dirichlet nodes as identity rows), so
+//    each coefficient of a line is one fused multiply-add of a per-line
+//    scalar and a table value, and the system is solved divided by theta;
+//  - a CTA owns a strip of consecutive v lines and marches along y; each y
+//    plane's strip (plus one halo line on each side) arrives by one
+//    cp.async.bulk.tensor box copy issued by one thread into a ring of four
+//    shared-memory slots with an mbarrier each, so the SM issues no load
+//    instructions for the rows and every row crosses L2 about once;
+//  - the tensor is viewed as 32-node chunks (x0, chunk, v, y plane) and the
+//    box is 36 nodes wide in x0: the four nodes past each chunk are outside
+//    the tensor and arrive as zeros, which pads every 128-byte chunk to 144
+//    bytes in shared memory so that the lanes' 16-byte reads of their nodes
+//    fall in distinct banks without any address swizzle;
+//  - the forward elimination of the partition solve runs inside the
+//    right-hand-side sweep, node pair by node pair, so only the eliminated
+//    rows stay live, and the interface system is solved by parallel cyclic
+//    reduction on rows normalised to a unit diagonal (three shuffles each
+//    way per level, one reciprocal per level).
+// An r line is owned by S lanes of a warp holding M consecutive nodes each
+// (S M a multiple of 32, at least n_r; the nodes past n_r are identity rows
+// fed with zeros). Every wait on a plane copy is bounded: a CTA whose wait
+// runs out counts itself in a device counter (read by pass1t_timeouts),
+// waits a bounded time for its other copies and leaves without writing.
+#include <cuda.h>  // CUtensorMap and the tensor-map encoder's signature
+
+#include <mutex>
+
+#include "hjm_kernels.cuh"
+
+namespace hjm {
+namespace {
+
+constexpr int kSlots = 4;          // y planes in the ring
+constexpr int kChunk = 32;         // nodes per chunk of the tensor view
+constexpr int kChunkPad = 36;      // nodes per chunk in shared memory
+constexpr int kChunkBytes = kChunkPad * 4;
+constexpr unsigned kWaitPolls = 1u << 22;  // polls of a plane's barrier before giving up
+
+template <int S, int M>
+struct Shape1t {
+    static constexpr int G = 32 / S;           // lines side by side in a warp
+    static constexpr int BX = S * M;           // nodes per staged row
+    static constexpr int NCH = BX / kChunk;    // chunks per staged row
+    static constexpr int RSB = NCH * kChunkBytes;  // bytes per staged row
+    // table row of a lane padded so that the lanes' 16-byte reads of one
+    // table fall in distinct banks (M / 4 odd)
+    static constexpr int MP = ((M / 4) & 1) ? M : M + 4;
+    static_assert(M % 4 == 0 && BX % kChunk == 0, "whole 16-byte vectors and whole chunks");
+};
+
+__device__ unsigned g_p1t_timeouts;   // CTAs that gave up a wait
+__device__ int g_p1t_drop = -1;       // test hook: plane never copied
+__device__ unsigned g_p1t_limit = kWaitPolls;
+
+__host__ __device__ inline int round128(int x) { return (x + 127) & ~127; }
+
+
+// ----------------------------------------------------- PTX: TMA, mbarrier
+
+__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Makes the initialised barriers visible to the asynchronous (TMA) proxy.
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// One box (36 x NCH x rows x 1) of the 4-D view into shared memory at dst;
+// completion is signalled on bar. c0 is always 0 (16-byte aligned).
+__device__ __forceinline__ void tma_box(unsigned dst, const CUtensorMap* tm, int c1, int c2, int c3, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+        "l"(reinterpret_cast<unsigned long long>(tm)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;\n" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Paired FP32 arithmetic (one instruction for both components, each rounded
+// as its scalar counterpart).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+__device__ __forceinline__ float4 lds4(const unsigned char* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 lds4f(const float* p) { return *reinterpret_cast<const float4*>(p); }
+
+}  // namespace
+
+namespace {
+
+// Per-plane scalars, stored as pairs (both components equal) so that the
+// paired instructions take them without a copy: (a(t^n) + y) / theta,
+// a(t^{n+1/2}) + y, 1 / (2 h_y J_y theta), -2 kappa y dt / (2 h_y J_y theta),
+// the y-face weights yA, yB of the neighbour planes ja, jb (A_y U =
+// g6 (yA (U_ja - U) + yB (U_jb - U))), and the Dirichlet data (g at r_min,
+// g at r_max).
+enum { PJ_AF = 0, PJ_AI = 2, PJ_IJY = 4, PJ_KYY = 6, PJ_YA = 8, PJ_YB = 10, PJ_G = 12, PJ_N = 16 };
+// Per-line scalars, as pairs: v, v / theta, -v, -v / theta, 2 v, the weights
+// of the v-neighbour rows' second difference (U_a - U) + (U_b - U) and
+// difference U_b - U_a, (cA + cB) / 2 and (cB - cA) / 2 times dt / theta
+// (cA, cB from the v tables, one-sided on the v faces), and the mixed-term
+// weight v / (J_v theta) (0 on the v faces).
+enum { LK_V = 0, LK_VT = 2, LK_NV = 4, LK_NVT = 6, LK_TV = 8, LK_CS = 10, LK_CD = 12, LK_VQ = 14, LK_N = 16 };
+
+}  // namespace
+
+namespace {
+
+// Shared-memory bytes of one launch shape: barriers, tables, per-plane and
+// per-line scalars, and the ring.
+__host__ __device__ inline int p1t_smem(int S, int M, int RK, int JC)
+{
+    const int G = 32 / S, MP = ((M / 4) & 1) ? M : M + 4, KB = 4 * G * RK;
+    const int slot = round128((KB + 2) * (S * M / kChunk) * kChunkBytes);
+    // 128 bytes of slack to align the layout to 128 bytes (the box copies'
+    // destinations) whatever the dynamic shared memory's base alignment
+    return 128 + 128 + round128(R2_N * S * MP * 4) + round128(PJ_N * JC * 4) + round128(LK_N * KB * 4) +
+           kSlots * slot;
+}
+
+// One r line on an S-lane segment; lane sl holds the line's nodes
+// e0 = sl M .. e0 + M - 1 and vo[q] is the byte offset of its q-th 4-node
+// vector in a staged row. rc, ra, rb: the staged rows of the line and of its
+// v neighbours (one-sided on the v faces) in plane j; pa, pb: the line's rows
+// in the y-neighbour planes ja, jb. tl: the lane's folded tables (table t at
+// tl + t S MP). lk, pj: the line's and the plane's scalar pairs. YIN: j is
+// not a y face (centred y difference). EXACT: n_r = S M, so the r_max node
+// is the last lane's last node. Returns dU1 on the lane's nodes in x.
+template <int S, int M, bool EXACT, bool YIN>
+__device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const unsigned char* rc,
+                                         const unsigned char* ra, const unsigned char* rb,
+                                         const unsigned char* pa, const unsigned char* pb, const int (&vo)[M / 4],
+                                         const float* lk, const float* pj, int sl, int nr, float (&x)[M])
+{
+    using C = Shape1t<S, M>;
+    constexpr int Q = M / 4;
+    constexpr int TS = S * C::MP;  // floats per table
+    constexpr unsigned FULL = 0xffffffffu;
+
+    // line and plane scalars (pairs)
+    const float4 k01 = lds4f(lk), k23 = lds4f(lk + 4), k45 = lds4f(lk + 8), k67 = lds4f(lk + 12);
+    const float4 j01 = lds4f(pj), j23 = lds4f(pj + 4), j45 = lds4f(pj + 8), j67 = lds4f(pj + 12);
+    const float2 v2 = f2(k01.x, k01.y), vt2 = f2(k01.z, k01.w), nv2 = f2(k23.x, k23.y);
+    const float2 nvt2 = f2(k23.z, k23.w), tv2 = f2(k45.x, k45.y), cS2 = f2(k45.z, k45.w);
+    const float2 cD2 = f2(k67.x, k67.y), vq2 = f2(k67.z, k67.w);
+    const float2 aF2 = f2(j01.x, j01.y), aI2 = f2(j01.z, j01.w);
+    const float2 vy2 = mul2(v2, f2(j23.x, j23.y)), ky2 = f2(j23.z, j23.w);
+    const float2 yA2 = f2(j45.x, j45.y), yB2 = f2(j45.z, j45.w);
+    const float gLo = j67.x, gHi = j67.y;
+
+    // The line's U^n, and of its v-neighbour rows the second difference
+    // (U_a - U) + (U_b - U) and the difference U_b - U_a.
+    float uc[M], ws[M], wd[M];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float4 c = lds4(rc + vo[q]), a = lds4(ra + vo[q]), b = lds4(rb + vo[q]);
+        uc[4 * q] = c.x;
+        uc[4 * q + 1] = c.y;
+        uc[4 * q + 2] = c.z;
+        uc[4 * q + 3] = c.w;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 u = h ? f2(c.z, c.w) : f2(c.x, c.y);
+            const float2 ua = h ? f2(a.z, a.w) : f2(a.x, a.y), ub = h ? f2(b.z, b.w) : f2(b.x, b.y);
+            const float2 s2 = add2(sub2(ua, u), sub2(ub, u)), d2 = sub2(ub, ua);
+            ws[4 * q + 2 * h] = s2.x;
+            ws[4 * q + 2 * h + 1] = s2.y;
+            wd[4 * q + 2 * h] = d2.x;
+            wd[4 * q + 2 * h + 1] = d2.y;
+        }
+    }
+    // r neighbours across lanes (at the line's ends the lane's own values:
+    // finite, and multiplied by the zero tables of the Dirichlet or padding node)
+    const float uL = __shfl_up_sync(FULL, uc[M - 1], 1, S), uR = __shfl_down_sync(FULL, uc[0], 1, S);
+    const float wL = __shfl_up_sync(FULL, wd[M - 1], 1, S), wR = __shfl_down_sync(FULL, wd[0], 1, S);
+    const float u0 = uc[0], uM = uc[M - 1];
+    // first differences e[m] = U_{m+1} - U_m, m = -1 .. M-1 (stored at m + 1)
+    float e[M + 1];
+    e[0] = uc[0] - uL;
+#pragma unroll
+    for (int m = 0; m < M - 1; ++m) e[m + 1] = uc[m + 1] - uc[m];
+    e[M] = uR - uc[M - 1];
+
+    // Node pairs: the right-hand side dt F / theta, the row of the r system
+    // divided by theta (a x_{m-1} + b x_m + c x_{m+1} with c = -up), and the
+    // forward elimination of the partition solve: rows m >= 1 become
+    //   A[m] x_s + x_m + C[m] x_{m+1} = D[m]   (x_s: the lane's first unknown),
+    // row 0 A[0] x_prev + x_s + C[0] x_1 = D[0] (x_prev: the previous lane's
+    // last unknown).
+    float A[M], Cc[M], D[M];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const float* t = tl + 4 * q;
+        const float4 tL = lds4f(t + R2_L * TS), tU = lds4f(t + R2_U * TS), tP = lds4f(t + R2_P * TS);
+        const float4 tQ = lds4f(t + R2_Q * TS), tB = lds4f(t + R2_B * TS), tE1 = lds4f(t + R2_E1 * TS);
+        const float4 tE4 = lds4f(t + R2_E4 * TS), tQT = lds4f(t + R2_QT * TS), tRT = lds4f(t + R2_RT * TS);
+        const float4 tX = lds4f(t + R2_X * TS), tY = lds4f(t + R2_Y * TS);
+        const float4 ya = lds4(pa + vo[q]), yb = lds4(pb + vo[q]);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int m = 4 * q + 2 * h;
+#define HJM_PR(v4) (h ? f2(v4.z, v4.w) : f2(v4.x, v4.y))
+            const float2 Pp = HJM_PR(tP), E1 = HJM_PR(tE1);
+            const float2 u = f2(uc[m], uc[m + 1]);
+            // r part: g1 d2U + g4 d1U + RT U
+            const float2 d2 = f2(e[m + 1] - e[m], e[m + 2] - e[m + 1]);
+            const float2 d1 = f2(e[m + 1] + e[m], e[m + 2] + e[m + 1]);
+            const float2 g4 = fma2(nvt2, HJM_PR(tE4), fma2(aF2, Pp, HJM_PR(tQT)));
+            float2 acc = mul2(HJM_PR(tRT), u);
+            acc = fma2(mul2(vt2, E1), d2, acc);
+            acc = fma2(g4, d1, acc);
+            // v part: cA (U_{v,a} - U) + cB (U_{v,b} - U)
+            acc = fma2(cS2, f2(ws[m], ws[m + 1]), acc);
+            acc = fma2(cD2, f2(wd[m], wd[m + 1]), acc);
+            // mixed r-v term: X vq (wd_{m+1} - wd_{m-1})
+            const float wm1 = m > 0 ? wd[m - 1] : wL;
+            const float wp2 = m + 2 < M ? wd[m + 2] : wR;
+            acc = fma2(mul2(HJM_PR(tX), vq2), f2(wd[m + 1] - wm1, wp2 - wd[m]), acc);
+            // y part: g6 (yA (U_{y,a} - U) + yB (U_{y,b} - U))
+            const float2 g6 = fma2(HJM_PR(tY), vy2, ky2);
+            float2 ty;
+            if constexpr (YIN)
+                ty = sub2(HJM_PR(yb), HJM_PR(ya));
+            else
+                ty = fma2(yB2, sub2(HJM_PR(yb), u), mul2(yA2, sub2(HJM_PR(ya), u)));
+            acc = fma2(g6, ty, acc);
+            // row of the r system at t^{n+1/2}, divided by theta
+            const float2 sI = fma2(aI2, Pp, HJM_PR(tQ));
+            const float2 a = fma2(nv2, HJM_PR(tL), sI);   // -lower
+            const float2 up = fma2(v2, HJM_PR(tU), sI);   // upper (c = -up)
+            const float2 b = fma2(tv2, E1, HJM_PR(tB));   // 1/theta - diag
+#undef HJM_PR
+#pragma unroll
+            for (int z = 0; z < 2; ++z) {
+                const int mm = m + z;
+                const float az = z ? a.y : a.x, bz = z ? b.y : b.x, uz = z ? up.y : up.x;
+                const float dz = z ? acc.y : acc.x;
+                if (mm < 2) {
+                    const float r = rcp_approx(bz);
+                    A[mm] = az * r;
+                    Cc[mm] = -uz * r;
+                    D[mm] = dz * r;
+                } else {
+                    const float r = rcp_approx(fmaf(-az, Cc[mm - 1], bz));
+                    D[mm] = r * fmaf(-az, D[mm - 1], dz);
+                    A[mm] = -r * (az * A[mm - 1]);
+                    Cc[mm] = -uz * r;
+                }
+            }
+        }
+    }
+    // Dirichlet rows (identity rows from the tables): r_min on the first
+    // lane's first node, r_max on node n_r - 1.
+    if (sl == 0) D[0] = gLo - u0;
+    if constexpr (EXACT) {
+        if (sl == S - 1) D[M - 1] = gHi - uM;
+    } else {
+        const int mh = nr - 1 - sl * M;
+        if (mh >= 0 && mh < M) {
+            const int e = nr - 1;
+            const float un = *reinterpret_cast<const float*>(rc + (e >> 5) * kChunkBytes + (e & 31) * 4);
+#pragma unroll
+            for (int m = 0; m < M; ++m)
+                if (m == mh) D[m] = gHi - un;
+        }
+    }
+    // Backward elimination: rows 1 .. M-2 become A x_s + x_m + C x_e = D.
+#pragma unroll
+    for (int m = M - 3; m >= 1; --m) {
+        D[m] = fmaf(-Cc[m], D[m + 1], D[m]);
+        A[m] = fmaf(-Cc[m], A[m + 1], A[m]);
+        Cc[m] = -Cc[m] * Cc[m + 1];
+    }
+    // Row 0 in terms of x_prev and x_e.
+    {
+        const float r = rcp_approx(fmaf(-Cc[0], A[1], 1.0f));
+        D[0] = r * fmaf(-Cc[0], D[1], D[0]);
+        A[0] = r * A[0];
+        Cc[0] = -r * Cc[0] * Cc[1];
+    }
+    // Interface equations in the lanes' last unknowns x_e, normalised to a
+    // unit diagonal, solved by parallel cyclic reduction over width-S
+    // shuffles. Lanes without a partner s below (above) have al = 0 (ga = 0)
+    // already (the line's first row has no sub-diagonal, its last no
+    // super-diagonal, and each level doubles the zeroed span), so the
+    // out-of-range shuffles (which return the lane's own finite values) are
+    // multiplied by zero.
+    const float aS = A[0], cS = Cc[0], dS = D[0];
+    const float aE = A[M - 1], cE = Cc[M - 1], dE = D[M - 1];
+    float aSn = __shfl_down_sync(FULL, aS, 1, S);
+    float cSn = __shfl_down_sync(FULL, cS, 1, S);
+    float dSn = __shfl_down_sync(FULL, dS, 1, S);
+    if (sl == S - 1) aSn = cSn = dSn = 0.f;
+    float al, ga, de;
+    {
+        const float be = fmaf(-aE, cS, fmaf(-cE, aSn, 1.0f));
+        const float r = rcp_approx(be);
+        al = -aE * aS * r;
+        ga = -cE * cSn * r;
+        de = fmaf(-aE, dS, fmaf(-cE, dSn, dE)) * r;
+    }
+#pragma unroll
+    for (int s = 1; s < S; s <<= 1) {
+        const float alm = __shfl_up_sync(FULL, al, s, S), gam = __shfl_up_sync(FULL, ga, s, S);
+        const float dem = __shfl_up_sync(FULL, de, s, S);
+        const float alp = __shfl_down_sync(FULL, al, s, S), gap = __shfl_down_sync(FULL, ga, s, S);
+        const float dep = __shfl_down_sync(FULL, de, s, S);
+        const float r = rcp_approx(fmaf(-al, gam, fmaf(-ga, alp, 1.0f)));
+        const float nde = fmaf(-al, dem, fmaf(-ga, dep, de));
+        al = -al * alm * r;
+        ga = -ga * gap * r;
+        de = nde * r;
+    }
+    const float xE = de;
+    float xEp = __shfl_up_sync(FULL, xE, 1, S);
+    if (sl == 0) xEp = 0.f;
+    const float xS = fmaf(-aS, xEp, fmaf(-cS, xE, dS));
+#pragma unroll
+    for (int m = 1; m < M - 1; ++m) x[m] = fmaf(-A[m], xS, fmaf(-Cc[m], xE, D[m]));
+    x[0] = xS;
+    x[M - 1] = xE;
+}
+
+}  // namespace
+
+namespace {
+
+// Polls the barrier of plane p (slot (p - jf) & 3, phase parity
+// ((p - jf) >> 2) & 1) at most `limit` times.
+__device__ __forceinline__ bool wait_plane(unsigned bar0, int p, int jf, unsigned limit)
+{
+    const int i = p - jf;
+    const unsigned bar = bar0 + 8u * (unsigned)(i & (kSlots - 1)), par = (unsigned)((i >> 2) & 1);
+    for (unsigned it = 0; it < limit; ++it)
+        if (mbar_try_wait(bar, par)) return true;
+    return false;
+}
+
+// Grid: one CTA per (instrument b, strip of KB = 4 (32/S) RK v lines, run of
+// JC y planes); 4 warps, each segment of S lanes takes lines sg, sg + 4G, ...
+// of the strip for every plane of the run.
+// CTAs per SM the register budget is sized for: lanes of 12 or 16 nodes hold
+// more live rows than 128 registers (four CTAs) allow without spills.
+template <int M>
+struct P1tOcc {
+    static constexpr int value = M >= 12 ? 3 : 4;
+};
+
+template <int S, int M, bool EXACT>
+__global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<float> P, const __grid_constant__ CUtensorMap tm,
+                                                   float* __restrict__ out, const int n, const int RK, const int JC)
+{
+    using C = Shape1t<S, M>;
+    constexpr int G = C::G, MP = C::MP, Q = M / 4;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = sm_raw + ((128u - (su32(sm_raw) & 127u)) & 127u);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int seg = lane / S, sl = lane % S, sg = warp * G + seg;
+    const int nr = P.nr, nv = P.nv, ny = P.ny;
+    const int KB = 4 * G * RK;
+    const int strips = (nv + KB - 1) / KB, runs = (ny + JC - 1) / JC;
+    const int b = blockIdx.x / (strips * runs);
+    const int st = (blockIdx.x / runs) % strips, rn = blockIdx.x % runs;
+    const int k0 = st * KB, k1 = min(k0 + KB, nv);
+    const int j0 = rn * JC, j1 = min(j0 + JC, ny);
+    // Planes in the ring: from the y-1 neighbour of j0 (two planes further
+    // back for a run that ends on the y_max face, whose one-sided stencil
+    // reaches plane n_y - 3) to the y+1 neighbour of the run's last plane
+    // (at least plane 2 for a run starting on the y = 0 face).
+    const int jf = max(0, min(j0 - 1, ny - 3));
+    const int jl = min(max(j1, j0 == 0 ? 2 : 0), ny - 1);
+
+    unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm);
+    int* abort_flag = reinterpret_cast<int*>(sm + 64);
+    float* tsm = reinterpret_cast<float*>(sm + 128);
+    float* pjs = tsm + round128(R2_N * S * MP * 4) / 4;
+    float* lks = pjs + round128(PJ_N * JC * 4) / 4;
+    unsigned char* ring = reinterpret_cast<unsigned char*>(lks) + round128(LK_N * KB * 4);
+    const int slotB = round128((KB + 2) * C::RSB);
+    const unsigned bar0 = su32(bar), ring0 = su32(ring);
+    const unsigned boxB = (unsigned)((KB + 2) * C::RSB);
+
+    if (tid == 0) {
+        for (int i = 0; i < kSlots; ++i) mbar_init(bar0 + 8u * i, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    // folded r tables (nodes past n_r: zeros, B = 1, i.e. identity rows)
+    const float* __restrict__ r2 = P.r2 + (size_t)b * R2_N * nr;
+    for (int idx = tid; idx < R2_N * C::BX; idx += blockDim.x) {
+        const int t = idx / C::BX, e = idx % C::BX;
+        tsm[(t * S + e / M) * MP + e % M] = e < nr ? r2[t * nr + e] : (t == R2_B ? 1.0f : 0.0f);
+    }
+    const float* sc = P.sc + (size_t)b * SC_N;
+    const float dt = sc[SC_DT], ith = sc[SC_ITH], dth = dt * ith;
+    // per-plane scalars of the run
+    {
+        const float aF = P.st[((size_t)b * P.nsteps + n) * 2], aI = P.st[((size_t)b * P.nsteps + n) * 2 + 1];
+        const int yord = P.fl[(size_t)b * FL_N + FL_YORDER];
+        const float* yt = P.yt + (size_t)b * YT_N * ny;
+        const float* dir = P.dir + ((size_t)b * P.nsteps + n) * 2 * ny;
+        for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
+            const int j = j0 + jj;
+            const float y = yt[YT_Y * ny + j], iJy = yt[YT_IJ * ny + j], ky = yt[YT_KY * ny + j];
+            const bool yin = j > 0 && j < ny - 1;
+            const float yA = yin ? -1.f : (yord == 1 ? (j == 0 ? 2.f : -2.f) : (j == 0 ? 4.f : -4.f));
+            const float yB = yin ? 1.f : (yord == 1 ? 0.f : (j == 0 ? -1.f : 1.f));
+            const float v[6] = {(aF + y) * ith, aI + y, iJy * ith, ky * iJy * dth, yA, yB};
+            float* o = pjs + jj * PJ_N;
+            for (int q = 0; q < 6; ++q) o[2 * q] = o[2 * q + 1] = v[q];
+            o[PJ_G] = dir[j];
+            o[PJ_G + 1] = dir[ny + j];
+            o[PJ_G + 2] = o[PJ_G + 3] = 0.f;
+        }
+    }
+    // per-line scalars of the strip
+    {
+        const float* vt = P.vt + (size_t)b * VT_N * nv;
+        for (int li = tid; li < KB; li += blockDim.x) {
+            const int k = min(k0 + li, k1 - 1);
+            const float v = vt[VT_V * nv + k], g2 = vt[VT_G2 * nv + k], g5 = vt[VT_G5 * nv + k];
+            const float fv = vt[VT_FV * nv + k];
+            const bool vin = k > 0 && k < nv - 1;
+            const float vq = vin ? v * vt[VT_IJ * nv + k] : 0.f;
+            const float cA = vin ? g2 - g5 : (k == 0 ? 4.f * fv : -4.f * fv);
+            const float cB = vin ? g2 + g5 : (k == 0 ? -fv : fv);
+            const float w[8] = {v, v * ith, -v, -v * ith, 2.f * v, 0.5f * (cA + cB) * dth, 0.5f * (cB - cA) * dth,
+                                vq * ith};
+            float* o = lks + li * LK_N;
+            for (int q = 0; q < 8; ++q) o[2 * q] = o[2 * q + 1] = w[q];
+        }
+    }
+    // the lane's 4-node vectors within a staged row (32-node chunks padded to 36)
+    int vo[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int e = sl * M + 4 * q;
+        vo[q] = (e >> 5) * kChunkBytes + (e & 31) * 4;
+    }
+    __syncthreads();  // barriers initialised, tables and scalars in place
+
+    const int drop = g_p1t_drop;
+    const unsigned limit = g_p1t_limit;
+    int last = jf - 1;  // last plane copied (thread 0)
+    auto issue = [&](int p) {
+        last = p;
+        if (p == drop) return;  // test hook: the copy never starts, its waits run out
+        const int i = p - jf, s = i & (kSlots - 1);
+        mbar_expect_tx(bar0 + 8u * s, boxB);
+        tma_box(ring0 + (unsigned)(s * slotB), &tm, 0, k0 - 1, b * ny + p, bar0 + 8u * s);
+    };
+    if (tid == 0)
+        for (int p = jf; p <= min(j0 + 1, jl); ++p) issue(p);
+
+    const float* tl = tsm + sl * MP;
+    for (int j = j0; j < j1; ++j) {
+        __syncthreads();  // every thread is done with plane j-2's slot
+        if (*abort_flag) break;
+        if (tid == 0 && j + 2 <= jl) issue(j + 2);  // into the slot of plane j-2
+        const bool yin = j > 0 && j < ny - 1;
+        const int ja = yin ? j - 1 : (j == 0 ? 1 : ny - 2), jb = yin ? j + 1 : (j == 0 ? 2 : ny - 3);
+        if (!(wait_plane(bar0, j, jf, limit) && wait_plane(bar0, ja, jf, limit) &&
+              wait_plane(bar0, jb, jf, limit))) {
+            atomicExch(abort_flag, 1);
+            continue;
+        }
+        const unsigned char* pc = ring + ((j - jf) & (kSlots - 1)) * slotB;
+        const unsigned char* pa = ring + ((ja - jf) & (kSlots - 1)) * slotB;
+        const unsigned char* pb = ring + ((jb - jf) & (kSlots - 1)) * slotB;
+        const float* pjj = pjs + (j - j0) * PJ_N;
+        for (int r = 0; r < RK; ++r) {
+            const int li = sg + 4 * G * r;
+            const bool valid = k0 + li < k1;
+            const int k = valid ? k0 + li : k1 - 1;  // segment-uniform; invalid lines are not stored
+            const bool vin = k > 0 && k < nv - 1;
+            const int ka = vin ? k - 1 : (k == 0 ? 1 : nv - 2), kb = vin ? k + 1 : (k == 0 ? 2 : nv - 3);
+            const int rowc = (k - k0 + 1) * C::RSB;
+            float xr[M];
+            if (yin)
+                p1t_line<S, M, EXACT, true>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB, pc + (kb - k0 + 1) * C::RSB,
+                                            pa + rowc, pb + rowc, vo, lks + (k - k0) * LK_N, pjj, sl, nr, xr);
+            else
+                p1t_line<S, M, EXACT, false>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB,
+                                             pc + (kb - k0 + 1) * C::RSB, pa + rowc, pb + rowc, vo,
+                                             lks + (k - k0) * LK_N, pjj, sl, nr, xr);
+            if (valid) {
+                float* o = out + ((size_t)(b * ny + j) * nv + k) * nr + sl * M;
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    if (EXACT || sl * M + 4 * q + 4 <= nr)
+                        reinterpret_cast<float4*>(o)[q] =
+                            make_float4(xr[4 * q], xr[4 * q + 1], xr[4 * q + 2], xr[4 * q + 3]);
+            }
+        }
+    }
+    __syncthreads();  // every thread has left the loop (a late timeout is seen below)
+    if (tid == 0 && *abort_flag) {
+        // leave no copy in flight into this CTA's shared memory: wait (bounded)
+        // for the last planes copied, one per slot
+        for (int p = max(jf, last - kSlots + 1); p <= last; ++p)
+            if (p != drop) wait_plane(bar0, p, jf, limit);
+        atomicAdd(&g_p1t_timeouts, 1u);
+    }
+    __syncthreads();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------- host
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (the
+// library does not link the driver library).
+EncodeTiled encoder()
+{
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(f);
+    });
+    return fn;
+}
+
+// 4-D view of a group's FP32 field U[b][j][k][i]: (i mod 32, i / 32, k,
+// b n_y + j), box (36, chunks, rows, 1) starting at x0 = 0 (16-byte aligned).
+cudaError_t field_map(CUtensorMap* m, const float* U, int nr, int nv, long long planes, int chunks, int rows)
+{
+    const EncodeTiled fn = encoder();
+    if (!fn) return cudaErrorNotSupported;
+    const cuuint64_t dims[4] = {(cuuint64_t)kChunk, (cuuint64_t)(nr / kChunk), (cuuint64_t)nv, (cuuint64_t)planes};
+    const cuuint64_t strides[3] = {(cuuint64_t)kChunk * 4, (cuuint64_t)nr * 4, (cuuint64_t)nr * nv * 4};
+    const cuuint32_t box[4] = {(cuuint32_t)kChunkPad, (cuuint32_t)chunks, (cuuint32_t)rows, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(U), dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+constexpr int kSmemLimit = 227 * 1024;
+
+// (S, M) shapes compiled: n_r up to 64, 96, 128, 192, 256 and 512.
+#define P1T_SHAPES(X) X(4, 16) X(8, 8) X(8, 12) X(8, 16) X(16, 12) X(16, 16) X(32, 16)
+
+bool p1t_compiled(int S, int M)
+{
+#define P1T_IS(S_, M_) if (S == S_ && M == M_) return true;
+    P1T_SHAPES(P1T_IS)
+#undef P1T_IS
+    return false;
+}
+
+template <int S, int M>
+cudaError_t p1t_launch(const March<float>& P, const float* U, float* out, int n, const Tile& t, cudaStream_t s)
+{
+    using C = Shape1t<S, M>;
+    const int KB = 4 * C::G * t.p1_R;
+    CUtensorMap m;
+    cudaError_t e = field_map(&m, U, P.nr, P.nv, (long long)P.B * P.ny, C::NCH, KB + 2);
+    if (e != cudaSuccess) return e;
+    const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
+    const unsigned grid = (unsigned)((long long)P.B * strips * runs);
+    const size_t smem = (size_t)p1t_smem(S, M, t.p1_R, t.p1_J);
+    if (P.nr == C::BX)
+        k_pass1t<S, M, true><<<grid, 128, smem, s>>>(P, m, out, n, t.p1_R, t.p1_J);
+    else
+        k_pass1t<S, M, false><<<grid, 128, smem, s>>>(P, m, out, n, t.p1_R, t.p1_J);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool pass1t_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
+{
+    if (elem != sizeof(float) || t.p1_stage != 2 || !p1t_compiled(t.p1_S, t.p1_M)) return false;
+    if (nr % kChunk != 0 || t.p1_S * t.p1_M < nr || nv < 4 || ny < 4) return false;
+    if (t.p1_R < 1 || t.p1_R > 8 || t.p1_J < 1 || t.p1_J > 4096) return false;
+    const int KB = 4 * (32 / t.p1_S) * t.p1_R;
+    // the one-sided v stencil of the last line reaches two lines back
+    if (nv % KB != 0 && nv % KB < 3) return false;
+    if (KB + 2 > 256) return false;
+    return p1t_smem(t.p1_S, t.p1_M, t.p1_R, t.p1_J) <= kSmemLimit;
+}
+
+cudaError_t launch_pass1t(const March<float>& P, const float* U, float* out, int n, const Tile& t, cudaStream_t s)
+{
+    if (!pass1t_valid(t, P.nr, P.nv, P.ny, sizeof(float)) || !P.tma_ok) return cudaErrorInvalidValue;
+    if (((reinterpret_cast<uintptr_t>(U) | reinterpret_cast<uintptr_t>(out)) & 15) != 0)
+        return cudaErrorInvalidValue;
+#define P1T_CASE(S_, M_) \
+    if (t.p1_S == S_ && t.p1_M == M_) return p1t_launch<S_, M_>(P, U, out, n, t, s);
+    P1T_SHAPES(P1T_CASE)
+#undef P1T_CASE
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t init_pass1t()
+{
+    cudaError_t e = cudaSuccess;
+#define P1T_ATTR(S_, M_)                                                                                 \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_pass1t<S_, M_, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                 kSmemLimit);                                                            \
+    if (e == cudaSuccess)                                                                                \
+        e = cudaFuncSetAttribute(k_pass1t<S_, M_, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                 kSmemLimit);
+    P1T_SHAPES(P1T_ATTR)
+#undef P1T_ATTR
+    return e;
+}
+
+cudaError_t pass1t_timeouts(unsigned* count, bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_p1t_timeouts, sizeof(unsigned));
+    if (e == cudaSuccess && reset) {
+        const unsigned z = 0;
+        e = cudaMemcpyToSymbol(g_p1t_timeouts, &z, sizeof(unsigned));
+    }
+    return e;
+}
+
+cudaError_t pass1t_test_drop(int plane, unsigned limit)
+{
+    cudaError_t e = cudaMemcpyToSymbol(g_p1t_drop, &plane, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_p1t_limit, &limit, sizeof(unsigned));
+    return e;
+}
+
+}  // namespace hjm

@@ -168,6 +168,17 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         rt[RT_C4B * nr + i] = (T)(-p.kappa * z / J * 0.5 * ihr);
         rt[RT_C3 * nr + i] = (T)(p.lambda * rg * p.eps * p.rho / J * 0.25 * ihr * ihv);
         rt[RT_CY * nr + i] = (T)(lam2 * r2g);
+        // folded tables (R2_L ..): zeros on the Dirichlet nodes, B = 1
+        T* r2 = (T*)g.r2 + (size_t)b * R2_N * nr;
+        const bool dir = i == nr - 1 || (i == 0 && p.gamma == 0.0);
+        const double dt = D.dt, ith = p.theta_adi > 0.0 ? 1.0 / p.theta_adi : 0.0;
+        const double c1 = 0.5 * lam2 * r2g / (J * J) * ihr * ihr;
+        const double c4v = 0.5 * lam2 * r2g * J2 / (J * J * J) * 0.5 * ihr;
+        const double ij = 0.5 * ihr / J, c4b = -p.kappa * z / J * 0.5 * ihr;
+        const double f[R2_N] = {dt * (c1 + c4v), dt * (c1 - c4v), dt * ij, dt * c4b, ith + dt * z, dt * c1,
+                                dt * c4v, dt * c4b * ith, -dt * z * ith,
+                                dt * p.lambda * rg * p.eps * p.rho / J * 0.25 * ihr * ihv, dt * lam2 * r2g};
+        for (int q = 0; q < R2_N; ++q) r2[q * nr + i] = (T)(dir ? (q == R2_B ? 1.0 : 0.0) : f[q]);
     }
     // v axis: A_v = g2 d_vv + g5 d_v, g2 = zeta_vv / J^2,
     // g5 = mu_v / J - zeta_vv J2 / J^3; on the v faces mu_v / J alone.
@@ -208,6 +219,7 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         sc[SC_CX] = (T)(0.5 - c1);
         sc[SC_HE] = (T)he;
         sc[SC_KD] = (T)((1.0 - he) / (1.0 - c1));
+        sc[SC_ITH] = (T)(p.theta_adi > 0.0 ? 1.0 / p.theta_adi : 0.0);
         int* fl = g.fl + (size_t)b * FL_N;
         fl[FL_RLO_DIR] = p.gamma == 0.0;
         fl[FL_YORDER] = p.yorder;
@@ -675,6 +687,7 @@ size_t tables_bytes(int nr, int nv, int ny, int nsteps, int B, size_t elem)
 {
     size_t s = 0;
     s += align_up((size_t)B * RT_N * nr * elem);
+    s += align_up((size_t)B * R2_N * nr * elem);
     s += align_up((size_t)B * VT_N * nv * elem);
     s += align_up((size_t)B * YT_N * ny * elem);
     s += align_up((size_t)B * SC_N * elem);
@@ -701,6 +714,7 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
         return (void*)q;
     };
     g.rt = take(B * RT_N * g.nr * elem);
+    g.r2 = take(B * R2_N * g.nr * elem);
     g.vt = take(B * VT_N * g.nv * elem);
     g.yt = take(B * YT_N * g.ny * elem);
     g.sc = take(B * SC_N * elem);
@@ -770,6 +784,7 @@ March<T> march_args(const GroupTables& g)
     P.B = g.B;
     P.N = (long long)g.nr * g.nv * g.ny;
     P.rt = (const T*)g.rt;
+    P.r2 = (const T*)g.r2;
     P.vt = (const T*)g.vt;
     P.yt = (const T*)g.yt;
     P.sc = (const T*)g.sc;
@@ -783,6 +798,7 @@ March<T> march_args(const GroupTables& g)
     P.yp = (const T*)g.yp;
     P.p2P = g.p2P;
     P.p3P = g.p3P;
+    P.tma_ok = g.tma_ok;
     return P;
 }
 

@@ -125,6 +125,8 @@ def _load():
         "hjm_tile_get": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
         "hjm_tile_set": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
         "hjm_autotune": ([P(hjm_batch_item), C.c_size_t, st, C.c_int, vp], st),
+        "hjm_wait_status": ([st], st),
+        "hjm_test_drop_plane": ([C.c_int, C.c_uint], st),
         "hjm_status_string": ([st], C.c_char_p),
         "hjm_last_error": ([], C.c_char_p),
     }
@@ -142,7 +144,7 @@ EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch
             "hjm_surrogate_get_params", "hjm_surrogate_set_params", "hjm_surrogate_error_table",
             "hjm_surrogate_save", "hjm_surrogate_load", "hjm_surrogate_destroy", "hjm_mlp_gemm",
             "hjm_trace_enable", "hjm_trace_read", "hjm_tile_get", "hjm_tile_set", "hjm_autotune",
-            "hjm_status_string", "hjm_last_error")
+            "hjm_wait_status", "hjm_test_drop_plane", "hjm_status_string", "hjm_last_error")
 
 
 class HJMError(RuntimeError):
@@ -312,6 +314,16 @@ def hjm_autotune(items, precision=HJM_FP32, steps=8, stream=None):
     """Time every candidate launch shape on the items' grid shapes and keep the fastest."""
     arr = items if isinstance(items, C.Array) else make_items(items)
     _check(lib.hjm_autotune(arr, len(arr), PRECISIONS[precision], int(steps), _stream(stream)))
+
+
+def hjm_wait_status(reset=False):
+    """Raises HJMError (HJM_ETIMEOUT) when a bounded device wait gave up."""
+    _check(lib.hjm_wait_status(1 if reset else 0))
+
+
+def hjm_test_drop_plane(plane, polls=0):
+    """Test hook: y plane `plane` is never copied by the TMA-fed pass 1 (-1: off)."""
+    _check(lib.hjm_test_drop_plane(int(plane), int(polls)))
 
 
 def hjm_trace_enable(on):
