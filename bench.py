@@ -212,6 +212,8 @@ def kernel_name(kind, tile, prec="fp32", scheme=0):
     if tile is None:
         return "k_" + kind
     if kind == "pass1":
+        if tile[5] == 2:
+            return "k_pass1t" + (" + k_pass1" if scheme else "")
         if tile[5] == 1:
             return "k_pass1s_r96" if prec == "fp32" and tile[1] <= 8 else "k_pass1s"
         return "k_pass1_r96" if prec == "fp32" and tile[1] == 8 and not scheme else "k_pass1"

@@ -264,10 +264,13 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * with each y plane's strip copied by the Tensor Memory Accelerator (one
  * box copy per plane, FP32, n_r a multiple of 32, v strips of at least 3
  * nodes or a multiple of the strip; shapes (p1_lanes: p1_nodes) (4: 16),
- * (8: 8, 12, 16), (16: 12, 16), (32: 16); lines of r nodes at the Section
+ * (8: 8, 12, 16), (16: 8, 12, 16), (32: 8, 16); lines of r nodes at the Section
  * 5.1 Douglas stage only: the Craig-Sneyd correction stage and groups with
- * gamma > 0 or theta_adi = 0 fall back to the default shape of pass 1). A
- * shape changes speed and the rounding of the line solves, nothing else.
+ * gamma > 0 or theta_adi = 0 fall back to the default shape of pass 1), 3
+ * the same kernel persistent (p1_planes = 0): one CTA per resident slot of
+ * the GPU, each marching an equal share (to one plane) of the group's
+ * (instrument, strip, y plane) units. A shape changes speed and the
+ * rounding of the line solves, nothing else.
  * tile_cfg in hjm_price_info packs p1_lanes | p1_nodes << 8 | p1_lines << 14
  * | p2_warps << 21 | p3_warps << 25 | p1_staged << 29. */
 typedef struct {

@@ -974,23 +974,24 @@ static std::vector<Tile> pass1_candidates(int nr, int nv, int ny, size_t elem, c
             t.p1_S = S;
             t.p1_M = M;
             t.p1_R = 1;
-            t.p1_stage = 2;
-            t.p1_J = 8;
+            t.p1_stage = 3;
+            t.p1_J = 0;
             if (tile_valid(t, nr, nv, ny, elem)) cover2 = std::min(cover2, S * M);
         }
     for (int S : {4, 8, 16, 32})
         for (int M : {8, 12, 16}) {
             if (S * M > std::max(nr + nr / 4, cover2)) continue;
-            for (int R : {1, 2})
-                for (int J : {8, 16, 32}) {
+            for (int R : {1, 2}) {
+                for (int J : {0, 16}) {  // persistent balanced grid, runs of 16 planes
                     Tile t = base;
                     t.p1_S = S;
                     t.p1_M = M;
                     t.p1_R = R;
-                    t.p1_stage = 2;
+                    t.p1_stage = J == 0 ? 3 : 2;
                     t.p1_J = J;
                     if (tile_valid(t, nr, nv, ny, elem)) out.push_back(t);
                 }
+            }
         }
     return out;
 }

@@ -839,7 +839,7 @@ bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
 {
     if (!(split_valid(nv, t.p2_P) || pass23_valid(nr, nv, ny, t.p2_P, elem)) || !split_valid(ny, t.p3_P))
         return false;
-    if (t.p1_stage == 2) return pass1t_valid(t, nr, nv, ny, elem);
+    if (t.p1_stage == 2 || t.p1_stage == 3) return pass1t_valid(t, nr, nv, ny, elem);
     if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
     if (t.p1_stage == 0) return t.p1_J == 0;
     // staged rows are copied in 16-byte pieces
@@ -921,7 +921,7 @@ cudaError_t launch_pass1(const March<T>& P, const T* U, const T* Y, T* out, int 
                          cudaStream_t s)
 {
     if (!tile_valid(t, P.nr, P.nv, P.ny, sizeof(T))) return cudaErrorInvalidValue;
-    if (t.p1_stage == 2) {
+    if (t.p1_stage == 2 || t.p1_stage == 3) {
         // TMA-fed pass 1; the correction stage of the Craig-Sneyd family and
         // groups with gamma > 0 or theta = 0 run the default rows-from-memory
         // shape instead

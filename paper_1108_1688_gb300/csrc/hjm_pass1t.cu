@@ -33,7 +33,10 @@
 // waits a bounded time for its other copies and leaves without writing.
 #include <cuda.h>  // CUtensorMap and the tensor-map encoder's signature
 
+#include <algorithm>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "hjm_kernels.cuh"
 
@@ -45,6 +48,7 @@ constexpr int kChunk = 32;         // nodes per chunk of the tensor view
 constexpr int kChunkPad = 36;      // nodes per chunk in shared memory
 constexpr int kChunkBytes = kChunkPad * 4;
 constexpr unsigned kWaitPolls = 1u << 22;  // polls of a plane's barrier before giving up
+constexpr int kPlaneBatch = 64;    // planes whose scalars are formed at once
 
 template <int S, int M>
 struct Shape1t {
@@ -152,16 +156,16 @@ enum { LK_V = 0, LK_VT = 2, LK_NV = 4, LK_NVT = 6, LK_TV = 8, LK_CS = 10, LK_CD 
 
 namespace {
 
-// Shared-memory bytes of one launch shape: barriers, tables, per-plane and
-// per-line scalars, and the ring.
-__host__ __device__ inline int p1t_smem(int S, int M, int RK, int JC)
+// Shared-memory bytes of one launch shape: barriers, tables, the scalars of
+// kPlaneBatch planes, per-line scalars and the ring.
+__host__ __device__ inline int p1t_smem(int S, int M, int RK)
 {
     const int G = 32 / S, MP = ((M / 4) & 1) ? M : M + 4, KB = 4 * G * RK;
     const int slot = round128((KB + 2) * (S * M / kChunk) * kChunkBytes);
     // 128 bytes of slack to align the layout to 128 bytes (the box copies'
     // destinations) whatever the dynamic shared memory's base alignment
-    return 128 + 128 + round128(R2_N * S * MP * 4) + round128(PJ_N * JC * 4) + round128(LK_N * KB * 4) +
-           kSlots * slot;
+    return 128 + 128 + round128(R2_N * S * MP * 4) + round128(kPlaneBatch * PJ_N * 4) +
+           round128(LK_N * KB * 4) + kSlots * slot;
 }
 
 // One r line on an S-lane segment; lane sl holds the line's nodes
@@ -371,30 +375,60 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
 
 namespace {
 
-// Polls the barrier of plane p (slot (p - jf) & 3, phase parity
-// ((p - jf) >> 2) & 1) at most `limit` times.
-__device__ __forceinline__ bool wait_plane(unsigned bar0, int p, int jf, unsigned limit)
+// Polls the barrier of the copy with sequence number seq (slot seq & 3,
+// phase parity (seq >> 2) & 1) at most `limit` times.
+__device__ __forceinline__ bool wait_slot(unsigned bar0, unsigned seq)
 {
-    const int i = p - jf;
-    const unsigned bar = bar0 + 8u * (unsigned)(i & (kSlots - 1)), par = (unsigned)((i >> 2) & 1);
-    for (unsigned it = 0; it < limit; ++it)
+    const unsigned bar = bar0 + 8u * (seq & (kSlots - 1)), par = (seq >> 2) & 1u;
+    if (mbar_try_wait(bar, par)) return true;  // the usual case: the copy has landed
+    const unsigned limit = g_p1t_limit;
+    for (unsigned it = 1; it < limit; ++it)
         if (mbar_try_wait(bar, par)) return true;
     return false;
 }
 
-// Grid: one CTA per (instrument b, strip of KB = 4 (32/S) RK v lines, run of
-// JC y planes); 4 warps, each segment of S lanes takes lines sg, sg + 4G, ...
-// of the strip for every plane of the run.
 // CTAs per SM the register budget is sized for: lanes of 12 or 16 nodes hold
-// more live rows than 128 registers (four CTAs) allow without spills.
+// more live rows than 128 registers (four CTAs) allow without spills; 8-node
+// lanes fit 96 registers (five CTAs).
 template <int M>
 struct P1tOcc {
-    static constexpr int value = M >= 12 ? 3 : 4;
+    static constexpr int value = M >= 12 ? 3 : 5;
 };
 
+// Per-plane scalars of plane j of instrument b at step n (see PJ_).
+__device__ __forceinline__ void plane_scalars(const March<float>& P, int b, int n, int j, float* o)
+{
+    const int ny = P.ny;
+    const float* sc = P.sc + (size_t)b * SC_N;
+    const float ith = sc[SC_ITH], dth = sc[SC_DT] * ith;
+    const float aF = P.st[((size_t)b * P.nsteps + n) * 2], aI = P.st[((size_t)b * P.nsteps + n) * 2 + 1];
+    const int yord = P.fl[(size_t)b * FL_N + FL_YORDER];
+    const float* yt = P.yt + (size_t)b * YT_N * ny;
+    const float* dir = P.dir + ((size_t)b * P.nsteps + n) * 2 * ny;
+    const float y = yt[YT_Y * ny + j], iJy = yt[YT_IJ * ny + j], ky = yt[YT_KY * ny + j];
+    const bool yin = j > 0 && j < ny - 1;
+    const float yA = yin ? -1.f : (yord == 1 ? (j == 0 ? 2.f : -2.f) : (j == 0 ? 4.f : -4.f));
+    const float yB = yin ? 1.f : (yord == 1 ? 0.f : (j == 0 ? -1.f : 1.f));
+    const float v[6] = {(aF + y) * ith, aI + y, iJy * ith, ky * iJy * dth, yA, yB};
+    for (int q = 0; q < 6; ++q) o[2 * q] = o[2 * q + 1] = v[q];
+    o[PJ_G] = dir[j];
+    o[PJ_G + 1] = dir[ny + j];
+    o[PJ_G + 2] = o[PJ_G + 3] = 0.f;
+}
+
+// Work: the units (instrument b, strip of KB = 4 (32/S) RK v lines, y plane
+// j), ordered b, strip, j. JC > 0: CTA i takes the run of JC planes
+// i mod runs of strip (i / runs) mod strips of instrument i / (strips runs).
+// JC = 0 (persistent): the grid is one CTA per resident slot and CTA i takes
+// units [T i / grid, T (i + 1) / grid) of the T = B strips n_y units, i.e.
+// an equal share (to one plane) marched as runs of constant (b, strip).
+// A CTA marches a run along y with the 4-slot ring; its 4 warps' segments
+// take lines sg, sg + 4G, ... of the strip for every plane.
 template <int S, int M, bool EXACT>
-__global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<float> P, const __grid_constant__ CUtensorMap tm,
-                                                   float* __restrict__ out, const int n, const int RK, const int JC)
+__global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<float> P,
+                                                                   const __grid_constant__ CUtensorMap tm,
+                                                                   float* __restrict__ out, const int n,
+                                                                   const int RK, const int JC)
 {
     using C = Shape1t<S, M>;
     constexpr int G = C::G, MP = C::MP, Q = M / 4;
@@ -404,147 +438,160 @@ __global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<fl
     const int seg = lane / S, sl = lane % S, sg = warp * G + seg;
     const int nr = P.nr, nv = P.nv, ny = P.ny;
     const int KB = 4 * G * RK;
-    const int strips = (nv + KB - 1) / KB, runs = (ny + JC - 1) / JC;
-    const int b = blockIdx.x / (strips * runs);
-    const int st = (blockIdx.x / runs) % strips, rn = blockIdx.x % runs;
-    const int k0 = st * KB, k1 = min(k0 + KB, nv);
-    const int j0 = rn * JC, j1 = min(j0 + JC, ny);
-    // Planes in the ring: from the y-1 neighbour of j0 (two planes further
-    // back for a run that ends on the y_max face, whose one-sided stencil
-    // reaches plane n_y - 3) to the y+1 neighbour of the run's last plane
-    // (at least plane 2 for a run starting on the y = 0 face).
-    const int jf = max(0, min(j0 - 1, ny - 3));
-    const int jl = min(max(j1, j0 == 0 ? 2 : 0), ny - 1);
+    const int strips = (nv + KB - 1) / KB;
 
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(sm);
     int* abort_flag = reinterpret_cast<int*>(sm + 64);
     float* tsm = reinterpret_cast<float*>(sm + 128);
     float* pjs = tsm + round128(R2_N * S * MP * 4) / 4;
-    float* lks = pjs + round128(PJ_N * JC * 4) / 4;
+    float* lks = pjs + round128(kPlaneBatch * PJ_N * 4) / 4;
     unsigned char* ring = reinterpret_cast<unsigned char*>(lks) + round128(LK_N * KB * 4);
     const int slotB = round128((KB + 2) * C::RSB);
     const unsigned bar0 = su32(bar), ring0 = su32(ring);
     const unsigned boxB = (unsigned)((KB + 2) * C::RSB);
 
+    // unit indices fit 32 bits (checked by the launcher)
+    int u, uend;
+    if (JC > 0) {
+        const int runs = (ny + JC - 1) / JC;
+        const int b = blockIdx.x / (strips * runs), st = (blockIdx.x / runs) % strips, rn = blockIdx.x % runs;
+        u = (b * strips + st) * ny + rn * JC;
+        uend = u + min(JC, ny - rn * JC);
+    } else {
+        const long long T = (long long)P.B * strips * ny;
+        u = (int)(T * blockIdx.x / gridDim.x);
+        uend = (int)(T * (blockIdx.x + 1) / gridDim.x);
+    }
     if (tid == 0) {
         for (int i = 0; i < kSlots; ++i) mbar_init(bar0 + 8u * i, 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
-    // folded r tables (nodes past n_r: zeros, B = 1, i.e. identity rows)
-    const float* __restrict__ r2 = P.r2 + (size_t)b * R2_N * nr;
-    for (int idx = tid; idx < R2_N * C::BX; idx += blockDim.x) {
-        const int t = idx / C::BX, e = idx % C::BX;
-        tsm[(t * S + e / M) * MP + e % M] = e < nr ? r2[t * nr + e] : (t == R2_B ? 1.0f : 0.0f);
-    }
-    const float* sc = P.sc + (size_t)b * SC_N;
-    const float dt = sc[SC_DT], ith = sc[SC_ITH], dth = dt * ith;
-    // per-plane scalars of the run
-    {
-        const float aF = P.st[((size_t)b * P.nsteps + n) * 2], aI = P.st[((size_t)b * P.nsteps + n) * 2 + 1];
-        const int yord = P.fl[(size_t)b * FL_N + FL_YORDER];
-        const float* yt = P.yt + (size_t)b * YT_N * ny;
-        const float* dir = P.dir + ((size_t)b * P.nsteps + n) * 2 * ny;
-        for (int jj = tid; jj < j1 - j0; jj += blockDim.x) {
-            const int j = j0 + jj;
-            const float y = yt[YT_Y * ny + j], iJy = yt[YT_IJ * ny + j], ky = yt[YT_KY * ny + j];
-            const bool yin = j > 0 && j < ny - 1;
-            const float yA = yin ? -1.f : (yord == 1 ? (j == 0 ? 2.f : -2.f) : (j == 0 ? 4.f : -4.f));
-            const float yB = yin ? 1.f : (yord == 1 ? 0.f : (j == 0 ? -1.f : 1.f));
-            const float v[6] = {(aF + y) * ith, aI + y, iJy * ith, ky * iJy * dth, yA, yB};
-            float* o = pjs + jj * PJ_N;
-            for (int q = 0; q < 6; ++q) o[2 * q] = o[2 * q + 1] = v[q];
-            o[PJ_G] = dir[j];
-            o[PJ_G + 1] = dir[ny + j];
-            o[PJ_G + 2] = o[PJ_G + 3] = 0.f;
-        }
-    }
-    // per-line scalars of the strip
-    {
-        const float* vt = P.vt + (size_t)b * VT_N * nv;
-        for (int li = tid; li < KB; li += blockDim.x) {
-            const int k = min(k0 + li, k1 - 1);
-            const float v = vt[VT_V * nv + k], g2 = vt[VT_G2 * nv + k], g5 = vt[VT_G5 * nv + k];
-            const float fv = vt[VT_FV * nv + k];
-            const bool vin = k > 0 && k < nv - 1;
-            const float vq = vin ? v * vt[VT_IJ * nv + k] : 0.f;
-            const float cA = vin ? g2 - g5 : (k == 0 ? 4.f * fv : -4.f * fv);
-            const float cB = vin ? g2 + g5 : (k == 0 ? -fv : fv);
-            const float w[8] = {v, v * ith, -v, -v * ith, 2.f * v, 0.5f * (cA + cB) * dth, 0.5f * (cB - cA) * dth,
-                                vq * ith};
-            float* o = lks + li * LK_N;
-            for (int q = 0; q < 8; ++q) o[2 * q] = o[2 * q + 1] = w[q];
-        }
-    }
-    // the lane's 4-node vectors within a staged row (32-node chunks padded to 36)
-    int vo[Q];
+    int vo[Q];  // the lane's 4-node vectors within a staged row (32-node chunks padded to 36)
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int e = sl * M + 4 * q;
         vo[q] = (e >> 5) * kChunkBytes + (e & 31) * 4;
     }
-    __syncthreads();  // barriers initialised, tables and scalars in place
-
-    const int drop = g_p1t_drop;
-    const unsigned limit = g_p1t_limit;
-    int last = jf - 1;  // last plane copied (thread 0)
-    auto issue = [&](int p) {
-        last = p;
-        if (p == drop) return;  // test hook: the copy never starts, its waits run out
-        const int i = p - jf, s = i & (kSlots - 1);
-        mbar_expect_tx(bar0 + 8u * s, boxB);
-        tma_box(ring0 + (unsigned)(s * slotB), &tm, 0, k0 - 1, b * ny + p, bar0 + 8u * s);
-    };
-    if (tid == 0)
-        for (int p = jf; p <= min(j0 + 1, jl); ++p) issue(p);
-
     const float* tl = tsm + sl * MP;
-    for (int j = j0; j < j1; ++j) {
-        __syncthreads();  // every thread is done with plane j-2's slot
-        if (*abort_flag) break;
-        if (tid == 0 && j + 2 <= jl) issue(j + 2);  // into the slot of plane j-2
-        const bool yin = j > 0 && j < ny - 1;
-        const int ja = yin ? j - 1 : (j == 0 ? 1 : ny - 2), jb = yin ? j + 1 : (j == 0 ? 2 : ny - 3);
-        if (!(wait_plane(bar0, j, jf, limit) && wait_plane(bar0, ja, jf, limit) &&
-              wait_plane(bar0, jb, jf, limit))) {
-            atomicExch(abort_flag, 1);
-            continue;
-        }
-        const unsigned char* pc = ring + ((j - jf) & (kSlots - 1)) * slotB;
-        const unsigned char* pa = ring + ((ja - jf) & (kSlots - 1)) * slotB;
-        const unsigned char* pb = ring + ((jb - jf) & (kSlots - 1)) * slotB;
-        const float* pjj = pjs + (j - j0) * PJ_N;
-        for (int r = 0; r < RK; ++r) {
-            const int li = sg + 4 * G * r;
-            const bool valid = k0 + li < k1;
-            const int k = valid ? k0 + li : k1 - 1;  // segment-uniform; invalid lines are not stored
-            const bool vin = k > 0 && k < nv - 1;
-            const int ka = vin ? k - 1 : (k == 0 ? 1 : nv - 2), kb = vin ? k + 1 : (k == 0 ? 2 : nv - 3);
-            const int rowc = (k - k0 + 1) * C::RSB;
-            float xr[M];
-            if (yin)
-                p1t_line<S, M, EXACT, true>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB, pc + (kb - k0 + 1) * C::RSB,
-                                            pa + rowc, pb + rowc, vo, lks + (k - k0) * LK_N, pjj, sl, nr, xr);
-            else
-                p1t_line<S, M, EXACT, false>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB,
-                                             pc + (kb - k0 + 1) * C::RSB, pa + rowc, pb + rowc, vo,
-                                             lks + (k - k0) * LK_N, pjj, sl, nr, xr);
-            if (valid) {
-                float* o = out + ((size_t)(b * ny + j) * nv + k) * nr + sl * M;
-#pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    if (EXACT || sl * M + 4 * q + 4 <= nr)
-                        reinterpret_cast<float4*>(o)[q] =
-                            make_float4(xr[4 * q], xr[4 * q + 1], xr[4 * q + 2], xr[4 * q + 3]);
+    unsigned seq = 0;    // sequence number of the CTA's next plane copy (slot seq & 3)
+    int cur_b = -1, cur_st = -1;
+    int jf = 0, last = -1;  // the current run's first plane and last plane copied (thread 0)
+    unsigned seq_run = 0;   // sequence number of the current run's first copy
+
+    while (u < uend) {
+        const int b = u / (strips * ny), rem = u % (strips * ny);
+        const int st = rem / ny, j0 = rem % ny;
+        const int j1 = min(ny, j0 + (uend - u));
+        const int k0 = st * KB, k1 = min(k0 + KB, nv);
+        // Planes in the ring: from the y-1 neighbour of j0 (two planes further
+        // back for a run that ends on the y_max face, whose one-sided stencil
+        // reaches plane n_y - 3) to the y+1 neighbour of the run's last plane
+        // (at least plane 2 for a run starting on the y = 0 face).
+        jf = max(0, min(j0 - 1, ny - 3));
+        const int jl = min(max(j1, j0 == 0 ? 2 : 0), ny - 1);
+        __syncthreads();  // the previous run is done with tables, scalars and slots
+        if (b != cur_b) {
+            // folded r tables (nodes past n_r: zeros, B = 1, i.e. identity rows)
+            const float* __restrict__ r2 = P.r2 + (size_t)b * R2_N * nr;
+            for (int idx = tid; idx < R2_N * C::BX; idx += blockDim.x) {
+                const int t = idx / C::BX, e = idx % C::BX;
+                tsm[(t * S + e / M) * MP + e % M] = e < nr ? r2[t * nr + e] : (t == R2_B ? 1.0f : 0.0f);
             }
         }
+        if (b != cur_b || st != cur_st) {
+            const float* sc = P.sc + (size_t)b * SC_N;
+            const float ith = sc[SC_ITH], dth = sc[SC_DT] * ith;
+            const float* vt = P.vt + (size_t)b * VT_N * nv;
+            for (int li = tid; li < KB; li += blockDim.x) {
+                const int k = min(k0 + li, k1 - 1);
+                const float v = vt[VT_V * nv + k], g2 = vt[VT_G2 * nv + k], g5 = vt[VT_G5 * nv + k];
+                const float fv = vt[VT_FV * nv + k];
+                const bool vin = k > 0 && k < nv - 1;
+                const float vq = vin ? v * vt[VT_IJ * nv + k] : 0.f;
+                const float cA = vin ? g2 - g5 : (k == 0 ? 4.f * fv : -4.f * fv);
+                const float cB = vin ? g2 + g5 : (k == 0 ? -fv : fv);
+                const float w[8] = {v, v * ith, -v, -v * ith, 2.f * v, 0.5f * (cA + cB) * dth,
+                                    0.5f * (cB - cA) * dth, vq * ith};
+                float* o = lks + li * LK_N;
+                for (int q = 0; q < 8; ++q) o[2 * q] = o[2 * q + 1] = w[q];
+            }
+        }
+        cur_b = b;
+        cur_st = st;
+        for (int jj = tid; jj < min(j1 - j0, kPlaneBatch); jj += blockDim.x)
+            plane_scalars(P, b, n, j0 + jj, pjs + jj * PJ_N);
+        __syncthreads();  // tables and scalars in place
+
+        seq_run = seq;
+        auto issue = [&](int p) {
+            last = p;
+            if (p == g_p1t_drop) return;  // test hook: the copy never starts, its waits run out
+            const unsigned sq = seq_run + (unsigned)(p - jf), s = sq & (kSlots - 1);
+            mbar_expect_tx(bar0 + 8u * s, boxB);
+            tma_box(ring0 + s * (unsigned)slotB, &tm, 0, k0 - 1, b * ny + p, bar0 + 8u * s);
+        };
+        if (tid == 0)
+            for (int p = jf; p <= min(j0 + 1, jl); ++p) issue(p);
+
+        for (int j = j0; j < j1; ++j) {
+            __syncthreads();  // every thread is done with plane j-2's slot
+            if (*abort_flag) break;
+            if (tid == 0 && j + 2 <= jl) issue(j + 2);  // into the slot of plane j-2
+            if (j > j0 && (j - j0) % kPlaneBatch == 0) {  // the next batch of plane scalars
+                for (int jj = tid; jj < min(j1 - j, kPlaneBatch); jj += blockDim.x)
+                    plane_scalars(P, b, n, j + jj, pjs + jj * PJ_N);
+                __syncthreads();
+            }
+            const bool yin = j > 0 && j < ny - 1;
+            const int ja = yin ? j - 1 : (j == 0 ? 1 : ny - 2), jb = yin ? j + 1 : (j == 0 ? 2 : ny - 3);
+            const unsigned sc_ = seq_run + (unsigned)(j - jf), sa = seq_run + (unsigned)(ja - jf),
+                           sb = seq_run + (unsigned)(jb - jf);
+            if (!(wait_slot(bar0, sc_) && wait_slot(bar0, sa) && wait_slot(bar0, sb))) {
+                atomicExch(abort_flag, 1);
+                continue;
+            }
+            const unsigned char* pc = ring + (sc_ & (kSlots - 1)) * slotB;
+            const unsigned char* pa = ring + (sa & (kSlots - 1)) * slotB;
+            const unsigned char* pb = ring + (sb & (kSlots - 1)) * slotB;
+            const float* pjj = pjs + ((j - j0) % kPlaneBatch) * PJ_N;
+            for (int r = 0; r < RK; ++r) {
+                const int li = sg + 4 * G * r;
+                const bool valid = k0 + li < k1;
+                const int k = valid ? k0 + li : k1 - 1;  // segment-uniform; invalid lines are not stored
+                const bool vin = k > 0 && k < nv - 1;
+                const int ka = vin ? k - 1 : (k == 0 ? 1 : nv - 2), kb = vin ? k + 1 : (k == 0 ? 2 : nv - 3);
+                const int rowc = (k - k0 + 1) * C::RSB;
+                float xr[M];
+                if (yin)
+                    p1t_line<S, M, EXACT, true>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB,
+                                                pc + (kb - k0 + 1) * C::RSB, pa + rowc, pb + rowc, vo,
+                                                lks + (k - k0) * LK_N, pjj, sl, nr, xr);
+                else
+                    p1t_line<S, M, EXACT, false>(tl, pc + rowc, pc + (ka - k0 + 1) * C::RSB,
+                                                 pc + (kb - k0 + 1) * C::RSB, pa + rowc, pb + rowc, vo,
+                                                 lks + (k - k0) * LK_N, pjj, sl, nr, xr);
+                if (valid) {
+                    float* o = out + ((size_t)(b * ny + j) * nv + k) * nr + sl * M;
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        if (EXACT || sl * M + 4 * q + 4 <= nr)
+                            reinterpret_cast<float4*>(o)[q] =
+                                make_float4(xr[4 * q], xr[4 * q + 1], xr[4 * q + 2], xr[4 * q + 3]);
+                }
+            }
+        }
+        __syncthreads();
+        if (*abort_flag) break;
+        seq += (unsigned)(jl - jf + 1);
+        u += j1 - j0;
     }
-    __syncthreads();  // every thread has left the loop (a late timeout is seen below)
+    __syncthreads();  // every thread has left the loops (a late timeout is seen below)
     if (tid == 0 && *abort_flag) {
         // leave no copy in flight into this CTA's shared memory: wait (bounded)
-        // for the last planes copied, one per slot
+        // for the current run's last planes copied, one per slot
         for (int p = max(jf, last - kSlots + 1); p <= last; ++p)
-            if (p != drop) wait_plane(bar0, p, jf, limit);
+            if (p != g_p1t_drop) wait_slot(bar0, seq_run + (unsigned)(p - jf));
         atomicAdd(&g_p1t_timeouts, 1u);
     }
     __syncthreads();
@@ -596,7 +643,7 @@ cudaError_t field_map(CUtensorMap* m, const float* U, int nr, int nv, long long 
 constexpr int kSmemLimit = 227 * 1024;
 
 // (S, M) shapes compiled: n_r up to 64, 96, 128, 192, 256 and 512.
-#define P1T_SHAPES(X) X(4, 16) X(8, 8) X(8, 12) X(8, 16) X(16, 12) X(16, 16) X(32, 16)
+#define P1T_SHAPES(X) X(4, 16) X(8, 8) X(8, 12) X(8, 16) X(16, 8) X(16, 12) X(16, 16) X(32, 8) X(32, 16)
 
 bool p1t_compiled(int S, int M)
 {
@@ -604,6 +651,31 @@ bool p1t_compiled(int S, int M)
     P1T_SHAPES(P1T_IS)
 #undef P1T_IS
     return false;
+}
+
+// Resident CTAs of a kernel at this shared-memory size times the SM count
+// of the current device (the persistent grid), cached per kernel.
+template <typename K>
+int resident_ctas(K kernel, size_t smem)
+{
+    static std::mutex mu;
+    static int dev_cached = -1, sms = 0;
+    static std::vector<std::pair<std::pair<const void*, size_t>, int>> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev != dev_cached) {
+        cache.clear();
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        dev_cached = dev;
+    }
+    const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), smem);
+    for (const auto& c : cache)
+        if (c.first == key) return c.second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, 128, smem) != cudaSuccess) return 0;
+    cache.emplace_back(key, nb * sms);
+    return nb * sms;
 }
 
 template <int S, int M>
@@ -614,13 +686,22 @@ cudaError_t p1t_launch(const March<float>& P, const float* U, float* out, int n,
     CUtensorMap m;
     cudaError_t e = field_map(&m, U, P.nr, P.nv, (long long)P.B * P.ny, C::NCH, KB + 2);
     if (e != cudaSuccess) return e;
-    const int strips = (P.nv + KB - 1) / KB, runs = (P.ny + t.p1_J - 1) / t.p1_J;
-    const unsigned grid = (unsigned)((long long)P.B * strips * runs);
-    const size_t smem = (size_t)p1t_smem(S, M, t.p1_R, t.p1_J);
-    if (P.nr == C::BX)
-        k_pass1t<S, M, true><<<grid, 128, smem, s>>>(P, m, out, n, t.p1_R, t.p1_J);
-    else
-        k_pass1t<S, M, false><<<grid, 128, smem, s>>>(P, m, out, n, t.p1_R, t.p1_J);
+    const int strips = (P.nv + KB - 1) / KB;
+    const size_t smem = (size_t)p1t_smem(S, M, t.p1_R);
+    const bool exact = P.nr == C::BX;
+    auto kern = exact ? k_pass1t<S, M, true> : k_pass1t<S, M, false>;
+    long long grid;
+    int JC = t.p1_J;
+    const long long units = (long long)P.B * strips * P.ny;
+    if (units >= (1ll << 31)) return cudaErrorInvalidValue;
+    if (t.p1_stage == 3) {  // persistent: one CTA per resident slot, an equal share of the units each
+        grid = std::min<long long>(units, resident_ctas(kern, smem));
+        JC = 0;
+        if (grid < 1) return cudaErrorInvalidConfiguration;
+    } else {
+        grid = (long long)P.B * strips * ((P.ny + JC - 1) / JC);
+    }
+    kern<<<(unsigned)grid, 128, smem, s>>>(P, m, out, n, t.p1_R, JC);
     return cudaGetLastError();
 }
 
@@ -628,14 +709,17 @@ cudaError_t p1t_launch(const March<float>& P, const float* U, float* out, int n,
 
 bool pass1t_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
 {
-    if (elem != sizeof(float) || t.p1_stage != 2 || !p1t_compiled(t.p1_S, t.p1_M)) return false;
+    if (elem != sizeof(float) || (t.p1_stage != 2 && t.p1_stage != 3) || !p1t_compiled(t.p1_S, t.p1_M))
+        return false;
     if (nr % kChunk != 0 || t.p1_S * t.p1_M < nr || nv < 4 || ny < 4) return false;
-    if (t.p1_R < 1 || t.p1_R > 8 || t.p1_J < 1 || t.p1_J > 4096) return false;
+    if (t.p1_R < 1 || t.p1_R > 8) return false;
+    // stage 2: runs of p1_J planes; stage 3: persistent, p1_J = 0
+    if (t.p1_stage == 2 ? (t.p1_J < 1 || t.p1_J > 4096) : t.p1_J != 0) return false;
     const int KB = 4 * (32 / t.p1_S) * t.p1_R;
     // the one-sided v stencil of the last line reaches two lines back
     if (nv % KB != 0 && nv % KB < 3) return false;
     if (KB + 2 > 256) return false;
-    return p1t_smem(t.p1_S, t.p1_M, t.p1_R, t.p1_J) <= kSmemLimit;
+    return p1t_smem(t.p1_S, t.p1_M, t.p1_R) <= kSmemLimit;
 }
 
 cudaError_t launch_pass1t(const March<float>& P, const float* U, float* out, int n, const Tile& t, cudaStream_t s)

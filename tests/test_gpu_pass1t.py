@@ -1,8 +1,9 @@
-"""The TMA-fed pass 1 (launch shapes with p1_staged = 2) against the CPU FP64
-oracle: one Douglas pass 1 (Section 5.1: dt F(U^n) with the r-v mixed term,
+"""The TMA-fed pass 1 (launch shapes with p1_staged = 2, and 3 persistent)
+against the CPU FP64 oracle: one Douglas pass 1 (Section 5.1: dt F(U^n) with the r-v mixed term,
 then the r-line solve) for every compiled (lanes, nodes) shape, strips of one
 or two lines per segment, runs of 1, 3 and 8 y planes (so runs start and end
-on both y faces, and a run may hold the last plane alone), v strips that
+on both y faces, and a run may hold the last plane alone) and the persistent
+grid's balanced shares (runs that cross strips and instruments), v strips that
 leave a ragged last strip, first- and second-order y faces, Nelson-Siegel
 drift (a(t) at t^n and t^{n+1/2} differ) and flat curves; whole marches of
 FP32 prices; the shapes the kernel does not cover falling back to the
@@ -18,7 +19,7 @@ from paper_1108_1688_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(4, 16), (8, 8), (8, 12), (8, 16), (16, 12), (16, 16), (32, 16)]
+SHAPES = [(4, 16), (8, 8), (8, 12), (8, 16), (16, 8), (16, 12), (16, 16), (32, 8), (32, 16)]
 
 
 @pytest.fixture(scope="module")
@@ -61,6 +62,7 @@ def tma_tiles(nr, nv):
                 continue
             for J in (1, 3, 8):
                 out.append((S, M, R, 1, 1, 2, J))
+            out.append((S, M, R, 1, 1, 3, 0))  # persistent, balanced shares
     return out
 
 
@@ -141,12 +143,13 @@ def test_tma_shapes_are_validated(H):
         H.hjm_tile_set(128, 64, 64, "fp32", (12, 16, 1, 1, 1, 2, 8))  # 12 lanes: not compiled
 
 
-def test_bounded_wait_runs_out_and_reports(H):
+@pytest.mark.parametrize("tile", [(8, 8, 1, 1, 1, 2, 3), (8, 8, 1, 1, 1, 3, 0)])
+def test_bounded_wait_runs_out_and_reports(H, tile):
     # A plane copy that is never started: every CTA whose run needs plane 2
     # gives up after a short bounded wait, leaves without writing, and the
     # host reads HJM_ETIMEOUT; afterwards the device prices normally again.
-    items = [_caplet(64, 10, 16, 6, seed=8)]
-    H.hjm_tile_set(64, 16, 10, "fp32", (8, 8, 1, 1, 1, 2, 3))
+    items = [_caplet(64, 10, 16, 6, seed=8), _caplet(64, 10, 16, 6, seed=9)]
+    H.hjm_tile_set(64, 16, 10, "fp32", tile)
     try:
         ref = H.hjm_price_batch(items, "fp32")[0]
         H.hjm_wait_status(reset=True)
@@ -158,7 +161,7 @@ def test_bounded_wait_runs_out_and_reports(H):
         H.hjm_test_drop_plane(-1, 0)
         H.hjm_tile_set(64, 16, 10, "fp32", None)
     H.hjm_wait_status(reset=True)
-    H.hjm_tile_set(64, 16, 10, "fp32", (8, 8, 1, 1, 1, 2, 3))
+    H.hjm_tile_set(64, 16, 10, "fp32", tile)
     try:
         again = H.hjm_price_batch(items, "fp32")[0]
     finally:
