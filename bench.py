@@ -1,27 +1,34 @@
 """Benchmark of the GPU Douglas ADI pricing path.
 
-Workload (default, --workload config2): 100 seeded 5y-into-6m ATM caplets on a
-128 (rate) x 64 (accumulated variance) x 64 (volatility) grid with 400 Douglas
-steps, Nelson-Siegel curves and (epsilon, rho) drawn as in the paper-shaped
-config (seed 1108002), FP32 march with FP64 set-up and read-out. One step of
-this benchmark = one hjm_price_batch call over all 100 caplets (set-up,
-terminal field, 400 steps x 3 kernel passes, read-out): 2.097e10 grid-point-
-steps. The state (100 x 2 MiB x 2 fields = 420 MB) is larger than L2, so no
-flush is needed between steps.
+Default workload (--workload headline): the 256-caplet batch (seed 1108003):
+expiries U{1..10}y into 6m, strikes ATM +/- 200 bp, each caplet with its own
+Nelson-Siegel curve and (epsilon, rho), on uneven grids n_r x n_r/2 x n_r/2
+with n_r in {64, 96, ..., 256} and 2 n_r Douglas steps, FP32 march with FP64
+set-up and read-out. One step of this benchmark = one hjm_price_batch call
+over all 256 caplets (every shape group's set-up, terminal field, march and
+read-out; the groups run as branches of one CUDA graph). Measured the same way
+beside it, under "secondary": the 100-caplet batch of 5y-into-6m ATM caplets
+on 128 x 64 x 64 with 400 steps (seed 1108002) and the bandwidth-stress
+caplet, 10y-into-6m ATM on 512 x 256 x 256 with 1000 steps. Every working set
+is larger than L2 (no flush needed between steps).
 
 Metric: grid-point-steps/s (caplets/s reported beside it). `value` is timed
 with CUDA events on the launching stream with the outputs in device memory
-(the 100 parameter structs, 25 KB, are uploaded inside each call); `e2e` is
-the same call with host outputs, wall-clocked. Under torchrun every rank runs
-its own replica of the batch on its own GPU (weak scaling); value = all
-ranks' grid-point-steps / the slowest rank's time.
+(the parameter structs are uploaded inside each call); `e2e` is the same call
+with host outputs, wall-clocked. `roofline` is the dominant kernel's
+algorithmic bytes (the pass's words per grid-point-step x the call's
+grid-point-steps) over its device time per call (trace mode); `step_hbm` the
+same for the whole step (7 words per grid-point-step). Under torchrun every
+rank runs its own replica of the batch on its own GPU (weak scaling); value =
+all ranks' grid-point-steps / the slowest rank's time.
 
 --precision fp64 marches in FP64; --precision mixed marches in FP32 and
 re-prices in FP64 the instruments whose rounding bound misses 1e-4 (the
 count is reported in config.mixed).
 
---impl reference times the CPU FP64 oracle (the plain serial C reference
-written from the paper) on a bounded sample of the same workload.
+cpu_baseline and --impl reference time the CPU FP64 oracle (the plain C
+reference written from the paper; its OpenMP build shares the lines of each
+pass among all host cores) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -70,6 +77,8 @@ def workload_items(name, instruments=None, march_steps=None, scheme="douglas"):
 
 def _workload_items(name, instruments=None, march_steps=None):
     from paper_1108_1688_gb300 import workloads as W
+    if name == "headline":
+        name = "config3"
     if name == "config2":
         n = instruments or 100
         ns = march_steps or 400
@@ -184,7 +193,7 @@ def barrier(world):
 
 # ---------------------------------------------------------------- helpers
 
-MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu")
+MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu", "hjm_pass1t.cu")
 
 
 def source_digest():
@@ -267,14 +276,13 @@ def recorded_traffic(kernel, workload, points_per_launch, tile=None):
     return rec["dram_bytes_per_point"] * points_per_launch
 
 
-def cpu_baseline(items, budget_s=12.0, max_steps=200):
-    """The oracle, as it stands, on a bounded sample: the set-up and the first
-    Douglas steps of the first instrument of the workload, serial."""
+def _oracle_rate(it, omp, budget_s, max_steps):
+    """Grid-point-steps/s of the oracle on the set-up and the first Douglas
+    steps of one instrument, within a time budget."""
     import oracle
-    it = items[0]
     g = it["grid"]
     pts = g["n_r"] * g["n_v"] * g["n_y"]
-    with oracle.Ctx(it) as X:
+    with oracle.Ctx(it, omp=omp) as X:
         t0 = time.perf_counter()
         U = X.terminal()
         n = 0
@@ -282,10 +290,24 @@ def cpu_baseline(items, budget_s=12.0, max_steps=200):
             U = X.step(n, U)
             n += 1
         dt = time.perf_counter() - t0
-    return {"value": n * pts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "instrument 0 of the workload: set-up and the first %d of %d ADI steps "
-                      "on %dx%dx%d (serial FP64 C oracle)" % (n, g["n_steps"], g["n_r"], g["n_y"], g["n_v"]),
-            "seconds": dt}
+    return n * pts / dt, n, dt
+
+
+def cpu_baseline(items, budget_s=12.0, max_steps=200):
+    """The oracle, as it stands, on a bounded sample of the workload (the
+    set-up and the first Douglas steps of its first instrument): the OpenMP
+    build on every host core (the reported value) and the serial build."""
+    it = items[0]
+    g = it["grid"]
+    cores = os.cpu_count() or 1
+    v_omp, n_omp, s_omp = _oracle_rate(it, True, budget_s, max_steps)
+    v_ser, n_ser, s_ser = _oracle_rate(it, False, budget_s, max_steps)
+    return {"value": v_omp, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "instrument 0 of the workload: set-up and the first %d of %d ADI steps on %dx%dx%d "
+                      "(FP64 C oracle, OpenMP over the lines of each pass, %d threads)"
+                      % (n_omp, g["n_steps"], g["n_r"], g["n_y"], g["n_v"], cores),
+            "seconds": s_omp,
+            "serial": {"value": v_ser, "cores": 1, "steps": n_ser, "seconds": s_ser}}
 
 
 # ------------------------------------------------------------------- arms
@@ -295,13 +317,14 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    oracle.build()
+    oracle.build(omp=True)
     items, desc = workload_items(args.workload, args.instruments, args.march_steps, args.scheme)
     it = items[0]
     g = it["grid"]
     pts = g["n_r"] * g["n_v"] * g["n_y"]
     per_step = max(1, args.ref_steps_per_step)
-    with oracle.Ctx(it) as X:
+    cores = os.cpu_count() or 1
+    with oracle.Ctx(it, omp=True) as X:
         U = X.terminal()
         n = 0
         for _ in range(args.warmup):
@@ -321,9 +344,10 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": desc, "sample": "%d ADI step(s) of instrument 0 per step" % per_step},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "%d ADI step(s) of instrument 0 (%dx%dx%d) per step, serial FP64 C"
-                                   % (per_step, g["n_r"], g["n_y"], g["n_v"])},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d ADI step(s) of instrument 0 (%dx%dx%d) per step, FP64 C, OpenMP over "
+                                   "the lines of each pass, %d threads" % (per_step, g["n_r"], g["n_y"], g["n_v"],
+                                                                          cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -425,19 +449,38 @@ def run_surrogate(args):
     print(json.dumps(line))
 
 
-def run_ours(args):
+def _tiles_for_workload(hjm, items, prec, arr, stream, args):
+    """Launch shapes: fixed (--tile), from a file (--tiles), or picked by the
+    library's autotuner on the workload's grid shapes (untimed)."""
+    if args.tile:
+        t = [int(v) for v in args.tile.split(",")]
+        for x in items:
+            g = x["grid"]
+            hjm.hjm_tile_set(g["n_r"], g["n_v"], g["n_y"], prec, t)
+    elif args.tiles and os.path.exists(args.tiles):
+        for key, t in json.load(open(args.tiles)).items():
+            nr_, ny_, nv_ = (int(v) for v in key.split("x"))
+            hjm.hjm_tile_set(nr_, nv_, ny_, prec, t)
+    elif not args.no_autotune:
+        hjm.hjm_autotune(arr, prec, steps=8, stream=stream)
+    tiles = {}
+    for x in items:
+        g = x["grid"]
+        key = "%dx%dx%d" % (g["n_r"], g["n_y"], g["n_v"])
+        tiles[key] = list(hjm.hjm_tile_get(g["n_r"], g["n_v"], g["n_y"], prec))
+    if args.tiles and not os.path.exists(args.tiles):
+        json.dump(tiles, open(args.tiles, "w"))
+    return tiles
+
+
+def measure(wname, args, world, local, hjm):
+    """One workload: autotune (untimed), W warm-up calls, K device-timed
+    hjm_price_batch calls (value), K end-to-end calls with host outputs (e2e),
+    a few traced calls for the per-kernel roofline. Returns the JSON line."""
     import numpy as np
     import torch
 
-    world, rank, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    from paper_1108_1688_gb300 import _build
-    if rank == 0 or world == 1:
-        _build.build()
-    barrier(world)
-    from paper_1108_1688_gb300 import hjm
-
-    items, desc = workload_items(args.workload, args.instruments, args.march_steps, args.scheme)
+    items, desc = workload_items(wname, args.instruments, args.march_steps, args.scheme)
     scheme = SCHEMES[args.scheme][0]
     prec = args.precision
     # MIXED marches with the FP32 kernels and launch shapes, re-running in
@@ -455,28 +498,7 @@ def run_ours(args):
     def step_dev():
         hjm.hjm_price_batch(arr, prec, out=out, stream=stream)
 
-    # Launch shapes: the library's autotuner times the candidate shapes of
-    # every grid shape of the workload once (untimed, before the warm-up).
-    tiles = {}
-    if args.tile:
-        t = [int(v) for v in args.tile.split(",")]
-        for x in items:
-            g = x["grid"]
-            hjm.hjm_tile_set(g["n_r"], g["n_v"], g["n_y"], prec, t)
-    elif args.tiles and os.path.exists(args.tiles):
-        # launch shapes saved by an earlier run of the same workload
-        for key, t in json.load(open(args.tiles)).items():
-            nr_, ny_, nv_ = (int(v) for v in key.split("x"))
-            hjm.hjm_tile_set(nr_, nv_, ny_, prec, t)
-    elif not args.no_autotune:
-        hjm.hjm_autotune(arr, prec, steps=8, stream=stream)
-    for x in items:
-        g = x["grid"]
-        key = "%dx%dx%d" % (g["n_r"], g["n_y"], g["n_v"])
-        tiles[key] = list(hjm.hjm_tile_get(g["n_r"], g["n_v"], g["n_y"], prec))
-    if args.tiles and not os.path.exists(args.tiles):
-        json.dump(tiles, open(args.tiles, "w"))
-
+    tiles = _tiles_for_workload(hjm, items, prec, arr, stream, args)
     for _ in range(args.warmup):
         step_dev()
     torch.cuda.synchronize()
@@ -507,13 +529,15 @@ def run_ours(args):
     e2e_max = reduce_max(e2e_s, world, device="cuda")
 
     # ---- per-kernel device times (trace mode: kernel by kernel, event pairs)
+    calls = max(1, min(args.steps, 3))
     hjm.hjm_trace_enable(True)
     hjm.hjm_trace_read(reset=True)
-    for _ in range(max(1, min(args.steps, 3))):
+    for _ in range(calls):
         step_dev()
     torch.cuda.synchronize()
     trace = hjm.hjm_trace_read(reset=True)
     hjm.hjm_trace_enable(False)
+    hjm.hjm_wait_status()
 
     total_points = sum(x["grid"]["n_r"] * x["grid"]["n_v"] * x["grid"]["n_y"] for x in items)
     elem = 4 if kprec == "fp32" else 8
@@ -524,31 +548,39 @@ def run_ours(args):
     avg_ms = tot_ms / max(launches, 1)
     roof = None
     if dom in WORDS_PER_POINT:
-        # one launch covers every grid point of every instrument of one shape
-        # group; for a single-shape workload that is all of them
+        # every pass of every step touches every point of every instrument
+        # once, so one call moves words x elem x (grid-point-steps) bytes in
+        # this pass; achieved = that / the pass's device time per call (for a
+        # batch of one grid shape this is the per-launch figure)
+        alg_call = (WORDS_PER_POINT_CS if scheme else WORDS_PER_POINT)[dom] * elem * ps
+        ms_call = tot_ms / calls
+        peak, peak_kind = measured_peaks()
+        achieved = alg_call / (ms_call * 1e-3) / 1e9
+        names = sorted({kernel_name(dom, tuple(t), kprec, scheme) for t in tiles.values()})
         shapes = {(x["grid"]["n_r"], x["grid"]["n_v"], x["grid"]["n_y"], x["grid"]["n_steps"]) for x in items}
         pts_launch = total_points / len(shapes)
-        alg = (WORDS_PER_POINT_CS if scheme else WORDS_PER_POINT)[dom] * elem * pts_launch
-        peak, peak_kind = measured_peaks()
-        achieved = alg / (avg_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "kernel": kernel_name(dom, tile_used, kprec, scheme), "achieved": achieved, "peak": peak,
+        roof = {"bound": "hbm", "kernel": " / ".join(names), "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms,
-                "traffic": recorded_traffic(dom, "%s-%s%s" % (args.workload, kprec, "-" + args.scheme if scheme else ""),
+                "algorithmic_bytes_per_launch": alg_call * calls / max(launches, 1), "avg_launch_ms": avg_ms,
+                "launches_per_call": launches / calls,
+                "traffic": recorded_traffic(dom, "%s-%s%s" % (wname, kprec, "-" + args.scheme if scheme else ""),
                                             pts_launch,
                                             ",".join(map(str, tile_used)) if tile_used else None)}
         if prec == "fp64" and dom == "pass1" and not scheme and tile_used is not None:
             # FP64 pass 1 is bound by FP64 arithmetic, not by HBM: report it
             # against the FP64 peak, the byte figures kept beside it
             fpp = pass1_flops_per_point(tile_used[0], tile_used[1])
-            flops = fpp * pts_launch
-            tf = flops / (avg_ms * 1e-3) / 1e12
+            flops = fpp * ps / (tot_ms / calls * 1e-3)
+            tf = flops / 1e12
             roof = {"bound": "alu", "kernel": roof["kernel"], "achieved": tf, "peak": FP64_PEAK_TFLOPS,
                     "peak_kind": "nominal (152 SMs x 2 FP64 FMA/clock x 2 flops x 2.07 GHz)", "unit": "TFLOP/s",
-                    "frac": tf / FP64_PEAK_TFLOPS, "flops_per_point": fpp, "algorithmic_flops_per_launch": flops,
-                    "avg_launch_ms": avg_ms, "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak,
-                    "traffic": roof["traffic"]}
+                    "frac": tf / FP64_PEAK_TFLOPS, "flops_per_point": fpp, "avg_launch_ms": avg_ms,
+                    "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak, "traffic": roof["traffic"]}
     shares = {k: round(trace[k][1] / max(sum(v[1] for v in trace.values()), 1e-12), 4) for k in KERNEL_KINDS}
+    # whole step against the HBM roofline: the three passes' algorithmic bytes
+    # (7 words per grid-point-step, 15 for the Craig-Sneyd family) per call
+    step_words = 15 if scheme else 7
+    step_gbs = step_words * elem * ps / (ms_max / args.steps * 1e-3) / 1e9
 
     # step launches: set-up, terminal, per ADI step 3 per stage (2 with the
     # strided passes fused) and 2 stages for the Craig-Sneyd family, read-out
@@ -591,11 +623,13 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "mixed" if prec == "mixed" else ("f32" if kprec == "fp32" else "f64"),
         "data": "synthetic",
-        "config": {"workload": desc, "instruments": n, "grid_point_steps_per_step": ps,
+        "config": {"workload": desc, "name": wname, "instruments": n, "grid_point_steps_per_step": ps,
                    "caplets_per_s": world * n * args.steps / (ms_max * 1e-3),
                    "precision": prec, "l2": "working set %.0f MB > L2 (no flush)" % (2 * total_points * elem / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "param_upload_bytes_per_step": n * item_bytes,
+                   "step_hbm": {"algorithmic_gbs": step_gbs, "frac": step_gbs / measured_peaks()[0],
+                                "words_per_point_step": step_words},
                    "tiles": {"autotuned": not (args.no_autotune or args.tile or args.tiles),
                              "from_file": bool(args.tiles), "fixed": bool(args.tile),
                              "r_x_y_x_v": tiles}},
@@ -609,10 +643,41 @@ def run_ours(args):
     }
     if mixed is not None:
         line["config"]["mixed"] = mixed
+    return line, items
+
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    from paper_1108_1688_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    barrier(world)
+    from paper_1108_1688_gb300 import hjm
+
+    # The headline: the 256-caplet uneven batch (the batched workload of the
+    # paper-shaped configurations and the largest single-GPU one), with the
+    # 100-caplet batch and the 512x256x256 bandwidth-stress caplet measured
+    # separately beside it.
+    if args.workload == "headline":
+        main_w, secondary = "config3", ["config2", "config4"]
+    else:
+        main_w, secondary = args.workload, []
+    line, items = measure(main_w, args, world, local, hjm)
+    if secondary:
+        line["secondary"] = []
+        for w in secondary:
+            sub, _ = measure(w, args, world, local, hjm)
+            line["secondary"].append({k: sub[k] for k in ("value", "unit", "ms_per_step", "dtype", "config",
+                                                          "e2e", "gpu_launches", "clocks", "roofline",
+                                                          "kernel_shares")})
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
+            oracle.build(omp=True)
             line["cpu_baseline"] = cpu_baseline(items)
         print(json.dumps(line))
     if world > 1:
@@ -626,8 +691,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="config2",
-                    choices=["config1", "config2", "config3", "config4", "config5", "paper63"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "config1", "config2", "config3", "config4", "config5", "paper63"],
+                    help="headline (default): the 256-caplet uneven batch, with the 100-caplet batch and the "
+                         "512x256x256 caplet measured beside it")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
     ap.add_argument("--scheme", default="douglas", choices=list(SCHEMES),
                     help="ADI scheme: the paper's Douglas, or Craig-Sneyd / modified CS / Hundsdorfer-Verwer")

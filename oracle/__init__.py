@@ -70,24 +70,36 @@ def _fill(struct_t, d):
     return s
 
 
-def build(force=False):
-    """Compile the oracle into oracle/_build/liborc.so (plain gcc, -O2)."""
+_LIB_OMP = os.path.join(_LIB_DIR, "liborc_omp.so")
+
+
+def build(force=False, omp=False):
+    """Compile the oracle into oracle/_build/liborc.so (plain gcc, -O2), or
+    with omp into liborc_omp.so: the same source with its OpenMP pragmas
+    active (lines of a pass shared among threads; used only to time the
+    oracle on all host cores, same results as the serial build)."""
     os.makedirs(_LIB_DIR, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(os.path.join(_HERE, "hjm_oracle.h"))):
-        return _LIB
-    tmp = _LIB + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-    os.replace(tmp, _LIB)
-    return _LIB
+    out = _LIB_OMP if omp else _LIB
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= os.path.getmtime(_SRC)
+            and os.path.getmtime(out) >= os.path.getmtime(os.path.join(_HERE, "hjm_oracle.h"))):
+        return out
+    tmp = out + ".tmp.%d" % os.getpid()
+    flags = ["-fopenmp"] if omp else ["-Wno-unknown-pragmas"]
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared"] + flags + ["-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+_lib_omp = None
+
+
+def lib(omp=False):
+    """The oracle library with argument types set; omp: the OpenMP build."""
+    global _lib, _lib_omp
     with _lock:
-        if _lib is None:
-            L = C.CDLL(build())
+        if (_lib_omp if omp else _lib) is None:
+            L = C.CDLL(build(omp=omp))
             P = C.POINTER
             dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
             L.orc_ctx_create.argtypes = [P(Curve), P(Model), P(Grid), P(Inst), P(C.c_void_p)]
@@ -129,8 +141,11 @@ def lib():
             L.orc_dirichlet.restype = C.c_double
             L.orc_price.argtypes = [P(Curve), P(Model), P(Grid), P(Inst), P(C.c_double)]
             L.orc_price.restype = C.c_int
-            _lib = L
-    return _lib
+            if omp:
+                _lib_omp = L
+            else:
+                _lib = L
+    return _lib_omp if omp else _lib
 
 
 class OracleError(ValueError):
@@ -140,14 +155,15 @@ class OracleError(ValueError):
 class Ctx:
     """One discretised problem: an item dict (curve, model, grid, inst)."""
 
-    def __init__(self, item):
+    def __init__(self, item, omp=False):
         self.item = item
+        self._L = lib(omp)
         self._c = _fill(Curve, item["curve"])
         self._m = _fill(Model, item["model"])
         self._g = _fill(Grid, item["grid"])
         self._i = _fill(Inst, item["inst"])
         h = C.c_void_p()
-        st = lib().orc_ctx_create(C.byref(self._c), C.byref(self._m), C.byref(self._g),
+        st = self._L.orc_ctx_create(C.byref(self._c), C.byref(self._m), C.byref(self._g),
                                   C.byref(self._i), C.byref(h))
         if st != 0:
             raise OracleError("oracle rejected the inputs (status %d)" % st)
@@ -158,7 +174,7 @@ class Ctx:
 
     def close(self):
         if getattr(self, "_h", None):
-            lib().orc_ctx_destroy(self._h)
+            self._L.orc_ctx_destroy(self._h)
             self._h = None
 
     __del__ = close
@@ -172,19 +188,19 @@ class Ctx:
     # scalars
     @property
     def strike(self):
-        return lib().orc_strike(self._h)
+        return self._L.orc_strike(self._h)
 
     @property
     def dt(self):
-        return lib().orc_dt(self._h)
+        return self._L.orc_dt(self._h)
 
     def time(self, n):
-        return lib().orc_time(self._h, float(n))
+        return self._L.orc_time(self._h, float(n))
 
     def axis(self, axis):
         n = self.n[axis]
         z, J, J2 = np.empty(n), np.empty(n), np.empty(n)
-        lib().orc_axis(self._h, axis, z, J, J2)
+        self._L.orc_axis(self._h, axis, z, J, J2)
         return z, J, J2
 
     def _field(self):
@@ -192,57 +208,57 @@ class Ctx:
 
     def terminal(self):
         U = self._field()
-        lib().orc_terminal(self._h, U)
+        self._L.orc_terminal(self._h, U)
         return U
 
     def explicit(self, n, U):
         out = self._field()
-        lib().orc_explicit(self._h, int(n), np.ascontiguousarray(U, dtype=np.float64), out)
+        self._L.orc_explicit(self._h, int(n), np.ascontiguousarray(U, dtype=np.float64), out)
         return out
 
     def apply_F(self, t, U):
         out = self._field()
-        lib().orc_apply_F(self._h, float(t), np.ascontiguousarray(U, dtype=np.float64), out)
+        self._L.orc_apply_F(self._h, float(t), np.ascontiguousarray(U, dtype=np.float64), out)
         return out
 
     def apply_dir(self, d, t, U):
         out = self._field()
-        lib().orc_apply_dir(self._h, int(d), float(t), np.ascontiguousarray(U, dtype=np.float64), out)
+        self._L.orc_apply_dir(self._h, int(d), float(t), np.ascontiguousarray(U, dtype=np.float64), out)
         return out
 
     def solve_dir(self, d, t, rhs, return_bad=False):
         out = self._field()
-        bad = lib().orc_solve_dir(self._h, int(d), float(t),
+        bad = self._L.orc_solve_dir(self._h, int(d), float(t),
                                   np.ascontiguousarray(rhs, dtype=np.float64), out)
         return (out, bad) if return_bad else out
 
     def line_matrix(self, d, t, line):
         n = self.n[d]
         a, b, c = np.empty(n), np.empty(n), np.empty(n)
-        lib().orc_line_matrix(self._h, int(d), float(t), int(line), a, b, c)
+        self._L.orc_line_matrix(self._h, int(d), float(t), int(line), a, b, c)
         return a, b, c
 
     def step(self, n, U):
         U = np.array(U, dtype=np.float64, copy=True)
-        lib().orc_step(self._h, int(n), U)
+        self._L.orc_step(self._h, int(n), U)
         return U
 
     def march(self):
         U = self._field()
-        lib().orc_march(self._h, U)
+        self._L.orc_march(self._h, U)
         return U
 
     def readout(self, U):
-        return lib().orc_readout(self._h, np.ascontiguousarray(U, dtype=np.float64))
+        return self._L.orc_readout(self._h, np.ascontiguousarray(U, dtype=np.float64))
 
     def readout_greeks(self, U):
         """(dC/dr, dC/dv) at the read-out point."""
         a, b = C.c_double(), C.c_double()
-        lib().orc_readout_greeks(self._h, np.ascontiguousarray(U, dtype=np.float64), C.byref(a), C.byref(b))
+        self._L.orc_readout_greeks(self._h, np.ascontiguousarray(U, dtype=np.float64), C.byref(a), C.byref(b))
         return a.value, b.value
 
     def dirichlet(self, t, r, y):
-        return lib().orc_dirichlet(self._h, float(t), float(r), float(y))
+        return self._L.orc_dirichlet(self._h, float(t), float(r), float(y))
 
 
 def price(item):

@@ -2,9 +2,11 @@
  * Plain CPU FP64 oracle of the discretised HJM-SV pricing PDE.
  *
  * TEST INFRASTRUCTURE ONLY: the GPU library is checked against this file; the
- * product path never loads it. Everything here is serial, unblocked and in
- * the order the paper states the method, so that it can be read against the
- * paper line by line:
+ * product path never loads it. Everything here is unblocked and in the order
+ * the paper states the method, so that it can be read against the paper line
+ * by line. It is serial as built for the tests; the few OpenMP pragmas only
+ * share independent lines (or planes) among threads in the separate OpenMP
+ * build that times the oracle on all host cores, with the same results:
  *
  *   Model and PDE ............ Section 3.1 (SDEs, bond formula with G(s)),
  *                              Section 3.2 (Eq. (1) and its coefficient list)
@@ -528,6 +530,7 @@ static double apply_node(const orc_ctx* x, int d, double t, const double* U,
 
 void orc_apply_dir(const orc_ctx* x, int d, double t, const double* U, double* AU)
 {
+#pragma omp parallel for
     for (int j = 0; j < x->n[2]; ++j)
         for (int k = 0; k < x->n[1]; ++k)
             for (int i = 0; i < x->n[0]; ++i)
@@ -537,6 +540,7 @@ void orc_apply_dir(const orc_ctx* x, int d, double t, const double* U, double* A
 /* F(U) of Section 5: the sum of all four split operators. */
 void orc_apply_F(const orc_ctx* x, double t, const double* U, double* F)
 {
+#pragma omp parallel for
     for (int j = 0; j < x->n[2]; ++j)
         for (int k = 0; k < x->n[1]; ++k)
             for (int i = 0; i < x->n[0]; ++i) {
@@ -557,6 +561,7 @@ void orc_explicit(const orc_ctx* x, int n, const double* U, double* dU0)
     int mid = x->g.explicit_midpoint || x->g.scheme != 0;
     double t = orc_time(x, mid ? n + 0.5 : n), t1 = orc_time(x, n + 1);
     orc_apply_F(x, t, U, dU0);
+#pragma omp parallel for
     for (int j = 0; j < x->n[2]; ++j)
         for (int k = 0; k < x->n[1]; ++k)
             for (int i = 0; i < x->n[0]; ++i) {
@@ -675,9 +680,15 @@ static void thomas(int n, const double* a, const double* b, const double* c,
 long orc_solve_dir(const orc_ctx* x, int d, double t, const double* rhs, double* out)
 {
     int n = x->n[d];
+    long bad = 0;
+    /* Lines are independent; the OpenMP build of this file (the multi-core
+     * timing of the oracle) shares them among threads, each with its own
+     * scratch, and gives the same results as the serial build. */
+#pragma omp parallel reduction(+ : bad)
+    {
     double* a = (double*)malloc(sizeof(double) * n * 7);
     double *b = a + n, *c = b + n, *r = c + n, *s = r + n, *cp = s + n, *dp = cp + n;
-    long bad = 0;
+#pragma omp for
     for (long line = 0; line < n_lines(x, d); ++line) {
         orc_line_matrix(x, d, t, line, a, b, c);
         for (int p = 0; p < n; ++p) {
@@ -694,6 +705,7 @@ long orc_solve_dir(const orc_ctx* x, int d, double t, const double* rhs, double*
         }
     }
     free(a);
+    }
     return bad;
 }
 

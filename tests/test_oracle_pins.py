@@ -909,3 +909,16 @@ def test_bond_delta_converges_to_closed_form(orc):
         vegas.append(abs(dv))
     assert errs[1] < 1e-4 and errs[0] / errs[1] > 3.5, errs
     assert vegas[0] < 2e-6 and vegas[1] < vegas[0], vegas
+
+
+def test_openmp_build_gives_the_serial_results(orc):
+    # The OpenMP build of the oracle (used only to time it on every host core)
+    # shares the lines of each pass among threads; each line's arithmetic is
+    # unchanged, so a march must agree with the serial build bit for bit.
+    it = W.config2_draws(1, n_r=24, n_y=10, n_v=12, n_steps=6)[0]
+    with orc.Ctx(it) as A, orc.Ctx(it, omp=True) as B:
+        U, V = A.terminal(), B.terminal()
+        for n in range(4):
+            U, V = A.step(n, U), B.step(n, V)
+        assert np.array_equal(U, V)
+        assert A.readout(U) == B.readout(V)
