@@ -231,15 +231,24 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
     for (int m = 0; m < M - 1; ++m) e[m + 1] = uc[m + 1] - uc[m];
     e[M] = uR - uc[M - 1];
 
-    // Node pairs: the right-hand side dt F / theta, the row of the r system
-    // divided by theta (a x_{m-1} + b x_m + c x_{m+1} with c = -up), and the
-    // forward elimination of the partition solve: rows m >= 1 become
-    //   A[m] x_s + x_m + C[m] x_{m+1} = D[m]   (x_s: the lane's first unknown),
-    // row 0 A[0] x_prev + x_s + C[0] x_1 = D[0] (x_prev: the previous lane's
-    // last unknown).
+    // Node pairs: the right-hand side dt F / theta and the row of the r
+    // system divided by theta, a x_{m-1} + b x_m + c x_{m+1} = d (c = -up),
+    // fused with a two-sided elimination of the lane's chunk: rows 1 .. H-1
+    // (H = M/2) are eliminated downwards in terms of the chunk's first
+    // unknown x_s = x_0,
+    //   x_m + C[m] x_{m+1} + A[m] x_s = D[m],
+    // rows M-2 .. H upwards in terms of its last unknown x_e = x_{M-1},
+    //   x_m + C[m] x_{m-1} + A[m] x_e = D[m],
+    // so the two recurrences (each a reciprocal per row) are independent and
+    // half as long as one sweep. Pairs are visited from both ends inwards
+    // (4-node blocks 0, Q-1, 1, Q-2, ...). Rows 0 and M-1 are kept as they
+    // are for the interface equations.
     float A[M], Cc[M], D[M];
+    float a0 = 0.f, b0 = 1.f, up0 = 0.f, d0 = 0.f, aN = 0.f, bN = 1.f, upN = 0.f, dN = 0.f;
+    constexpr int H = M / 2;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    for (int s = 0; s < Q; ++s) {
+        const int q = (s & 1) ? Q - 1 - (s >> 1) : (s >> 1);  // 0, Q-1, 1, Q-2, ...
         const float* t = tl + 4 * q;
         const float4 tL = lds4f(t + R2_L * TS), tU = lds4f(t + R2_U * TS), tP = lds4f(t + R2_P * TS);
         const float4 tQ = lds4f(t + R2_Q * TS), tB = lds4f(t + R2_B * TS), tE1 = lds4f(t + R2_E1 * TS);
@@ -247,7 +256,9 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
         const float4 tX = lds4f(t + R2_X * TS), tY = lds4f(t + R2_Y * TS);
         const float4 ya = lds4(pa + vo[q]), yb = lds4(pb + vo[q]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int hh = 0; hh < 2; ++hh) {
+            // pairs of a block below H ascend, pairs at or above H descend
+            const int h = (4 * q + 2 < H + 1) ? hh : 1 - hh;
             const int m = 4 * q + 2 * h;
 #define HJM_PR(v4) (h ? f2(v4.z, v4.w) : f2(v4.x, v4.y))
             const float2 Pp = HJM_PR(tP), E1 = HJM_PR(tE1);
@@ -281,52 +292,87 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
             const float2 b = fma2(tv2, E1, HJM_PR(tB));   // 1/theta - diag
 #undef HJM_PR
 #pragma unroll
-            for (int z = 0; z < 2; ++z) {
+            for (int zz = 0; zz < 2; ++zz) {
+                const int z = m < H ? zz : 1 - zz;  // the bottom recurrence runs upwards
                 const int mm = m + z;
                 const float az = z ? a.y : a.x, bz = z ? b.y : b.x, uz = z ? up.y : up.x;
-                const float dz = z ? acc.y : acc.x;
-                if (mm < 2) {
-                    const float r = rcp_approx(bz);
-                    A[mm] = az * r;
-                    Cc[mm] = -uz * r;
-                    D[mm] = dz * r;
-                } else {
-                    const float r = rcp_approx(fmaf(-az, Cc[mm - 1], bz));
-                    D[mm] = r * fmaf(-az, D[mm - 1], dz);
-                    A[mm] = -r * (az * A[mm - 1]);
-                    Cc[mm] = -uz * r;
+                float dz = z ? acc.y : acc.x;
+                if constexpr (!EXACT)
+                    if (sl * M + mm == nr - 1) dz = gHi - uc[mm];  // Dirichlet row inside the chunk
+                if (mm == 0) {
+                    a0 = az, b0 = bz, up0 = uz, d0 = dz;
+                } else if (mm == M - 1) {
+                    aN = az, bN = bz, upN = uz, dN = dz;
+                } else if (mm < H) {  // downwards, reference x_s
+                    if (mm == 1) {
+                        const float r = rcp_approx(bz);
+                        Cc[mm] = -uz * r;
+                        D[mm] = dz * r;
+                        A[mm] = az * r;
+                    } else {
+                        const float r = rcp_approx(fmaf(-az, Cc[mm - 1], bz));
+                        Cc[mm] = -uz * r;
+                        D[mm] = r * fmaf(-az, D[mm - 1], dz);
+                        A[mm] = -r * (az * A[mm - 1]);
+                    }
+                } else {  // upwards, reference x_e
+                    if (mm == M - 2) {
+                        const float r = rcp_approx(bz);
+                        Cc[mm] = az * r;
+                        D[mm] = dz * r;
+                        A[mm] = -uz * r;
+                    } else {
+                        const float r = rcp_approx(fmaf(uz, Cc[mm + 1], bz));
+                        Cc[mm] = az * r;
+                        D[mm] = r * fmaf(uz, D[mm + 1], dz);
+                        A[mm] = r * (uz * A[mm + 1]);
+                    }
                 }
             }
         }
     }
     // Dirichlet rows (identity rows from the tables): r_min on the first
     // lane's first node, r_max on node n_r - 1.
-    if (sl == 0) D[0] = gLo - u0;
-    if constexpr (EXACT) {
-        if (sl == S - 1) D[M - 1] = gHi - uM;
-    } else {
-        const int mh = nr - 1 - sl * M;
-        if (mh >= 0 && mh < M) {
-            const int e = nr - 1;
-            const float un = *reinterpret_cast<const float*>(rc + (e >> 5) * kChunkBytes + (e & 31) * 4);
-#pragma unroll
-            for (int m = 0; m < M; ++m)
-                if (m == mh) D[m] = gHi - un;
-        }
-    }
-    // Backward elimination: rows 1 .. M-2 become A x_s + x_m + C x_e = D.
-#pragma unroll
-    for (int m = M - 3; m >= 1; --m) {
-        D[m] = fmaf(-Cc[m], D[m + 1], D[m]);
-        A[m] = fmaf(-Cc[m], A[m + 1], A[m]);
-        Cc[m] = -Cc[m] * Cc[m + 1];
-    }
-    // Row 0 in terms of x_prev and x_e.
+    if (sl == 0) d0 = gLo - u0;
+    if constexpr (EXACT)
+        if (sl == S - 1) dN = gHi - uM;
+    // Join the two recurrences at rows H-1 and H, then substitute outwards:
+    // every row 1 .. M-2 becomes x_m = D[m] + A[m] x_s + Cc[m] x_e.
     {
-        const float r = rcp_approx(fmaf(-Cc[0], A[1], 1.0f));
-        D[0] = r * fmaf(-Cc[0], D[1], D[0]);
-        A[0] = r * A[0];
-        Cc[0] = -r * Cc[0] * Cc[1];
+        const float rho = rcp_approx(fmaf(-Cc[H], Cc[H - 1], 1.0f));
+        const float fH = rho * fmaf(-Cc[H], D[H - 1], D[H]);
+        const float gH = rho * (Cc[H] * A[H - 1]);
+        const float kH = -rho * A[H];
+        const float fL = fmaf(-Cc[H - 1], fH, D[H - 1]);
+        const float gL = fmaf(-Cc[H - 1], gH, -A[H - 1]);
+        const float kL = -Cc[H - 1] * kH;
+        D[H] = fH, A[H] = gH, Cc[H] = kH;
+        D[H - 1] = fL, A[H - 1] = gL, Cc[H - 1] = kL;
+    }
+#pragma unroll
+    for (int t = 1; t < H - 1; ++t) {
+        const int mt = H - 1 - t, mb = H + t;  // top row going up, bottom row going down
+        const float ct = Cc[mt], cb = Cc[mb];
+        D[mt] = fmaf(-ct, D[mt + 1], D[mt]);
+        A[mt] = fmaf(-ct, A[mt + 1], -A[mt]);
+        Cc[mt] = -ct * Cc[mt + 1];
+        D[mb] = fmaf(-cb, D[mb - 1], D[mb]);
+        const float kb = fmaf(-cb, Cc[mb - 1], -A[mb]);
+        A[mb] = -cb * A[mb - 1];
+        Cc[mb] = kb;
+    }
+    // Rows 0 and M-1 in the form of the interface equations:
+    //   x_s = dS - aS x_prev - cS x_e,   aE x_s + x_e + cE x_next = dE.
+    float aS, cS, dS, aE, cE, dE;
+    {
+        const float r0 = rcp_approx(fmaf(-up0, A[1], b0));
+        dS = r0 * fmaf(up0, D[1], d0);
+        aS = r0 * a0;
+        cS = -r0 * (up0 * Cc[1]);
+        const float rN = rcp_approx(fmaf(aN, Cc[M - 2], bN));
+        aE = rN * (aN * A[M - 2]);
+        cE = -rN * upN;
+        dE = rN * fmaf(-aN, D[M - 2], dN);
     }
     // Interface equations in the lanes' last unknowns x_e, normalised to a
     // unit diagonal, solved by parallel cyclic reduction over width-S
@@ -335,8 +381,6 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
     // super-diagonal, and each level doubles the zeroed span), so the
     // out-of-range shuffles (which return the lane's own finite values) are
     // multiplied by zero.
-    const float aS = A[0], cS = Cc[0], dS = D[0];
-    const float aE = A[M - 1], cE = Cc[M - 1], dE = D[M - 1];
     float aSn = __shfl_down_sync(FULL, aS, 1, S);
     float cSn = __shfl_down_sync(FULL, cS, 1, S);
     float dSn = __shfl_down_sync(FULL, dS, 1, S);
@@ -366,7 +410,7 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
     if (sl == 0) xEp = 0.f;
     const float xS = fmaf(-aS, xEp, fmaf(-cS, xE, dS));
 #pragma unroll
-    for (int m = 1; m < M - 1; ++m) x[m] = fmaf(-A[m], xS, fmaf(-Cc[m], xE, D[m]));
+    for (int m = 1; m < M - 1; ++m) x[m] = fmaf(A[m], xS, fmaf(Cc[m], xE, D[m]));
     x[0] = xS;
     x[M - 1] = xE;
 }
