@@ -335,7 +335,7 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
     if (g->explicit_midpoint != 0 && g->explicit_midpoint != 1) return 1;
     if (g->scheme < 0 || g->scheme > 3) return 1;
     if (!(in->T > 0.0)) return 1;
-    if (in->kind != 0 && in->kind != 1) return 1;
+    if (in->kind != 0 && in->kind != 1 && in->kind != 2) return 1;
     double r0 = orc_curve_f(c, 0.0);
     if (r0 < g->r_min || r0 > g->r_max) return 1;
 
@@ -348,7 +348,7 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
     x->in = *in;
     x->K = 0.0;
     x->DM = 1.0;
-    if (in->kind == 1) {
+    if (in->kind == 1 || in->kind == 2) {
         if (!(in->TM > in->T)) { free(x); return 1; }
         x->K = in->K + (in->strike_atm_relative ? orc_atm_strike(c, in->T, in->TM) : 0.0);
         x->DM = 1.0 + (in->TM - in->T) * x->K;
@@ -357,7 +357,7 @@ int orc_ctx_create(const orc_curve* c, const orc_model* m, const orc_grid* g,
     x->dt = in->T / g->n_steps;
     x->n[0] = g->n_r; x->n[1] = g->n_v; x->n[2] = g->n_y;
     x->lo[0] = g->r_min; x->hi[0] = g->r_max; x->alpha[0] = g->alpha_r;
-    x->centre[0] = g->center_r_on_strike ? (in->kind == 1 ? x->K : r0) : g->k_r;
+    x->centre[0] = g->center_r_on_strike ? (in->kind != 0 ? x->K : r0) : g->k_r;
     x->lo[1] = 0.0; x->hi[1] = g->v_max; x->alpha[1] = g->alpha_v; x->centre[1] = g->k_v;
     x->lo[2] = 0.0; x->hi[2] = g->y_max; x->alpha[2] = g->alpha_y; x->centre[2] = 0.0;
     for (int d = 0; d < 3; ++d) {
@@ -445,13 +445,15 @@ static coeffs coeffs_at(const orc_ctx* x, int i, int k, int j, double t)
 }
 
 /* Dirichlet data g(t, r, y) (reading R8). Section 4.1 proposes the exact
- * bond as boundary data; for the caplet the deep in/out-of-the-money value. */
+ * bond as boundary data; for the caplet and the floorlet the deep in/out-of-
+ * the-money value, the positive part of the forward contract
+ * p(t,T) - Delta_M p(t,T_M) (caplet) or of its negative (floorlet). */
 double orc_dirichlet(const orc_ctx* x, double t, double r, double y)
 {
     double pT = orc_bond(&x->c, &x->m, t, x->in.T, r, y);
     if (x->in.kind == 0) return pT;
     double pM = orc_bond(&x->c, &x->m, t, x->in.TM, r, y);
-    double v = pT - x->DM * pM;
+    double v = x->in.kind == 1 ? pT - x->DM * pM : x->DM * pM - pT;
     return v > 0.0 ? v : 0.0;
 }
 
@@ -792,12 +794,36 @@ static void gauss_legendre(int n, double* xs, double* ws)
     }
 }
 
+/* Average over r in [ra, rb] of the floorlet payoff max(Delta_M p(T,T_M) - 1,
+ * 0) at fixed y: with p(T,T_M) = A(y) e^{-G r} it is positive for r below
+ * r* = ln(Delta_M A)/G, and its integral there is closed form. */
+static double floor_avg_r(const orc_ctx* x, double ra, double rb, double y)
+{
+    double T = x->in.T, TM = x->in.TM;
+    double G = orc_G(x->m.kappa, TM - T);
+    double A = orc_curve_P(&x->c, TM) / orc_curve_P(&x->c, T)
+             * exp(G * orc_curve_f(&x->c, T) - 0.5 * G * G * y);
+    double DA = x->DM * A;
+    if (!(rb > ra)) {
+        double v = DA * exp(-G * ra) - 1.0;
+        return v > 0.0 ? v : 0.0;
+    }
+    double rstar = log(DA) / G;
+    double mhi = rb < rstar ? rb : rstar;
+    if (mhi <= ra) return 0.0;
+    /* int_ra^mhi (DA e^{-G r} - 1) dr */
+    double integral = DA * exp(-G * ra) * (-expm1(-G * (mhi - ra))) / G - (mhi - ra);
+    return integral / (rb - ra);
+}
+
 /* Average over r in [ra, rb] of the caplet payoff max(1 - Delta_M p(T,T_M), 0)
  * at fixed y (Section 3.2 payoff, Section 7.2 average). With p(T,T_M) =
  * A(y) e^{-G r} the payoff is positive for r above r* = ln(Delta_M A)/G and
- * its integral there is closed form. */
+ * its integral there is closed form. The floorlet pays the other side,
+ * max(Delta_M p(T,T_M) - 1, 0), positive below r*. */
 static double payoff_avg_r(const orc_ctx* x, double ra, double rb, double y)
 {
+    if (x->in.kind == 2) return floor_avg_r(x, ra, rb, y);
     double T = x->in.T, TM = x->in.TM;
     double G = orc_G(x->m.kappa, TM - T);
     double A = orc_curve_P(&x->c, TM) / orc_curve_P(&x->c, T)
@@ -816,8 +842,8 @@ static double payoff_avg_r(const orc_ctx* x, double ra, double rb, double y)
 }
 
 /* Terminal field U^0 at t = T: 1 for the bond (Section 3.2); the payoff
- * averaged over each node's control volume in r and y for the caplet
- * (Section 7.2, reading R11). v plays no role. */
+ * averaged over each node's control volume in r and y for the caplet and the
+ * floorlet (Section 7.2, reading R11). v plays no role. */
 void orc_terminal(const orc_ctx* x, double* U)
 {
     long N = orc_n_points(x);

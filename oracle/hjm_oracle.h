@@ -69,7 +69,9 @@ typedef struct {
 
 /* Instrument: kind 0 zero-coupon bond maturing at T; kind 1 caplet with
  * expiry T, payment date TM and strike K (K is added to the ATM forward
- * rate when strike_atm_relative != 0). */
+ * rate when strike_atm_relative != 0), paying at T the put on the bond
+ * max(1 - Delta_M p(T,T_M), 0), Delta_M = 1 + (TM - T) K (Section 3.2);
+ * kind 2 the floorlet on the same period, max(Delta_M p(T,T_M) - 1, 0). */
 typedef struct {
     int kind;
     double T, TM, K;

@@ -97,6 +97,28 @@ def caplet(T, TM, K=0.0, atm_relative=True):
                 strike_atm_relative=1 if atm_relative else 0)
 
 
+def floorlet(T, TM, K=0.0, atm_relative=True):
+    """Floorlet on [T, TM]: pays max(Delta_M p(T,TM) - 1, 0) at T (the other
+    side of the caplet; caplet - floorlet is the forward contract)."""
+    return dict(kind=2, T=float(T), TM=float(TM), K=float(K),
+                strike_atm_relative=1 if atm_relative else 0)
+
+
+def strip(curve, mdl, T0, tenor, count, K, kind=1, n_r=64, n_y=32, n_v=32, steps_per_year=24, **grid_kw):
+    """A cap (kind 1) or floor (kind 2) as its strip of caplets / floorlets on
+    the periods [T0 + i tenor, T0 + (i + 1) tenor], i < count, each with
+    absolute strike K on its own grid (the domain recipe of default_grid for
+    its expiry, steps_per_year time steps a year). The strip's price is the
+    sum of the items' prices."""
+    out = []
+    for i in range(count):
+        T = T0 + i * tenor
+        inst = (caplet if kind == 1 else floorlet)(T, T + tenor, K, atm_relative=False)
+        ns = max(8, int(round(steps_per_year * T)))
+        out.append(item(curve, mdl, default_grid(curve, mdl, T, n_r, n_y, n_v, ns, **grid_kw), inst))
+    return out
+
+
 def curve_level_bound(curve):
     """An upper bound on |f(0,t)| read off the parameters (x e^{-x} <= 1/e);
     for a discrete curve a rough scale: twice the largest zero rate or

@@ -73,6 +73,10 @@ MUTATIONS = [
     ("knot forward sign", "        knot_curve_at(c, t, &s, &ds, &d2s);\n        return -ds;",
      "        knot_curve_at(c, t, &s, &ds, &d2s);\n        return ds;"),
     ("knot drift curvature sign in the PDE", "        df0 = -d2s;", "        df0 = d2s;"),
+    ("floorlet integral over the whole cell",
+     "double integral = DA * exp(-G * ra) * (-expm1(-G * (mhi - ra))) / G - (mhi - ra);",
+     "double integral = DA * exp(-G * ra) * (-expm1(-G * (mhi - ra))) / G - (rb - ra);"),
+    ("floorlet paid on the caplet side", "double mhi = rb < rstar ? rb : rstar;", "double mhi = rb;"),
 ]
 
 
@@ -106,6 +110,7 @@ def _pins(orc):
     yield lambda: P.test_douglas_step_equals_dense_product(orc, 1)
     yield lambda: P.test_dirichlet_data(orc)
     yield lambda: P.test_payoff_average_exact_in_r(orc)
+    yield lambda: P.test_floorlet_payoff_average_exact_in_r(orc)
     yield lambda: P.test_readout_exact_on_bicubics(orc)
     yield lambda: P.test_greeks_exact_on_bicubics(orc)
     yield lambda: P.test_config1_bond_price(orc)
