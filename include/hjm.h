@@ -140,8 +140,11 @@ typedef enum {
 /* Instruments of Section 3.2. ZCB pays 1 at T. CAPLET pays
  * max(1 - Delta_M p(T,T_M), 0) at T with Delta_M = 1 + (T_M - T) K; when
  * strike_atm_relative != 0 the strike is K plus the ATM simple forward
- * (P(0,T)/P(0,T_M) - 1)/(T_M - T). */
-typedef enum { HJM_ZCB = 0, HJM_CAPLET = 1 } hjm_kind;
+ * (P(0,T)/P(0,T_M) - 1)/(T_M - T). FLOORLET pays the other side,
+ * max(Delta_M p(T,T_M) - 1, 0) at T (caplet - floorlet is the forward
+ * contract, P(0,T) - Delta_M P(0,T_M) at t = 0). A cap (floor) is the sum of
+ * its caplets (floorlets): see hjm_price_strip. */
+typedef enum { HJM_ZCB = 0, HJM_CAPLET = 1, HJM_FLOORLET = 2 } hjm_kind;
 typedef struct {
     int kind;                 /* hjm_kind */
     double expiry_T, pay_TM, strike_K;
@@ -367,6 +370,18 @@ hjm_status hjm_surrogate_error_table(const hjm_surrogate* s, float* out);
 hjm_status hjm_surrogate_save(const hjm_surrogate* s, const char* path);
 hjm_status hjm_surrogate_load(const char* path, hjm_surrogate** out);
 hjm_status hjm_surrogate_destroy(hjm_surrogate* s);
+/* A cap or a floor (Section 1 motivates the model by their calibration): the
+ * strip of its caplets or floorlets, items[i] the period [T_i, T_i + tenor]
+ * with T_{i+1} = T_i + tenor, all of one kind (HJM_CAPLET for a cap,
+ * HJM_FLOORLET for a floor) with the same curve, model, tenor and absolute
+ * strike (strike_atm_relative = 0); each item on its own grid (the caller
+ * sizes the domain for its expiry). Prices the strip as one batch
+ * (hjm_price_batch, host outputs) and returns the sum in *strip_price and,
+ * when item_prices is not NULL, each period's price. HJM_EINVAL when the
+ * items do not form such a strip. */
+hjm_status hjm_price_strip(const hjm_batch_item* items, size_t n, hjm_precision precision, double tol_rel,
+                           double* strip_price, double* item_prices, void* cuda_stream);
+
 /* The surrogate's tensor-core product, exposed for testing: C[M x N] (FP32,
  * device) = op(A) op(B) with bfloat16 A, B (device); op(A)(m,k) = A[m lda+k]
  * or A[k lda+m] when trans_a, op(B)(k,n) = B[k ldb+n] or B[n ldb+k]. */

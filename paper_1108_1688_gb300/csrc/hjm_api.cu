@@ -134,11 +134,11 @@ static hjm_status validate(const hjm_curve& c, const hjm_model_params& m, const 
     if (in) {
         if (!finite_all({in->expiry_T, in->pay_TM, in->strike_K}))
             return fail(HJM_EINVAL, "non-finite instrument field");
-        if (in->kind != HJM_ZCB && in->kind != HJM_CAPLET)
+        if (in->kind != HJM_ZCB && in->kind != HJM_CAPLET && in->kind != HJM_FLOORLET)
             return fail(HJM_EINVAL, "unknown instrument kind %d", in->kind);
         if (!(in->expiry_T > 0.0)) return fail(HJM_EINVAL, "expiry must be > 0");
-        if (in->kind == HJM_CAPLET && !(in->pay_TM > in->expiry_T))
-            return fail(HJM_EINVAL, "caplet needs pay_TM > expiry_T");
+        if (in->kind != HJM_ZCB && !(in->pay_TM > in->expiry_T))
+            return fail(HJM_EINVAL, "caplet and floorlet need pay_TM > expiry_T");
     }
     return HJM_OK;
 }
@@ -183,7 +183,7 @@ static InstParams to_params(const hjm_batch_item& it)
     p.scheme = it.grid.scheme;
     p.kind = it.inst.kind;
     p.T = it.inst.expiry_T;
-    p.TM = it.inst.kind == HJM_CAPLET ? it.inst.pay_TM : it.inst.expiry_T;
+    p.TM = it.inst.kind != HJM_ZCB ? it.inst.pay_TM : it.inst.expiry_T;
     p.K = it.inst.strike_K;
     p.atm_rel = it.inst.strike_atm_relative != 0;
     return p;
@@ -882,6 +882,52 @@ extern "C" hjm_status hjm_price_batch(const hjm_batch_item* items, size_t n, hjm
     if (st != HJM_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
     return price_batch(*stream_workspace(s), items, n, precision, tol_rel, prices_out, infos_out, s);
+}
+
+// ------------------------------------------------------- caps and floors
+
+// Field by field (the struct has padding after its ints).
+static bool same_curve(const hjm_curve& a, const hjm_curve& b)
+{
+    if (a.kind != b.kind || a.flat_rate != b.flat_rate || a.beta0 != b.beta0 || a.beta1 != b.beta1 ||
+        a.beta2 != b.beta2 || a.tau != b.tau || a.n_knots != b.n_knots)
+        return false;
+    for (int k = 0; k < a.n_knots && k < HJM_MAX_KNOTS; ++k)
+        if (a.knot_t[k] != b.knot_t[k] || a.knot_P[k] != b.knot_P[k]) return false;
+    return true;
+}
+
+extern "C" hjm_status hjm_price_strip(const hjm_batch_item* items, size_t n, hjm_precision precision,
+                                      double tol_rel, double* strip_price, double* item_prices,
+                                      void* cuda_stream)
+{
+    if (!items || !strip_price || n == 0) return fail(HJM_EINVAL, "null argument or empty strip");
+    const hjm_instrument& f = items[0].inst;
+    if (f.kind != HJM_CAPLET && f.kind != HJM_FLOORLET)
+        return fail(HJM_EINVAL, "a strip holds caplets (a cap) or floorlets (a floor)");
+    const double tenor = f.pay_TM - f.expiry_T;
+    for (size_t i = 0; i < n; ++i) {
+        const hjm_batch_item& it = items[i];
+        if (it.inst.kind != f.kind || it.inst.strike_atm_relative != 0 || it.inst.strike_K != f.strike_K)
+            return fail(HJM_EINVAL, "strip item %zu: one kind and one absolute strike", i);
+        if (!same_curve(it.curve, items[0].curve) || memcmp(&it.model, &items[0].model, sizeof it.model) != 0)
+            return fail(HJM_EINVAL, "strip item %zu: the curve and the model of the strip", i);
+        const double ti = it.inst.pay_TM - it.inst.expiry_T;
+        if (fabs(ti - tenor) > 1e-12 * fmax(1.0, tenor))
+            return fail(HJM_EINVAL, "strip item %zu: the tenor of the strip", i);
+        if (i > 0 && fabs(it.inst.expiry_T - items[i - 1].inst.pay_TM) > 1e-12 * fmax(1.0, it.inst.expiry_T))
+            return fail(HJM_EINVAL, "strip item %zu does not start where item %zu ends", i, i - 1);
+    }
+    std::vector<double> p(n);
+    hjm_status st = hjm_price_batch(items, n, precision, tol_rel, p.data(), nullptr, cuda_stream);
+    if (st != HJM_OK) return st;
+    double s = 0.0;
+    for (size_t i = 0; i < n; ++i) {
+        s += p[i];
+        if (item_prices) item_prices[i] = p[i];
+    }
+    *strip_price = s;
+    return HJM_OK;
 }
 
 // ---------------------------------------------------------- launch shapes

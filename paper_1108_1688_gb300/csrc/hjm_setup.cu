@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
     __shared__ InstDerived D;
     if (tid == 0) {
         double K = 0.0, DM = 1.0;
-        if (p.kind == HJM_CAPLET) {
+        if (p.kind != HJM_ZCB) {
             K = p.K;
             if (p.atm_rel) K += (discount(p, p.T) / discount(p, p.TM) - 1.0) / (p.TM - p.T);
             DM = 1.0 + (p.TM - p.T) * K;
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         D.K = K;
         D.DM = DM;
         D.dt = p.T / ns;
-        D.centre_r = p.center_on_strike ? (p.kind == HJM_CAPLET ? K : fwd(p, 0.0)) : p.kr;
+        D.centre_r = p.center_on_strike ? (p.kind != HJM_ZCB ? K : fwd(p, 0.0)) : p.kr;
         g.derived[b] = D;
     }
     __syncthreads();
@@ -505,9 +505,9 @@ __global__ void __launch_bounds__(128) k_faces(GroupTables g)
         const double r = face ? p.rmax : p.rmin, y = axy[j], x = r - sc[2];
         const double pT = sc[0] * exp(-sc[3] * x - 0.5 * sc[3] * sc[3] * y);
         double v = pT;
-        if (p.kind == HJM_CAPLET) {
+        if (p.kind != HJM_ZCB) {
             const double pM = sc[1] * exp(-sc[4] * x - 0.5 * sc[4] * sc[4] * y);
-            v = fmax(pT - sc[5] * pM, 0.0);
+            v = fmax(p.kind == HJM_CAPLET ? pT - sc[5] * pM : sc[5] * pM - pT, 0.0);
         }
         dir[idx] = (T)v;
     }
@@ -537,6 +537,22 @@ __device__ void gauss_legendre8(double* x, double* wt, int q)
     wt[q] = 2.0 / ((1.0 - z * z) * dp * dp);
 }
 
+// Mean over r in [ra, rb] of the floorlet payoff max(Delta_M p(T,T_M; r, y) - 1,
+// 0), Delta_M p = e^{lnDA - G r}: positive below r* = lnDA / G, its integral
+// there closed form.
+__device__ double floorlet_r_mean(double G, double lnDA, double ra, double rb)
+{
+    if (!(rb > ra)) {
+        const double v = exp(lnDA - G * ra) - 1.0;
+        return v > 0.0 ? v : 0.0;
+    }
+    const double hi = fmin(rb, lnDA / G);
+    if (hi <= ra) return 0.0;
+    // int_ra^hi e^{lnDA - G r} - 1 dr
+    const double body = exp(lnDA - G * ra) * (-expm1(-G * (hi - ra))) / G;
+    return (body - (hi - ra)) / (rb - ra);
+}
+
 // Mean over r in [ra, rb] of max(1 - Delta_M p(T,T_M; r, y), 0) where
 // Delta_M p = e^{lnDA - G r}: the payoff is positive above r* = lnDA / G and
 // its integral there is closed form.
@@ -553,7 +569,7 @@ __device__ double caplet_r_mean(double G, double lnDA, double ra, double rb)
     return ((rb - lo) - tail) / (rb - ra);
 }
 
-// U^0 at t = T: 1 for a bond; for a caplet the payoff averaged over each
+// U^0 at t = T: 1 for a bond; for a caplet or floorlet the payoff averaged over each
 // node's control volume in r and y (Section 7.2; closed form in r, 8-point
 // Gauss-Legendre in y), the same for every v. One block per (y node,
 // instrument); the y cell and the curve factors are formed once per block.
@@ -565,7 +581,7 @@ __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
     const InstParams& p = g.params[b];
     __shared__ double gx[8], gw[8], sc[4];
     if (threadIdx.x < 8) gauss_legendre8(gx, gw, threadIdx.x);
-    if (p.kind == HJM_CAPLET && threadIdx.x == 32) {
+    if (p.kind != HJM_ZCB && threadIdx.x == 32) {
         const InstDerived D = g.derived[b];
         const double hy = 1.0 / (ny - 1);
         const double G = Gfun(p.kappa, p.TM - p.T);
@@ -581,14 +597,16 @@ __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
     const double centre = g.derived[b].centre_r;
     for (int i = threadIdx.x; i < nr; i += blockDim.x) {
         double val = 1.0;
-        if (p.kind == HJM_CAPLET) {
+        if (p.kind != HJM_ZCB) {
             const double ra = metric_z(fmax(0.0, (i - 0.5) * hr), p.rmin, p.rmax, p.ar, centre);
             const double rb = metric_z(fmin(1.0, (i + 0.5) * hr), p.rmin, p.rmax, p.ar, centre);
             const double G = sc[0], ya = sc[2], yb = sc[3];
             double s = 0.0;
             for (int q = 0; q < 8; ++q) {
                 const double yq = 0.5 * (ya + yb) + 0.5 * (yb - ya) * gx[q];
-                s += 0.5 * gw[q] * caplet_r_mean(G, sc[1] - 0.5 * G * G * yq, ra, rb);
+                const double lnDA = sc[1] - 0.5 * G * G * yq;
+                s += 0.5 * gw[q] * (p.kind == HJM_CAPLET ? caplet_r_mean(G, lnDA, ra, rb)
+                                                         : floorlet_r_mean(G, lnDA, ra, rb));
             }
             val = s;
         }

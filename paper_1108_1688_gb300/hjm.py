@@ -22,7 +22,7 @@ HJM_OK, HJM_EINVAL, HJM_ENOMEM, HJM_ECUDA, HJM_ETOL, HJM_ETIMEOUT, HJM_ENUMERIC,
 HJM_FP64, HJM_FP32, HJM_MIXED = 0, 1, 2
 HJM_CURVE_FLAT, HJM_CURVE_NELSON_SIEGEL, HJM_CURVE_KNOTS = 0, 1, 2
 HJM_SCHEME_DOUGLAS, HJM_SCHEME_CS, HJM_SCHEME_MCS, HJM_SCHEME_HV = 0, 1, 2, 3
-HJM_ZCB, HJM_CAPLET = 0, 1
+HJM_ZCB, HJM_CAPLET, HJM_FLOORLET = 0, 1, 2
 
 PRECISIONS = {"fp64": HJM_FP64, "fp32": HJM_FP32, "mixed": HJM_MIXED,
               HJM_FP64: HJM_FP64, HJM_FP32: HJM_FP32, HJM_MIXED: HJM_MIXED}
@@ -126,6 +126,7 @@ def _load():
         "hjm_tile_set": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
         "hjm_autotune": ([P(hjm_batch_item), C.c_size_t, st, C.c_int, vp], st),
         "hjm_wait_status": ([st], st),
+        "hjm_price_strip": ([P(hjm_batch_item), C.c_size_t, st, C.c_double, P(C.c_double), P(C.c_double), vp], st),
         "hjm_test_drop_plane": ([C.c_int, C.c_uint], st),
         "hjm_status_string": ([st], C.c_char_p),
         "hjm_last_error": ([], C.c_char_p),
@@ -144,7 +145,8 @@ EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch
             "hjm_surrogate_get_params", "hjm_surrogate_set_params", "hjm_surrogate_error_table",
             "hjm_surrogate_save", "hjm_surrogate_load", "hjm_surrogate_destroy", "hjm_mlp_gemm",
             "hjm_trace_enable", "hjm_trace_read", "hjm_tile_get", "hjm_tile_set", "hjm_autotune",
-            "hjm_wait_status", "hjm_test_drop_plane", "hjm_status_string", "hjm_last_error")
+            "hjm_wait_status", "hjm_test_drop_plane", "hjm_price_strip", "hjm_status_string",
+            "hjm_last_error")
 
 
 class HJMError(RuntimeError):
@@ -314,6 +316,16 @@ def hjm_autotune(items, precision=HJM_FP32, steps=8, stream=None):
     """Time every candidate launch shape on the items' grid shapes and keep the fastest."""
     arr = items if isinstance(items, C.Array) else make_items(items)
     _check(lib.hjm_autotune(arr, len(arr), PRECISIONS[precision], int(steps), _stream(stream)))
+
+
+def hjm_price_strip(items, precision=HJM_FP32, tol_rel=1e-4, stream=None):
+    """A cap or floor from its strip of caplets / floorlets: (total, per period)."""
+    arr = items if isinstance(items, C.Array) else make_items(items)
+    total = C.c_double()
+    each = (C.c_double * len(arr))()
+    _check(lib.hjm_price_strip(arr, len(arr), PRECISIONS[precision], float(tol_rel), C.byref(total), each,
+                               _stream(stream)))
+    return float(total.value), [float(v) for v in each]
 
 
 def hjm_wait_status(reset=False):
