@@ -315,7 +315,10 @@ hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_precision pre
  * of the curve over [T, T + delta]. Output: the forward premium C / P(0,T)
  * of the caplet paying max(1 - (1 + delta K) p(T, T_M), 0) at T (multiply by
  * the caller's P(0,T) for the price). With gamma = 0 this quantity depends on
- * the curve only through F.
+ * the curve only through F. It is the Gaussian-HJM caplet of Section 3.1
+ * (epsilon = 0: a put on the log-normal bond p(T,T_M), in closed form) plus
+ * the stochastic-volatility correction, and the network learns only the
+ * correction, scaled: q = (C - C_gauss) / (P(0,T) delta 1e-4).
  *
  * Training data are the library's own FP32 march prices (labels on a flat
  * curve with that forward), drawn uniformly over the box of features
@@ -349,15 +352,22 @@ hjm_status hjm_surrogate_create(const hjm_surrogate_cfg* cfg, void* cuda_stream,
 /* Draw, label with the march, train, build the error table. Synchronous. */
 hjm_status hjm_surrogate_train(const hjm_surrogate_cfg* cfg, void* cuda_stream, hjm_surrogate** out);
 /* epochs of AdamW on given data: x [n][9] raw inputs and t [n] scaled
- * targets C / (P(0,T) delta 0.01), both device. */
+ * targets q = (C - C_gauss) / (P(0,T) delta 1e-4), both device. */
 hjm_status hjm_surrogate_fit(hjm_surrogate* s, const float* x, const float* t, size_t n, int epochs,
                              void* cuda_stream, float* final_loss);
 /* Gated prices (device x [n][9], device price_out [n], device used_pde [n]
  * or NULL). Synchronises when rows fall back. */
 hjm_status hjm_surrogate_infer(hjm_surrogate* s, const float* x, size_t n, double* price_out,
                                uint8_t* used_pde, void* cuda_stream);
-/* The network alone: y_out [n] = scaled output (device). */
+/* The network alone: y_out [n] = scaled output q (device). */
 hjm_status hjm_surrogate_forward(hjm_surrogate* s, const float* x, size_t n, float* y_out, void* cuda_stream);
+/* The network alone as forward premia, C_gauss / P(0,T) + q delta 1e-4
+ * (device, double; no gate, no fallback). */
+hjm_status hjm_surrogate_premium(hjm_surrogate* s, const float* x, size_t n, double* premium_out,
+                                 void* cuda_stream);
+/* The closed-form part alone: the Gaussian-HJM caplet's forward premium
+ * C_gauss / P(0,T) of each row (device x [n][9], device double out [n]). */
+hjm_status hjm_surrogate_gauss_premium(const float* x, size_t n, double* premium_out, void* cuda_stream);
 /* Mean squared error of the scaled targets t and its gradient (device,
  * HJM_SURROGATE_PARAMS floats, layout W0 [256x9], b0, W1 [256x256], b1, W2,
  * b2, W3, b3, W4 [256], b4). loss_out: host float or NULL. */

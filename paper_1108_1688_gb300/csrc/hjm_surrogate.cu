@@ -6,9 +6,14 @@
 // Inputs x = (kappa, lambda, theta, epsilon, rho, T, delta, K, F): the model
 // parameters (gamma = 0, v0 = 1), expiry T, accrual delta = T_M - T, strike
 // K and the simple forward F of the curve over [T, T_M]. With gamma = 0 the
-// caplet price divided by P(0,T) depends on the curve only through F, so the
-// network learns q = C / (P(0,T) delta s0), s0 = 0.01, and reports the forward
-// premium C / P(0,T) = q delta s0; callers multiply by their P(0,T).
+// caplet price divided by P(0,T) depends on the curve only through F. The
+// forward premium C / P(0,T) splits into the Gaussian-HJM caplet (epsilon = 0:
+// v stays at v0 = 1 and the model is the Gaussian one of Section 3.1, whose
+// caplet is a put on the log-normal bond p(T,T_M), in closed form) and the
+// stochastic-volatility correction; the network learns only the correction,
+// q = (C - C_gauss) / (P(0,T) delta s_r), s_r = 1e-4, which carries the
+// epsilon, rho and theta dependence at order one, and reports the forward
+// premium C_gauss / P(0,T) + q delta s_r; callers multiply by their P(0,T).
 // Labels and fallback prices come from the march on a flat curve with that
 // forward (continuous rate c = ln(1 + F delta) / delta).
 //
@@ -35,11 +40,11 @@ hjm_status hjm_internal_fail(hjm_status s, const char* msg);
 
 namespace {
 
-constexpr double kPriceScale = 0.01;  // s0
+constexpr double kResidScale = 1e-4;  // s_r: the correction per unit accrual is at most a few 1e-4
 constexpr int kBinsT = 9, kBinsK = 8, kBins = kBinsT * kBinsK;
 constexpr double kGateTol = 1e-4;     // PDE-judged error accepted on C / P(0,T)
 constexpr double kGateSafety = 0.5;   // a bin answers when its held-out maximum is below half of it
-constexpr uint32_t kFileMagic = 0x484a4d53;  // "HJMS"
+constexpr uint32_t kFileMagic = 0x484a4d52;  // "HJMR": a network of the residual target
 
 hjm_status fail(hjm_status s, const char* msg) { return hjm_internal_fail(s, msg); }
 
@@ -98,28 +103,57 @@ __global__ void k_gather_rows(int rows, const int* __restrict__ idx, const float
     tb[r] = t[s];
 }
 
+// Forward premium C_gauss / P(0,T) of the Gaussian-HJM caplet (gamma = 0,
+// epsilon = 0, v = 1): ln p(T,T_M) is normal with standard deviation
+// sp = G(delta) sqrt(Var x(T)), G(s) = (1 - e^{-kappa s}) / kappa (the bond
+// formula of Section 3.1), Var x(T) = lambda^2 (1 - e^{-2 kappa T}) / (2 kappa),
+// and the caplet is Delta_M = 1 + delta K times a put on p(T,T_M) with strike
+// 1 / Delta_M; with P(0,T_M) / P(0,T) = 1 / (1 + F delta),
+//   C_gauss / P(0,T) = N(sp - h) - Delta_M / (1 + F delta) N(-h),
+//   h = ln(Delta_M / (1 + F delta)) / sp + sp / 2.
+__device__ double gauss_premium(double kap, double lam, double T, double dl, double K, double F)
+{
+    const double G = kap > 0.0 ? -expm1(-kap * dl) / kap : dl;
+    const double var = kap > 0.0 ? lam * lam * (-expm1(-2.0 * kap * T)) / (2.0 * kap) : lam * lam * T;
+    const double sp = G * sqrt(var);
+    const double a = (1.0 + dl * K) / (1.0 + F * dl);
+    const double h = log(a) / sp + 0.5 * sp;
+    return normcdf(sp - h) - a * normcdf(-h);
+}
+
+__global__ void k_gauss_premium(int rows, const float* __restrict__ x, double* __restrict__ out)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    const float* f = x + (size_t)r * kIn;
+    out[r] = gauss_premium(f[0], f[1], f[5], f[6], f[7], f[8]);
+}
+
 // Forward premium of a flat-curve caplet price: C / P(0,T), P(0,T) = e^{-cT},
-// c = ln(1 + F delta) / delta; `scaled` also divides by delta s0.
+// c = ln(1 + F delta) / delta; `scaled` gives the network's target instead,
+// (C / P(0,T) - C_gauss / P(0,T)) / (delta s_r).
 __global__ void k_forward_premium(int rows, const float* __restrict__ x, const double* __restrict__ C,
                                   float* __restrict__ qf, double* __restrict__ qd, int scaled)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    const double T = x[(size_t)r * kIn + 5], dl = x[(size_t)r * kIn + 6], F = x[(size_t)r * kIn + 8];
+    const float* f = x + (size_t)r * kIn;
+    const double T = f[5], dl = f[6], F = f[8];
     const double c = log1p(F * dl) / dl;
     double q = C[r] * exp(c * T);
-    if (scaled) q /= dl * kPriceScale;
+    if (scaled) q = (q - gauss_premium(f[0], f[1], T, dl, f[7], F)) / (dl * kResidScale);
     if (qf) qf[r] = (float)q;
     if (qd) qd[r] = q;
 }
 
-// Network output q -> forward premium q delta s0 (double).
+// Network output q -> forward premium C_gauss / P(0,T) + q delta s_r (double).
 __global__ void k_unscale(int rows, const float* __restrict__ x, const float* __restrict__ y,
                           double* __restrict__ out)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= rows) return;
-    out[r] = (double)y[r] * x[(size_t)r * kIn + 6] * kPriceScale;
+    const float* f = x + (size_t)r * kIn;
+    out[r] = gauss_premium(f[0], f[1], f[5], f[6], f[7], f[8]) + (double)y[r] * f[6] * kResidScale;
 }
 
 __device__ int bin_of(const float* f, const float* lo, const float* hi)
@@ -159,7 +193,7 @@ __global__ void k_bin_errors(int rows, const float* __restrict__ x, const float*
     for (int k = 0; k < kIn; ++k) f[k] = x[(size_t)r * kIn + k];
     f[7] -= f[8];
     const int b = bin_of(f, lo, hi);
-    const float err = fabsf(y[r] - t[r]) * f[6] * (float)kPriceScale;
+    const float err = fabsf(y[r] - t[r]) * f[6] * (float)kResidScale;
     atomicMax(reinterpret_cast<int*>(table + b), __float_as_int(err));
     atomicAdd(count + b, 1u);
 }
@@ -514,6 +548,33 @@ extern "C" hjm_status hjm_surrogate_forward(hjm_surrogate* s, const float* x, si
         if (r != HJM_OK) return r;
         SCU(cudaMemcpyAsync(y_out + r0, s->y.p, rows * sizeof(float), cudaMemcpyDeviceToDevice, st));
     }
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_surrogate_premium(hjm_surrogate* s, const float* x, size_t n, double* premium_out,
+                                            void* cuda_stream)
+{
+    if (!s || !x || !premium_out) return fail(HJM_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(s->mu);
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int chunk = 65536;
+    if (ensure_acts(s, (int)std::min<size_t>(n, chunk), false)) return fail(HJM_ENOMEM, "surrogate activations");
+    for (size_t r0 = 0; r0 < n; r0 += chunk) {
+        const int rows = (int)std::min<size_t>(chunk, n - r0);
+        hjm_status r = forward(s, x + r0 * kIn, rows, false, st);
+        if (r != HJM_OK) return r;
+        k_unscale<<<(rows + 255) / 256, 256, 0, st>>>(rows, x + r0 * kIn, s->y.p, premium_out + r0);
+        SCU(cudaGetLastError());
+    }
+    return HJM_OK;
+}
+
+extern "C" hjm_status hjm_surrogate_gauss_premium(const float* x, size_t n, double* premium_out, void* cuda_stream)
+{
+    if (!x || !premium_out) return fail(HJM_EINVAL, "null argument");
+    if (n == 0) return HJM_OK;
+    k_gauss_premium<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)cuda_stream>>>((int)n, x, premium_out);
+    SCU(cudaGetLastError());
     return HJM_OK;
 }
 

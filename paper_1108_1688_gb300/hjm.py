@@ -126,6 +126,8 @@ def _load():
         "hjm_tile_set": ([C.c_int, C.c_int, C.c_int, st, P(hjm_tile)], st),
         "hjm_autotune": ([P(hjm_batch_item), C.c_size_t, st, C.c_int, vp], st),
         "hjm_wait_status": ([st], st),
+        "hjm_surrogate_premium": ([vp, vp, C.c_size_t, vp, vp], st),
+        "hjm_surrogate_gauss_premium": ([vp, C.c_size_t, vp, vp], st),
         "hjm_price_strip": ([P(hjm_batch_item), C.c_size_t, st, C.c_double, P(C.c_double), P(C.c_double), vp], st),
         "hjm_test_drop_plane": ([C.c_int, C.c_uint], st),
         "hjm_status_string": ([st], C.c_char_p),
@@ -145,7 +147,8 @@ EXPORTED = ("hjm_grid_create", "hjm_grid_destroy", "hjm_price", "hjm_price_batch
             "hjm_surrogate_get_params", "hjm_surrogate_set_params", "hjm_surrogate_error_table",
             "hjm_surrogate_save", "hjm_surrogate_load", "hjm_surrogate_destroy", "hjm_mlp_gemm",
             "hjm_trace_enable", "hjm_trace_read", "hjm_tile_get", "hjm_tile_set", "hjm_autotune",
-            "hjm_wait_status", "hjm_test_drop_plane", "hjm_price_strip", "hjm_status_string",
+            "hjm_wait_status", "hjm_test_drop_plane", "hjm_price_strip", "hjm_surrogate_premium",
+            "hjm_surrogate_gauss_premium", "hjm_status_string",
             "hjm_last_error")
 
 
@@ -393,6 +396,20 @@ def hjm_surrogate_forward(h, x, y_out, stream=None):
     n = int(y_out.numel() if hasattr(y_out, "numel") else len(y_out))
     _check(lib.hjm_surrogate_forward(h, _ptr(x), n, _ptr(y_out), _stream(stream)))
     return y_out
+
+
+def hjm_surrogate_premium(h, x, premium_out, stream=None):
+    """The network alone as forward premia (Gaussian part + learned correction)."""
+    n = int(premium_out.numel() if hasattr(premium_out, "numel") else len(premium_out))
+    _check(lib.hjm_surrogate_premium(h, _ptr(x), n, _ptr(premium_out), _stream(stream)))
+    return premium_out
+
+
+def hjm_surrogate_gauss_premium(x, premium_out, stream=None):
+    """The closed-form Gaussian-HJM forward premium of each row."""
+    n = int(premium_out.numel() if hasattr(premium_out, "numel") else len(premium_out))
+    _check(lib.hjm_surrogate_gauss_premium(_ptr(x), n, _ptr(premium_out), _stream(stream)))
+    return premium_out
 
 
 def hjm_surrogate_loss_grad(h, x, t, grad_out, stream=None):
