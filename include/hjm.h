@@ -308,6 +308,9 @@ hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_precision pre
  * perceptron 9 -> 256 -> 256 -> 256 -> 256 -> 1 with SiLU activations; its
  * three 256 x 256 layers run on the tensor cores with bfloat16 operands and
  * FP32 accumulation (forward and backward), AdamW on FP32 master weights.
+ * Inference (hjm_surrogate_forward, _premium, _infer) runs all layers of a
+ * 128-row tile in one kernel on the fifth-generation tensor cores (tcgen05,
+ * accumulators in tensor memory); training runs them layer by layer.
  *
  * Inputs, per row (float, device, [n][9]): x = (kappa, lambda, theta,
  * epsilon, rho, T, delta, K, F) with gamma = 0 and v0 = 1: model parameters,
@@ -430,9 +433,11 @@ hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision precision,
                             void* cuda_stream);
 
 /* Bounded device-side waits (no counterpart in the paper). The TMA-fed pass
- * 1 (p1_staged = 2) waits on a barrier for each y plane it copies; a CTA
+ * 1 (p1_staged = 2, 3) waits on a barrier for each y plane it copies; a CTA
  * whose wait runs out of polls (the copy never arrived) stops without
- * writing the rest of its planes and is counted. hjm_wait_status
+ * writing the rest of its planes and is counted. The surrogate's fused
+ * tensor-core forward waits on a barrier for each layer's matrix products;
+ * a CTA whose wait runs out writes NaN for its rows and is counted too. hjm_wait_status
  * synchronises the current device and returns HJM_ETIMEOUT when any CTA has
  * given up since the last reset (reset != 0 clears the count), HJM_OK
  * otherwise; hjm_price and hjm_price_batch with host outputs check it

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "hjm_kernels.cuh"
+#include "hjm_mlp.cuh"
 
 using namespace hjm;
 
@@ -1321,9 +1322,12 @@ extern "C" hjm_status hjm_wait_status(int reset)
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
     CU_TRY(cudaDeviceSynchronize());
-    unsigned n = 0;
+    unsigned n = 0, m = 0;
     CU_TRY(pass1t_timeouts(&n, reset != 0));
-    return n ? fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n) : HJM_OK;
+    CU_TRY(mlp::forward_fused_timeouts(&m, reset != 0));
+    if (n) return fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n);
+    if (m) return fail(HJM_ETIMEOUT, "%u CTA(s) of the fused surrogate forward gave up waiting for the tensor cores", m);
+    return HJM_OK;
 }
 
 extern "C" hjm_status hjm_test_drop_plane(int plane, unsigned polls)

@@ -259,9 +259,15 @@ cudaError_t ensure_acts(hjm_surrogate* s, int rows, bool train)
     return cudaSuccess;
 }
 
-// Network forward on `rows` raw input rows x (device) into s->y.
+// Network forward on `rows` raw input rows x (device) into s->y. Inference
+// (keep = false) runs the fused tensor-core kernel; training keeps the
+// per-layer kernels, whose pre-activations the backward pass needs.
 hjm_status forward(hjm_surrogate* s, const float* x, int rows, bool keep, cudaStream_t st)
 {
+    if (!keep) {
+        SCU(forward_fused(rows, x, s->box.p, s->w.p, s->w16.p, s->y.p, st));
+        return HJM_OK;
+    }
     const float* W = s->w.p;
     const __nv_bfloat16* W16 = s->w16.p;
     const float* lo = s->box.p;
