@@ -193,7 +193,9 @@ def barrier(world):
 
 # ---------------------------------------------------------------- helpers
 
-MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu", "hjm_pass1t.cu")
+MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu", "hjm_pass1t.cu", "hjm_lines_t.cu",
+                 "hjm_tma.cuh")
+LINES_TMA = 15  # p2_warps / p3_warps code of the TMA-fed strided passes (HJM_LINES_TMA)
 
 
 def source_digest():
@@ -221,7 +223,7 @@ def kernel_name(kind, tile, prec="fp32", scheme=0):
     if tile is None:
         return "k_" + kind
     if kind == "pass1":
-        if tile[5] == 2:
+        if tile[5] in (2, 3):
             return "k_pass1t" + (" + k_pass1" if scheme else "")
         if tile[5] == 1:
             return "k_pass1s_r96" if prec == "fp32" and tile[1] <= 8 else "k_pass1s"
@@ -230,6 +232,8 @@ def kernel_name(kind, tile, prec="fp32", scheme=0):
         return "k_pass23"
     if kind in ("pass2", "pass3"):
         p = tile[3] if kind == "pass2" else tile[4]
+        if p == LINES_TMA:
+            return "k_lines_t"
         return "k_" + kind if p == 1 else "k_split_lines"
     return "k_" + kind
 

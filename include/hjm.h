@@ -257,7 +257,14 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * passes 2 and 3: a CTA holds the whole (v, y) plane of 8 consecutive r
  * nodes in shared memory and runs both line solves there (gamma = 0
  * groups, n_r * element size a multiple of 16, the plane within a CTA's
- * shared memory); p3_warps is then unused (1). Stepwise access
+ * shared memory); p3_warps is then unused (1). p2_warps / p3_warps =
+ * HJM_LINES_TMA: one lane per line, the lines moved in and out in tiles of
+ * 32 consecutive r nodes by the Tensor Memory Accelerator (one box copy in
+ * and one box store per tile, a persistent grid in which every warp marches
+ * its own tiles through a ring of shared-memory slots; FP32, n_r a multiple
+ * of 4, lines of at most 256 nodes; pass 3 in groups where every instrument
+ * has gamma = 0, the lane-per-line kernel otherwise; same results as 1,
+ * bit for bit). Stepwise access
  * (hjm_douglas_pass) always runs the passes separately. p1_staged selects how
  * pass 1 gets its five stencil rows: 0 straight from global memory, 1 a CTA
  * copies the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v nodes
@@ -276,6 +283,7 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * rounding of the line solves, nothing else.
  * tile_cfg in hjm_price_info packs p1_lanes | p1_nodes << 8 | p1_lines << 14
  * | p2_warps << 21 | p3_warps << 25 | p1_staged << 29. */
+#define HJM_LINES_TMA 15
 typedef struct {
     int p1_lanes;
     int p1_nodes;
@@ -422,9 +430,8 @@ hjm_status hjm_mlp_gemm(int M, int N, int K, const void* A, int lda, int trans_a
  *    HJM_ERANGE (FP64 fields of up to about 2^19 points per field fit, fewer
  *    with a Craig-Sneyd-family scheme, which holds a third field; the
  *    message states the bytes needed);
- *  - the first call on each device sets up the array's device address and the
- *    kernels' shared-memory limit; make that first call before any stream
- *    capture;
+ *  - the first call on each device looks up the array's device address and
+ *    sets the kernels' shared-memory limit;
  *  - every call shares the one array and leaves the last call's contents in
  *    it: calls that overlap on the GPU (different streams without ordering,
  *    or several host threads) race and give wrong prices; order them. */
@@ -435,16 +442,21 @@ hjm_status hjm_price_static(const hjm_batch_item* item, hjm_precision precision,
 /* Bounded device-side waits (no counterpart in the paper). The TMA-fed pass
  * 1 (p1_staged = 2, 3) waits on a barrier for each y plane it copies; a CTA
  * whose wait runs out of polls (the copy never arrived) stops without
- * writing the rest of its planes and is counted. The surrogate's fused
+ * writing the rest of its planes and is counted. The TMA-fed passes 2 and 3
+ * (HJM_LINES_TMA) wait on a barrier for each line tile; a warp whose wait
+ * runs out stops without writing the rest of its tiles and is counted. The
+ * surrogate's fused
  * tensor-core forward waits on a barrier for each layer's matrix products;
  * a CTA whose wait runs out writes NaN for its rows and is counted too. hjm_wait_status
  * synchronises the current device and returns HJM_ETIMEOUT when any CTA has
  * given up since the last reset (reset != 0 clears the count), HJM_OK
  * otherwise; hjm_price and hjm_price_batch with host outputs check it
  * themselves. hjm_test_drop_plane is a test hook: from the next launch on,
- * the copy of y plane `plane` (0 .. n_y - 1 of every instrument) is never
- * started and each wait gives up after `polls` polls; plane = -1 and polls
- * = 0 restore normal operation. */
+ * the copy of y plane `plane` (0 .. n_y - 1 of every instrument) in the
+ * TMA-fed pass 1, and of line tile `plane` of each launch of the TMA-fed
+ * passes 2 and 3 (tiles numbered r block fastest, then y plane (pass 2) or
+ * v node (pass 3), then instrument), is never started and each wait gives
+ * up after `polls` polls; plane = -1 and polls = 0 restore normal operation. */
 hjm_status hjm_wait_status(int reset);
 hjm_status hjm_test_drop_plane(int plane, unsigned polls);
 

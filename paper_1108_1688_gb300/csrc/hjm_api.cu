@@ -663,11 +663,14 @@ hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, siz
 // the march gave up since the last check.
 static hjm_status check_waits()
 {
-    unsigned n = 0;
+    unsigned n = 0, l = 0;
     CU_TRY(pass1t_timeouts(&n, false));
-    if (n == 0) return HJM_OK;
+    CU_TRY(lines_t_timeouts(&l, false));
+    if (n == 0 && l == 0) return HJM_OK;
     CU_TRY(pass1t_timeouts(&n, true));
-    return fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n);
+    CU_TRY(lines_t_timeouts(&l, true));
+    if (n) return fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n);
+    return fail(HJM_ETIMEOUT, "%u warp(s) of the TMA-fed strided passes gave up waiting for a line tile", l);
 }
 
 // Core of hjm_price_batch (caller holds g_mu, items validated).
@@ -1157,6 +1160,12 @@ extern "C" hjm_status hjm_autotune(const hjm_batch_item* items, size_t n, hjm_pr
                     t.p3_P = split_valid(ny, Pw) && !g.gpos ? Pw : 1;
                     cands.push_back(t);
                 }
+                {  // lines moved by TMA (FP32)
+                    Tile t = best;
+                    t.p2_P = lines_t_valid(0, nr, nv, ny, elem) ? kLinesTma : 1;
+                    t.p3_P = lines_t_valid(1, nr, nv, ny, elem) && !g.gpos ? kLinesTma : 1;
+                    if (t.p2_P == kLinesTma || t.p3_P == kLinesTma) cands.push_back(t);
+                }
                 best_ms[1] = best_ms[2] = 3.0e38f;
             }
             if (phase == 2) {
@@ -1322,10 +1331,12 @@ extern "C" hjm_status hjm_wait_status(int reset)
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
     CU_TRY(cudaDeviceSynchronize());
-    unsigned n = 0, m = 0;
+    unsigned n = 0, l = 0, m = 0;
     CU_TRY(pass1t_timeouts(&n, reset != 0));
+    CU_TRY(lines_t_timeouts(&l, reset != 0));
     CU_TRY(mlp::forward_fused_timeouts(&m, reset != 0));
     if (n) return fail(HJM_ETIMEOUT, "%u CTA(s) of the TMA-fed pass 1 gave up waiting for a plane copy", n);
+    if (l) return fail(HJM_ETIMEOUT, "%u warp(s) of the TMA-fed strided passes gave up waiting for a line tile", l);
     if (m) return fail(HJM_ETIMEOUT, "%u CTA(s) of the fused surrogate forward gave up waiting for the tensor cores", m);
     return HJM_OK;
 }
@@ -1337,7 +1348,9 @@ extern "C" hjm_status hjm_test_drop_plane(int plane, unsigned polls)
     hjm_status st = ensure_init();
     if (st != HJM_OK) return st;
     CU_TRY(cudaDeviceSynchronize());
-    CU_TRY(pass1t_test_drop(plane, plane < 0 || polls == 0 ? (1u << 22) : polls));
+    const unsigned lim = plane < 0 || polls == 0 ? (1u << 22) : polls;
+    CU_TRY(pass1t_test_drop(plane, lim));
+    CU_TRY(lines_t_test_drop(plane, lim));
     return HJM_OK;
 }
 

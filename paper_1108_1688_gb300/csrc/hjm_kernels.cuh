@@ -117,6 +117,18 @@ struct March {
                    // pass 1 applies)
 };
 
+// Rounding indicator: the largest |dU3| of step n on the 4 x 4 read-out
+// stencil of the y = 0 plane (non-negative floats order like their bits).
+template <typename T>
+__device__ __forceinline__ void note_increment(const March<T>& P, const int* fl, int b, int i, int k,
+                                               int n, T x0)
+{
+    if (P.acc == nullptr) return;
+    const int i0 = fl[FL_RI0], k0 = fl[FL_RK0];
+    if (i < i0 || i >= i0 + 4 || k < k0 || k >= k0 + 4) return;
+    atomicMax(reinterpret_cast<int*>(P.acc + (size_t)b * P.nsteps + n), __float_as_int(fabsf((float)x0)));
+}
+
 // Largest number of chunks a strided line is split into, and the largest
 // chunk a thread holds in registers.
 constexpr int kMaxSplit = 8;
@@ -190,8 +202,9 @@ struct Tile {
     int p1_S;  // pass 1: lanes per r line (8, 16, 32)
     int p1_M;  // pass 1: r nodes per lane; p1_S * p1_M >= n_r
     int p1_R;  // pass 1: lines per lane segment per CTA
-    int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8); 0: passes 2 and 3 fused
-    int p3_P;  // pass 3: warps sharing each y line (1, 2, 4, 8)
+    int p2_P;  // pass 2: warps sharing each v line (1, 2, 4, 8); 0: passes 2 and 3
+               // fused; kLinesTma: lines moved by TMA (k_lines_t)
+    int p3_P;  // pass 3: warps sharing each y line (1, 2, 4, 8); kLinesTma
     int p1_stage;  // pass 1: 0 rows from global memory, 1 staged y planes,
                    // 2 y planes staged by TMA (k_pass1t, FP32, gamma = 0)
     int p1_J;      // pass 1 staged: y planes marched per CTA (0 when not staged)
@@ -235,6 +248,22 @@ bool pass1t_valid(const Tile& t, int nr, int nv, int ny, size_t elem);
 cudaError_t launch_pass1t(const March<float>& P, const float* U, float* out, int n, const Tile& t,
                           cudaStream_t s);
 cudaError_t init_pass1t();
+// Strided passes fed by the Tensor Memory Accelerator (hjm_lines_t.cu), the
+// launch-shape code kLinesTma of p2_P / p3_P: FP32, n_r a multiple of 4,
+// lines of 2..256 nodes; pass 3 only for groups with gamma = 0 (the caller
+// falls back to the lane-per-line kernels otherwise, and when
+// launch_lines_t returns cudaErrorNotSupported: a field not 16-byte
+// aligned). axis 0: pass 2 (Un unused), axis 1: pass 3.
+constexpr int kLinesTma = 15;
+bool lines_t_valid(int axis, int nr, int nv, int ny, size_t elem);
+cudaError_t launch_lines_t(int axis, const March<float>& P, const float* in, const float* Un, float* out, int n,
+                           cudaStream_t s);
+cudaError_t init_lines_t();
+// Warps of the TMA-fed strided passes that gave up a wait (reset clears).
+cudaError_t lines_t_timeouts(unsigned* count, bool reset);
+// Test hook: from the next launch on, tile `tile` (-1: none) is never copied
+// and the waits give up after `limit` polls.
+cudaError_t lines_t_test_drop(long long tile, unsigned limit);
 // Reads (and with reset clears) the number of CTAs of the TMA-fed pass 1 that
 // gave up a wait on a plane copy; synchronises the device.
 cudaError_t pass1t_timeouts(unsigned* count, bool reset);

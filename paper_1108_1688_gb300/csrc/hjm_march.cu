@@ -19,7 +19,9 @@
 //   k_split_lines       2-8 warps per line, one chunk each, joined through a
 //                       precomputed reduced system (spike partition);
 //   k_pass23            passes 2 and 3 together on a shared-memory slab of
-//                       8 r nodes when its (v, y) plane fits.
+//                       8 r nodes when its (v, y) plane fits;
+//   k_lines_t           one lane per line, 32-line tiles moved in and out by
+//                       the Tensor Memory Accelerator (hjm_lines_t.cu).
 #include "hjm_kernels.cuh"
 
 namespace hjm {
@@ -82,18 +84,6 @@ __device__ __forceinline__ T gather_forward(T* col, int lane, const T* src, int 
         c[kk * 32] = dp;
     }
     return dp;
-}
-
-// Rounding indicator: the largest |dU3| of step n on the 4 x 4 read-out
-// stencil of the y = 0 plane (non-negative floats order like their bits).
-template <typename T>
-__device__ __forceinline__ void note_increment(const March<T>& P, const int* fl, int b, int i, int k,
-                                               int n, T x0)
-{
-    if (P.acc == nullptr) return;
-    const int i0 = fl[FL_RI0], k0 = fl[FL_RK0];
-    if (i < i0 || i >= i0 + 4 || k < k0 || k >= k0 + 4) return;
-    atomicMax(reinterpret_cast<int*>(P.acc + (size_t)b * P.nsteps + n), __float_as_int(fabsf((float)x0)));
 }
 
 // ------------------------------------------------------------------ pass 2
@@ -706,6 +696,7 @@ cudaError_t init_kernels()
 {
     cudaError_t e;
     if ((e = init_pass1())) return e;
+    if ((e = init_lines_t())) return e;
 #define SPLIT_ATTR(T_, MC_, AX_)                                                                             \
     if ((e = cudaFuncSetAttribute(k_split_lines<T_, MC_, AX_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                   (int)kSmemLimit)))                                                        \
@@ -732,7 +723,13 @@ cudaError_t init_kernels()
 template <typename T>
 cudaError_t launch_pass2(const March<T>& P, const T* in, T* out, cudaStream_t s)
 {
-    if (P.p2P > 1) {
+    if (P.p2P == kLinesTma) {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            const cudaError_t e = launch_lines_t(0, P, in, nullptr, out, 0, s);
+            if (e != cudaErrorNotSupported) return e;
+        }
+        // FP64 or a field not 16-byte aligned: one lane per line
+    } else if (P.p2P > 1) {
         if (!split_valid(P.nv, P.p2P)) return cudaErrorInvalidValue;
         return split_launch<T, 0>(P, in, nullptr, out, P.p2P, 0, s);
     }
@@ -747,8 +744,16 @@ template <typename T>
 cudaError_t launch_pass3(const March<T>& P, const T* in, const T* Un, T* out, bool any_gamma_pos,
                          int n, cudaStream_t s)
 {
-    // Split y lines need line-invariant y systems (gamma = 0 in the group).
-    if (P.p3P > 1 && !any_gamma_pos) {
+    // Split and TMA-fed y lines need line-invariant y systems (gamma = 0 in
+    // the group); otherwise one lane per line.
+    if (P.p3P == kLinesTma) {
+        if constexpr (sizeof(T) == sizeof(float)) {
+            if (!any_gamma_pos) {
+                const cudaError_t e = launch_lines_t(1, P, in, Un, out, n, s);
+                if (e != cudaErrorNotSupported) return e;
+            }
+        }
+    } else if (P.p3P > 1 && !any_gamma_pos) {
         if (!split_valid(P.ny, P.p3P)) return cudaErrorInvalidValue;
         return split_launch<T, 1>(P, in, Un, out, P.p3P, n, s);
     }

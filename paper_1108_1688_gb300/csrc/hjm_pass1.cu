@@ -818,14 +818,15 @@ static size_t p1s_smem(int nr, int S, int M, int RK, size_t elem)
 
 Tile default_tile(int nr, int nv, int ny, size_t elem)
 {
-    (void)nv;
-    (void)ny;
     Tile t{32, 16, 4, 1, 1, 0, 0};
-    // Heuristic table (the autotuner may replace it per grid shape).
+    // Heuristic table (the autotuner may replace it per grid shape); FP32
+    // strided lines moved by TMA wherever that kernel covers them.
     if (elem == 4) {
         if (nr <= 64) t = {8, 8, 4, 1, 1, 0, 0};
         else if (nr <= 128) t = {16, 8, 4, 1, 1, 0, 0};
         else if (nr <= 256) t = {32, 8, 4, 1, 1, 0, 0};
+        if (lines_t_valid(0, nr, nv, ny, elem)) t.p2_P = kLinesTma;
+        if (lines_t_valid(1, nr, nv, ny, elem)) t.p3_P = kLinesTma;
     } else {
         if (nr <= 32) t = {16, 2, 4, 1, 1, 0, 0};
         else if (nr <= 64) t = {16, 4, 4, 1, 1, 0, 0};
@@ -837,8 +838,10 @@ Tile default_tile(int nr, int nv, int ny, size_t elem)
 
 bool tile_valid(const Tile& t, int nr, int nv, int ny, size_t elem)
 {
-    if (!(split_valid(nv, t.p2_P) || pass23_valid(nr, nv, ny, t.p2_P, elem)) || !split_valid(ny, t.p3_P))
-        return false;
+    const bool p2ok = split_valid(nv, t.p2_P) || pass23_valid(nr, nv, ny, t.p2_P, elem) ||
+                      (t.p2_P == kLinesTma && lines_t_valid(0, nr, nv, ny, elem));
+    const bool p3ok = split_valid(ny, t.p3_P) || (t.p3_P == kLinesTma && lines_t_valid(1, nr, nv, ny, elem));
+    if (!p2ok || !p3ok) return false;
     if (t.p1_stage == 2 || t.p1_stage == 3) return pass1t_valid(t, nr, nv, ny, elem);
     if (!p1_compiled(elem, t.p1_S, t.p1_M) || t.p1_S * t.p1_M < nr || t.p1_R < 1 || t.p1_R > 64) return false;
     if (t.p1_stage == 0) return t.p1_J == 0;

@@ -31,14 +31,13 @@
 // fed with zeros). Every wait on a plane copy is bounded: a CTA whose wait
 // runs out counts itself in a device counter (read by pass1t_timeouts),
 // waits a bounded time for its other copies and leaves without writing.
-#include <cuda.h>  // CUtensorMap and the tensor-map encoder's signature
-
 #include <algorithm>
 #include <mutex>
 #include <utility>
 #include <vector>
 
 #include "hjm_kernels.cuh"
+#include "hjm_tma.cuh"
 
 namespace hjm {
 namespace {
@@ -71,39 +70,11 @@ __host__ __device__ inline int round128(int x) { return (x + 127) & ~127; }
 
 // ----------------------------------------------------- PTX: TMA, mbarrier
 
-__device__ __forceinline__ unsigned su32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
-}
-
-// Makes the initialised barriers visible to the asynchronous (TMA) proxy.
-__device__ __forceinline__ void fence_barrier_init()
-{
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n"
-        ".reg .pred p;\n"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        "selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
+using tma::su32;
+using tma::mbar_init;
+using tma::fence_barrier_init;
+using tma::mbar_expect_tx;
+using tma::mbar_try_wait;
 
 // One box (36 x NCH x rows x 1) of the 4-D view into shared memory at dst;
 // completion is signalled on bar. c0 is always 0 (16-byte aligned).
@@ -647,26 +618,8 @@ __global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<fl
 
 namespace {
 
-using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// The driver's tensor-map encoder, looked up once through the runtime (the
-// library does not link the driver library).
-EncodeTiled encoder()
-{
-    static EncodeTiled fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* f = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeTiled>(f);
-    });
-    return fn;
-}
+using tma::encoder;
+using tma::EncodeTiled;
 
 // 4-D view of a group's FP32 field U[b][j][k][i]: (i mod 32, i / 32, k,
 // b n_y + j), box (36, chunks, rows, 1) starting at x0 = 0 (16-byte aligned).

@@ -754,18 +754,20 @@ void tables_carve(GroupTables& g, void* block, size_t elem)
 cudaError_t launch_setup(const GroupTables& g, size_t elem, cudaStream_t s)
 {
     const dim3 faces(g.nsteps, g.B);
-    // p2P of 0 (passes 2 and 3 fused) or 1 needs no split factors for v
-    if (g.p2P < 0 || g.p2P > kMaxSplit || g.p3P < 1 || g.p3P > kMaxSplit) return cudaErrorInvalidValue;
+    // p2P of 0 (passes 2 and 3 fused), 1 or kLinesTma needs no split factors
+    auto ok = [](int P, int lo) { return (P >= lo && P <= kMaxSplit) || P == kLinesTma; };
+    if (!ok(g.p2P, 0) || !ok(g.p3P, 1)) return cudaErrorInvalidValue;
+    const bool sv = g.p2P > 1 && g.p2P <= kMaxSplit, sy = g.p3P > 1 && g.p3P <= kMaxSplit;
     if (elem == sizeof(float)) {
         k_setup<float><<<g.B, 256, 0, s>>>(g);
         k_faces<float><<<faces, 128, 0, s>>>(g);
-        if (g.p2P > 1) k_split<float><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
-        if (g.p3P > 1) k_split<float><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
+        if (sv) k_split<float><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
+        if (sy) k_split<float><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
     } else {
         k_setup<double><<<g.B, 256, 0, s>>>(g);
         k_faces<double><<<faces, 128, 0, s>>>(g);
-        if (g.p2P > 1) k_split<double><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
-        if (g.p3P > 1) k_split<double><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
+        if (sv) k_split<double><<<g.B, 32, 0, s>>>(g, 0, g.p2P);
+        if (sy) k_split<double><<<(unsigned)(g.B * g.nv), 32, 0, s>>>(g, 1, g.p3P);
     }
     return cudaGetLastError();
 }

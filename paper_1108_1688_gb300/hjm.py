@@ -29,6 +29,7 @@ PRECISIONS = {"fp64": HJM_FP64, "fp32": HJM_FP32, "mixed": HJM_MIXED,
 
 
 HJM_MAX_KNOTS = 32
+HJM_LINES_TMA = 15  # p2_warps / p3_warps: strided lines moved by the Tensor Memory Accelerator
 
 
 class hjm_curve(C.Structure):

@@ -89,6 +89,10 @@ def test_kernel_names_of_launch_shapes():
     assert bench.kernel_name("pass2", (16, 8, 8, 1, 4, 0, 0)) == "k_pass2"
     assert bench.kernel_name("pass3", (16, 8, 8, 1, 4, 0, 0)) == "k_split_lines"
     assert bench.kernel_name("pass3", (16, 8, 8, 0, 1, 0, 0)) == "k_pass23"
+    assert bench.kernel_name("pass1", (8, 16, 1, 1, 4, 2, 16)) == "k_pass1t"
+    assert bench.kernel_name("pass1", (16, 8, 1, 1, 4, 3, 0)) == "k_pass1t"
+    assert bench.kernel_name("pass2", (16, 8, 1, 15, 15, 3, 0)) == "k_lines_t"
+    assert bench.kernel_name("pass3", (16, 8, 1, 15, 15, 3, 0)) == "k_lines_t"
 
 
 def test_recorded_traffic_is_keyed_by_sources_and_launch_shape():

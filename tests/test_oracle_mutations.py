@@ -39,7 +39,8 @@ MUTATIONS = [
     ("v and y solves swapped", "orc_solve_dir(x, 1, th, a, b);\n    orc_solve_dir(x, 2, th, b, a);",
      "orc_solve_dir(x, 2, th, a, b);\n    orc_solve_dir(x, 1, th, b, a);"),
     ("Dirichlet data at t^n", "dU0[p] = orc_dirichlet(x, t1,", "dU0[p] = orc_dirichlet(x, t,"),
-    ("payoff kink sign", "double rstar = log(DA) / G;", "double rstar = -log(DA) / G;"),
+    ("payoff kink sign", "double rstar = log(DA) / G;\n    double mlo",
+     "double rstar = -log(DA) / G;\n    double mlo"),
     ("Delta_M without the strike", "x->DM = 1.0 + (in->TM - in->T) * x->K;", "x->DM = 1.0 + (in->TM - in->T);"),
     ("readout at the wrong v", "double xv = metric_xi(x, 1, x->m.v0) / x->h[1];",
      "double xv = metric_xi(x, 1, 0.5 * x->m.v0) / x->h[1];"),
