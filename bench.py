@@ -427,6 +427,17 @@ def run_surrogate(args):
                      for c, r in zip(C, x)])
     err = np.abs(got - want)
     ans = ~u
+    # discretisation error of the label grid: a sample of in-box rows priced
+    # on the label grid and on 128 x 64 x 64 with 256 steps (FP32; forward
+    # premia, the units of the errors above)
+    fine = W.surrogate_label_grid(128, 64, 64, 256)
+    xs = W.surrogate_draws(args.label_check, seed=W.SEED_BASE + 52)
+    fwd = np.array([math.exp(math.log1p(float(r[8]) * float(r[6])) / float(r[6]) * float(r[5])) for r in xs])
+    lab = np.concatenate([hjm.hjm_price_batch([W.surrogate_item(r, label) for r in xs[a:a + 1024]], "fp32")
+                          for a in range(0, len(xs), 1024)]) * fwd
+    ref = np.concatenate([hjm.hjm_price_batch([W.surrogate_item(r, fine) for r in xs[a:a + 1024]], "fp32")
+                          for a in range(0, len(xs), 1024)]) * fwd
+    gap = np.abs(lab - ref)
     line = {
         "metric": METRIC, "value": n_rows * args.steps / (ms * 1e-3), "unit": "caplet prices/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -447,7 +458,13 @@ def run_surrogate(args):
                       "max_err_fallback": float(err[u].max()) if u.any() else None,
                       "bins_under_gate": int((table <= 5e-5).sum()), "bins": int(table.size),
                       "network_ms_per_batch": round(net_ms, 4),
-                      "network_rows_per_s": n_rows / (net_ms * 1e-3)},
+                      "network_rows_per_s": n_rows / (net_ms * 1e-3),
+                      "error_table": [[float(v) if np.isfinite(v) else None for v in row]
+                                      for row in np.asarray(table).reshape(9, 8)],
+                      "label_grid_vs_128x64x64x256": {
+                          "rows": int(len(xs)), "max": float(gap.max()), "median": float(np.median(gap)),
+                          "p99": float(np.quantile(gap, 0.99)),
+                          "rows_over_1e-4": int((gap > 1e-4).sum())}},
     }
     hjm.hjm_surrogate_destroy(h)
     print(json.dumps(line))
@@ -500,7 +517,7 @@ def measure(wname, args, world, local, hjm):
     host_out = np.empty(n, dtype=np.float64)
 
     def step_dev():
-        hjm.hjm_price_batch(arr, prec, out=out, stream=stream)
+        hjm.hjm_price_batch(arr, prec, tol_rel=args.mixed_tol, out=out, stream=stream)
 
     tiles = _tiles_for_workload(hjm, items, prec, arr, stream, args)
     for _ in range(args.warmup):
@@ -528,7 +545,7 @@ def measure(wname, args, world, local, hjm):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        hjm.hjm_price_batch(arr, prec, out=host_out, stream=stream)  # syncs for the D2H read
+        hjm.hjm_price_batch(arr, prec, tol_rel=args.mixed_tol, out=host_out, stream=stream)  # syncs for the D2H read
     e2e_s = time.perf_counter() - t0
     e2e_max = reduce_max(e2e_s, world, device="cuda")
 
@@ -601,7 +618,7 @@ def measure(wname, args, world, local, hjm):
     if prec == "mixed":
         # how many instruments one call re-prices in FP64, and their launches
         # (the FP64 batch of those instruments, FP64 launch shapes)
-        _, infos = hjm.hjm_price_batch(arr, prec, out=host_out, infos=True, stream=stream)
+        _, infos = hjm.hjm_price_batch(arr, prec, tol_rel=args.mixed_tol, out=host_out, infos=True, stream=stream)
         redo = [x for x, inf in zip(items, infos) if inf.escalated]
         rg = {}
         for x in redo:
@@ -611,7 +628,7 @@ def measure(wname, args, world, local, hjm):
             rg[(g["n_r"], g["n_v"], g["n_y"], g["n_steps"])] = g["n_steps"] * per_stage * (2 if scheme else 1)
         if rg:
             launches_per_step += sum(3 + s for s in rg.values()) + 1
-        mixed = {"tol_rel": 1e-4, "escalated_per_step": len(redo),
+        mixed = {"tol_rel": args.mixed_tol, "escalated_per_step": len(redo),
                  "max_err_estimate": max(float(inf.err_estimate) for inf in infos)}
 
     line = {
@@ -700,6 +717,8 @@ def main(argv=None):
                     help="headline (default): the 256-caplet uneven batch, with the 100-caplet batch and the "
                          "512x256x256 caplet measured beside it")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64", "mixed"])
+    ap.add_argument("--mixed-tol", type=float, default=1e-4,
+                    help="MIXED: relative tolerance of the rounding bound (a small one forces FP64 re-pricing)")
     ap.add_argument("--scheme", default="douglas", choices=list(SCHEMES),
                     help="ADI scheme: the paper's Douglas, or Craig-Sneyd / modified CS / Hundsdorfer-Verwer")
     ap.add_argument("--ref-steps-per-step", type=int, default=2)
@@ -716,6 +735,8 @@ def main(argv=None):
     ap.add_argument("--labels", type=int, default=1 << 20, help="config5: PDE labels")
     ap.add_argument("--epochs", type=int, default=120, help="config5: training epochs")
     ap.add_argument("--label-grid", default="96x48x48x192", help="config5: label march n_r x n_y x n_v x steps")
+    ap.add_argument("--label-check", type=int, default=4096,
+                    help="config5: in-box rows priced on the label grid and on 128x64x64x256")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)

@@ -261,9 +261,11 @@ class Ctx:
         return self._L.orc_dirichlet(self._h, float(t), float(r), float(y))
 
 
-def price(item):
+def price(item, omp=False):
+    """Price of one item by the whole march (omp: the OpenMP build, same
+    results, for the benchmark-size cases)."""
     p = C.c_double()
-    st = lib().orc_price(C.byref(_fill(Curve, item["curve"])), C.byref(_fill(Model, item["model"])),
+    st = lib(omp).orc_price(C.byref(_fill(Curve, item["curve"])), C.byref(_fill(Model, item["model"])),
                          C.byref(_fill(Grid, item["grid"])), C.byref(_fill(Inst, item["inst"])),
                          C.byref(p))
     if st != 0:
