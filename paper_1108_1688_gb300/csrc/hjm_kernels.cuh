@@ -68,20 +68,22 @@ constexpr double kIndicatorC = 8.0;
 
 enum { RT_R, RT_IJ, RT_C1, RT_C4V, RT_C4B, RT_C3, RT_CY, RT_N };
 // Folded r tables of the TMA-fed pass 1 (gamma = 0 groups). With C1, C4V,
-// IJ, C4B, C3, CY the RT_ factors above, z the node's rate, dt the step and
-// theta the ADI weight, the kernel solves the r system divided by theta,
+// IJ, C4B the RT_ factors above, z the node's rate, dt the step and theta
+// the ADI weight, the kernel solves the r system divided by theta,
 //   a x_{i-1} + b x_i + c x_{i+1} = dt F / theta,
-//   a = s_I - v L,  c = -(v U + s_I),  b = B + 2 v E1,  s_I = (a_I + y) P + Q
-// (a_I = a(t^{n+1/2})), and forms the explicit r part from the undivided
-// second and first differences of U^n (no cancelling sums of large terms):
+//   a = s_I - v (E1 + E4),  c = -(v (E1 - E4) + s_I),  b = B + 2 v E1,
+//   s_I = (a_I + y) P + Q   (a_I = a(t^{n+1/2})),
+// and forms the explicit r part from the undivided second and first
+// differences of U^n (no cancelling sums of large terms):
 //   (dt/theta) A_r U = g1 d2U + g4 d1U + RT U,
-//   g1 = (v/theta) E1,  g4 = (a_F + y)/theta P + QT - (v/theta) E4.
-// So L = dt (C1 + C4V), U = dt (C1 - C4V), P = dt IJ, Q = dt C4B,
-// B = 1/theta + dt z, E1 = dt C1, E4 = dt C4V, QT = Q / theta,
-// RT = -dt z / theta; X and Y are the mixed-term and y-drift factors times
-// dt. The Dirichlet nodes (i = 0 and i = n_r - 1 when gamma = 0) carry zeros
-// and B = 1, so their rows are identity rows without a branch per node.
-enum { R2_L, R2_U, R2_P, R2_Q, R2_B, R2_E1, R2_E4, R2_QT, R2_RT, R2_X, R2_Y, R2_N };
+//   g1 = (v/theta) E1,  g4 = (a_F + y)/theta P + Q/theta - (v/theta) E4.
+// So P = dt IJ, Q = dt C4B, B = 1/theta + dt z, E1 = dt C1, E4 = dt C4V,
+// RT = -dt z / theta (a table of its own: 1/theta - B would cancel). With
+// gamma = 0 the mixed-term factor is P times the per-instrument SC_XP and
+// the y-drift factor the per-instrument SC_YL, so neither is a table. The
+// Dirichlet nodes (i = 0 and i = n_r - 1 when gamma = 0) carry zeros and
+// B = 1, so their rows are identity rows without a branch per node.
+enum { R2_P, R2_Q, R2_B, R2_E1, R2_E4, R2_RT, R2_N };
 enum { VT_V, VT_IJ, VT_G2, VT_G5, VT_FV, VT_N };
 enum { YT_Y, YT_IJ, YT_KY, YT_N };
 // Correction stage of the Craig-Sneyd family (all explicit operators at
@@ -91,8 +93,10 @@ enum { YT_Y, YT_IJ, YT_KY, YT_N };
 // he = 1 for HV (B = Y3), 0 otherwise (B = U^n). SC_CX = 1/2 - c1 is the
 // extra weight of the mixed term; on Dirichlet nodes Z0 - B = kd (g - U -
 // c1 E) with kd = (1 - he) / (1 - c1) (there E = g - U^n).
-// SC_ITH = 1 / theta (0 when theta = 0).
-enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_C1, SC_CX, SC_HE, SC_KD, SC_ITH, SC_N };
+// SC_ITH = 1 / theta (0 when theta = 0). SC_XP = lambda eps rho (n_v - 1) / 2
+// and SC_YL = dt lambda^2: the mixed-term factor over the r table P and the
+// y-drift factor of the TMA-fed pass 1 (gamma = 0).
+enum { SC_DT, SC_W, SC_IHR, SC_IHV, SC_IHY, SC_C1, SC_CX, SC_HE, SC_KD, SC_ITH, SC_XP, SC_YL, SC_N };
 enum { FL_RLO_DIR, FL_YORDER, FL_YLU, FL_RI0, FL_RK0, FL_PAD, FL_N };
 
 template <typename T>

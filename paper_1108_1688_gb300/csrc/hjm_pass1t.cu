@@ -111,10 +111,10 @@ namespace {
 
 // Per-plane scalars, stored as pairs (both components equal) so that the
 // paired instructions take them without a copy: (a(t^n) + y) / theta,
-// a(t^{n+1/2}) + y, 1 / (2 h_y J_y theta), -2 kappa y dt / (2 h_y J_y theta),
-// the y-face weights yA, yB of the neighbour planes ja, jb (A_y U =
-// g6 (yA (U_ja - U) + yB (U_jb - U))), and the Dirichlet data (g at r_min,
-// g at r_max).
+// a(t^{n+1/2}) + y, dt lambda^2 / (2 h_y J_y theta), -2 kappa y dt /
+// (2 h_y J_y theta), the y-face weights yA, yB of the neighbour planes ja,
+// jb (A_y U = g6 (yA (U_ja - U) + yB (U_jb - U))), the Dirichlet data (g at
+// r_min, g at r_max) and 1/theta.
 enum { PJ_AF = 0, PJ_AI = 2, PJ_IJY = 4, PJ_KYY = 6, PJ_YA = 8, PJ_YB = 10, PJ_G = 12, PJ_N = 16 };
 // Per-line scalars, as pairs: v, v / theta, -v, -v / theta, 2 v, the weights
 // of the v-neighbour rows' second difference (U_a - U) + (U_b - U) and
@@ -168,6 +168,10 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
     const float2 vy2 = mul2(v2, f2(j23.x, j23.y)), ky2 = f2(j23.z, j23.w);
     const float2 yA2 = f2(j45.x, j45.y), yB2 = f2(j45.z, j45.w);
     const float gLo = j67.x, gHi = j67.y;
+    const float2 ith2 = f2(j67.z, j67.w);  // 1/theta
+    // y drift g6 = (dt lambda^2 v - 2 kappa y dt) / (2 h_y J_y theta): one pair
+    // for the whole line (gamma = 0: no r dependence)
+    const float2 g6 = add2(vy2, ky2);
 
     // The line's U^n, and of its v-neighbour rows the second difference
     // (U_a - U) + (U_b - U) and the difference U_b - U_a.
@@ -221,10 +225,8 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
     for (int s = 0; s < Q; ++s) {
         const int q = (s & 1) ? Q - 1 - (s >> 1) : (s >> 1);  // 0, Q-1, 1, Q-2, ...
         const float* t = tl + 4 * q;
-        const float4 tL = lds4f(t + R2_L * TS), tU = lds4f(t + R2_U * TS), tP = lds4f(t + R2_P * TS);
-        const float4 tQ = lds4f(t + R2_Q * TS), tB = lds4f(t + R2_B * TS), tE1 = lds4f(t + R2_E1 * TS);
-        const float4 tE4 = lds4f(t + R2_E4 * TS), tQT = lds4f(t + R2_QT * TS), tRT = lds4f(t + R2_RT * TS);
-        const float4 tX = lds4f(t + R2_X * TS), tY = lds4f(t + R2_Y * TS);
+        const float4 tP = lds4f(t + R2_P * TS), tQ = lds4f(t + R2_Q * TS), tB = lds4f(t + R2_B * TS);
+        const float4 tE1 = lds4f(t + R2_E1 * TS), tE4 = lds4f(t + R2_E4 * TS), tRT = lds4f(t + R2_RT * TS);
         const float4 ya = lds4(pa + vo[q]), yb = lds4(pb + vo[q]);
 #pragma unroll
         for (int hh = 0; hh < 2; ++hh) {
@@ -232,24 +234,23 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
             const int h = (4 * q + 2 < H + 1) ? hh : 1 - hh;
             const int m = 4 * q + 2 * h;
 #define HJM_PR(v4) (h ? f2(v4.z, v4.w) : f2(v4.x, v4.y))
-            const float2 Pp = HJM_PR(tP), E1 = HJM_PR(tE1);
+            const float2 Pp = HJM_PR(tP), E1 = HJM_PR(tE1), E4 = HJM_PR(tE4), Qq = HJM_PR(tQ);
             const float2 u = f2(uc[m], uc[m + 1]);
             // r part: g1 d2U + g4 d1U + RT U
             const float2 d2 = f2(e[m + 1] - e[m], e[m + 2] - e[m + 1]);
             const float2 d1 = f2(e[m + 1] + e[m], e[m + 2] + e[m + 1]);
-            const float2 g4 = fma2(nvt2, HJM_PR(tE4), fma2(aF2, Pp, HJM_PR(tQT)));
+            const float2 g4 = fma2(nvt2, E4, fma2(aF2, Pp, mul2(ith2, Qq)));
             float2 acc = mul2(HJM_PR(tRT), u);
             acc = fma2(mul2(vt2, E1), d2, acc);
             acc = fma2(g4, d1, acc);
             // v part: cA (U_{v,a} - U) + cB (U_{v,b} - U)
             acc = fma2(cS2, f2(ws[m], ws[m + 1]), acc);
             acc = fma2(cD2, f2(wd[m], wd[m + 1]), acc);
-            // mixed r-v term: X vq (wd_{m+1} - wd_{m-1})
+            // mixed r-v term: X vq (wd_{m+1} - wd_{m-1}), X = P SC_XP (in vq)
             const float wm1 = m > 0 ? wd[m - 1] : wL;
             const float wp2 = m + 2 < M ? wd[m + 2] : wR;
-            acc = fma2(mul2(HJM_PR(tX), vq2), f2(wd[m + 1] - wm1, wp2 - wd[m]), acc);
+            acc = fma2(mul2(Pp, vq2), f2(wd[m + 1] - wm1, wp2 - wd[m]), acc);
             // y part: g6 (yA (U_{y,a} - U) + yB (U_{y,b} - U))
-            const float2 g6 = fma2(HJM_PR(tY), vy2, ky2);
             float2 ty;
             if constexpr (YIN)
                 ty = sub2(HJM_PR(yb), HJM_PR(ya));
@@ -257,9 +258,9 @@ __device__ __forceinline__ void p1t_line(const float* __restrict__ tl, const uns
                 ty = fma2(yB2, sub2(HJM_PR(yb), u), mul2(yA2, sub2(HJM_PR(ya), u)));
             acc = fma2(g6, ty, acc);
             // row of the r system at t^{n+1/2}, divided by theta
-            const float2 sI = fma2(aI2, Pp, HJM_PR(tQ));
-            const float2 a = fma2(nv2, HJM_PR(tL), sI);   // -lower
-            const float2 up = fma2(v2, HJM_PR(tU), sI);   // upper (c = -up)
+            const float2 sI = fma2(aI2, Pp, Qq);
+            const float2 a = fma2(nv2, add2(E1, E4), sI);   // -lower
+            const float2 up = fma2(v2, sub2(E1, E4), sI);   // upper (c = -up)
             const float2 b = fma2(tv2, E1, HJM_PR(tB));   // 1/theta - diag
 #undef HJM_PR
 #pragma unroll
@@ -424,11 +425,12 @@ __device__ __forceinline__ void plane_scalars(const March<float>& P, int b, int 
     const bool yin = j > 0 && j < ny - 1;
     const float yA = yin ? -1.f : (yord == 1 ? (j == 0 ? 2.f : -2.f) : (j == 0 ? 4.f : -4.f));
     const float yB = yin ? 1.f : (yord == 1 ? 0.f : (j == 0 ? -1.f : 1.f));
-    const float v[6] = {(aF + y) * ith, aI + y, iJy * ith, ky * iJy * dth, yA, yB};
+    // the y-drift factor dt lambda^2 (gamma = 0) folded into the v part of g6
+    const float v[6] = {(aF + y) * ith, aI + y, sc[SC_YL] * iJy * ith, ky * iJy * dth, yA, yB};
     for (int q = 0; q < 6; ++q) o[2 * q] = o[2 * q + 1] = v[q];
     o[PJ_G] = dir[j];
     o[PJ_G + 1] = dir[ny + j];
-    o[PJ_G + 2] = o[PJ_G + 3] = 0.f;
+    o[PJ_G + 2] = o[PJ_G + 3] = ith;
 }
 
 // Work: the units (instrument b, strip of KB = 4 (32/S) RK v lines, y plane
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<fl
         }
         if (b != cur_b || st != cur_st) {
             const float* sc = P.sc + (size_t)b * SC_N;
-            const float ith = sc[SC_ITH], dth = sc[SC_DT] * ith;
+            const float ith = sc[SC_ITH], dth = sc[SC_DT] * ith, xp = sc[SC_XP];
             const float* vt = P.vt + (size_t)b * VT_N * nv;
             for (int li = tid; li < KB; li += blockDim.x) {
                 const int k = min(k0 + li, k1 - 1);
@@ -526,8 +528,9 @@ __global__ void __launch_bounds__(128, P1tOcc<M>::value) k_pass1t(const March<fl
                 const float vq = vin ? v * vt[VT_IJ * nv + k] : 0.f;
                 const float cA = vin ? g2 - g5 : (k == 0 ? 4.f * fv : -4.f * fv);
                 const float cB = vin ? g2 + g5 : (k == 0 ? -fv : fv);
+                // the mixed term's factor X = P SC_XP: SC_XP rides on vq
                 const float w[8] = {v, v * ith, -v, -v * ith, 2.f * v, 0.5f * (cA + cB) * dth,
-                                    0.5f * (cB - cA) * dth, vq * ith};
+                                    0.5f * (cB - cA) * dth, vq * ith * xp};
                 float* o = lks + li * LK_N;
                 for (int q = 0; q < 8; ++q) o[2 * q] = o[2 * q + 1] = w[q];
             }

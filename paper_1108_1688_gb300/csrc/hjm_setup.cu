@@ -168,16 +168,14 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         rt[RT_C4B * nr + i] = (T)(-p.kappa * z / J * 0.5 * ihr);
         rt[RT_C3 * nr + i] = (T)(p.lambda * rg * p.eps * p.rho / J * 0.25 * ihr * ihv);
         rt[RT_CY * nr + i] = (T)(lam2 * r2g);
-        // folded tables (R2_L ..): zeros on the Dirichlet nodes, B = 1
+        // folded tables (R2_P ..): zeros on the Dirichlet nodes, B = 1
         T* r2 = (T*)g.r2 + (size_t)b * R2_N * nr;
         const bool dir = i == nr - 1 || (i == 0 && p.gamma == 0.0);
         const double dt = D.dt, ith = p.theta_adi > 0.0 ? 1.0 / p.theta_adi : 0.0;
         const double c1 = 0.5 * lam2 * r2g / (J * J) * ihr * ihr;
         const double c4v = 0.5 * lam2 * r2g * J2 / (J * J * J) * 0.5 * ihr;
         const double ij = 0.5 * ihr / J, c4b = -p.kappa * z / J * 0.5 * ihr;
-        const double f[R2_N] = {dt * (c1 + c4v), dt * (c1 - c4v), dt * ij, dt * c4b, ith + dt * z, dt * c1,
-                                dt * c4v, dt * c4b * ith, -dt * z * ith,
-                                dt * p.lambda * rg * p.eps * p.rho / J * 0.25 * ihr * ihv, dt * lam2 * r2g};
+        const double f[R2_N] = {dt * ij, dt * c4b, ith + dt * z, dt * c1, dt * c4v, -dt * z * ith};
         for (int q = 0; q < R2_N; ++q) r2[q * nr + i] = (T)(dir ? (q == R2_B ? 1.0 : 0.0) : f[q]);
     }
     // v axis: A_v = g2 d_vv + g5 d_v, g2 = zeta_vv / J^2,
@@ -220,6 +218,8 @@ __global__ void __launch_bounds__(256) k_setup(GroupTables g)
         sc[SC_HE] = (T)he;
         sc[SC_KD] = (T)((1.0 - he) / (1.0 - c1));
         sc[SC_ITH] = (T)(p.theta_adi > 0.0 ? 1.0 / p.theta_adi : 0.0);
+        sc[SC_XP] = (T)(p.lambda * p.eps * p.rho * 0.5 * (nv - 1));
+        sc[SC_YL] = (T)(D.dt * p.lambda * p.lambda);
         int* fl = g.fl + (size_t)b * FL_N;
         fl[FL_RLO_DIR] = p.gamma == 0.0;
         fl[FL_YORDER] = p.yorder;

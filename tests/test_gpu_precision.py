@@ -48,6 +48,23 @@ def test_indicator_bounds_fp32_error(H, orc):
     assert np.all(np.abs(p64 - want) <= 1e-10 * np.maximum(np.abs(want), 1e-3))
 
 
+def test_indicator_bounds_fp32_error_at_benchmark_size(H, orc):
+    # The safety factor C = 8 of the indicator was fitted on small grids;
+    # here three caplets of the 100-caplet benchmark batch at its full size
+    # (128 x 64 x 64, 400 steps) against the oracle (its OpenMP build, same
+    # results as the serial one): the indicator must still bound the FP32
+    # march's error, and MIXED at the stated 1e-4 keeps every FP32 price.
+    items = [W.config2_draws(100)[i] for i in (0, 50, 99)]
+    want = np.array([orc.price(x, omp=True) for x in items])
+    p32, inf = H.hjm_price_batch(items, "fp32", infos=True)
+    err = np.abs(p32 - want)
+    ind = np.array([inf[i].err_estimate for i in range(len(items))])
+    assert np.all(err <= ind), list(zip(err, ind))
+    assert np.all(ind <= 1e-4 * np.abs(p32)), list(zip(ind, p32))
+    pm, infm = H.hjm_price_batch(items, "mixed", tol_rel=1e-4, infos=True)
+    assert np.array_equal(pm, p32) and not any(infm[i].escalated for i in range(len(items)))
+
+
 def test_mixed_keeps_fp32_when_within_tolerance(H):
     items = W.config2_draws(4, seed=W.SEED_BASE + 41, n_r=48, n_y=16, n_v=16, n_steps=60)
     p32 = H.hjm_price_batch(items, "fp32")
