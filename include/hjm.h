@@ -45,9 +45,15 @@ typedef enum {
 
 /* Arithmetic of the time march. FP64: state, operator and solves in double.
  * FP32: state, operator and solves in float (set-up and read-out stay in
- * double). MIXED: the FP32 march for every instrument, then an FP64 re-run of
- * each instrument whose a-posteriori rounding indicator exceeds
- * max(tol_rel |price|, 1e-6); MIXED synchronises the stream. */
+ * double). MIXED: the FP32 march for every instrument; each instrument whose
+ * a-posteriori rounding indicator exceeds max(tol_rel |price|, 1e-6) (every
+ * instrument when tol_rel = 0) is priced again, a Douglas-scheme instrument
+ * first by the escalation march: FP32 increments on an FP64 state (each step
+ * splits U^n = hi + lo into its FP32 rounding and FP32 remainder, runs the
+ * FP32 step on both, the Dirichlet data split the same way, and adds both
+ * increments to U^n in double; about three FP32 steps of memory traffic per
+ * step), then in FP64 if its indicator still misses (and for the
+ * Craig-Sneyd family). MIXED synchronises the stream. */
 typedef enum { HJM_FP64 = 0, HJM_FP32 = 1, HJM_MIXED = 2 } hjm_precision;
 
 /* Initial forward curve f(0,t) (Section 2: p(0,T) = exp(-int_0^T f(0,s) ds)).
@@ -152,13 +158,18 @@ typedef struct {
 } hjm_instrument;
 
 /* Per-price report. err_estimate is the a-posteriori rounding indicator of
- * the march that produced the price: C u (|p| + sqrt(n_steps) max|U| +
- * sum_n max|dU3_n|), u the unit roundoff of the march type, the maxima over
- * the 4 x 4 read-out stencil on y = 0, C a safety factor calibrated against
- * the FP64 oracle. */
+ * the march that produced the price: C (u_op |p| + u_state sqrt(n_steps)
+ * max|U| + u_incr sum_n max|dU3_n|), the u the unit roundoffs of the
+ * operator's coefficients, the state and the increments (all that of the
+ * march type; for the escalation march of MIXED the FP32 one for the
+ * coefficients and increments and the FP64 one for the state), the maxima
+ * over the 4 x 4 read-out stencil on y = 0, C a safety factor calibrated
+ * against the FP64 oracle. */
 typedef struct {
-    int precision_used;       /* hjm_precision actually used for the price */
-    int escalated;            /* 1 if an FP32 result was replaced by FP64 */
+    int precision_used;       /* HJM_FP32 or HJM_FP64: the march's type; HJM_MIXED:
+                                 MIXED's escalation march (FP32 increments on an
+                                 FP64 state) */
+    int escalated;            /* 1 if the FP32 result was replaced */
     double err_estimate;
     int n_steps;
     float time_us;            /* device time of the whole call, microseconds */
@@ -181,8 +192,9 @@ hjm_status hjm_grid_destroy(hjm_grid* grid);
 /* Price one instrument (Sections 3.2, 5.1): FP64 setup on the device, the
  * Douglas march of n_steps steps in the requested precision, FP64 cubic
  * readout at r = f(0,0), v = v0, y = 0. Synchronises the grid's stream.
- * tol_rel: relative tolerance for the MIXED escalation (ignored otherwise).
- * price_out: host double. info_out may be NULL. */
+ * tol_rel: relative tolerance for the MIXED escalation (ignored otherwise;
+ * 0 re-prices every instrument by the escalation). price_out: host double.
+ * info_out may be NULL. */
 hjm_status hjm_price(hjm_grid* grid, const hjm_instrument* inst, hjm_precision precision,
                      double tol_rel, double* price_out, hjm_price_info* info_out);
 

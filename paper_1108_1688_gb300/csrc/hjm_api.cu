@@ -278,6 +278,14 @@ struct Group {
     void* U = nullptr;
     void* A = nullptr;
     void* Y = nullptr;  // Craig-Sneyd family: the first stage's result Y3
+    // MIXED's escalation march (FP32 increments on an FP64 state): the FP64
+    // state, the FP32 remainder field, a zero field, and the Dirichlet data
+    // in FP64 and as their FP32 remainder
+    void* U64 = nullptr;
+    void* D = nullptr;
+    void* Z = nullptr;
+    void* dir64 = nullptr;
+    void* dirlo = nullptr;
     double* prices = nullptr;
     double* ind = nullptr;     // rounding indicators
     double* greeks = nullptr;  // [2 B]: dC/dr, dC/dv at the read-out point
@@ -412,6 +420,42 @@ hjm_status group_sequence(const Group& g, size_t elem, cudaStream_t s)
     return HJM_OK;
 }
 
+// MIXED's escalation march of one Douglas group, FP32 increments on an FP64
+// state: each step splits U^n = hi + lo (hi its FP32 rounding, lo the FP32
+// remainder), runs the FP32 Douglas step on hi (with the FP32 Dirichlet
+// data) and on lo (with the data's FP32 remainder), each increment written
+// on its own (added to a zero field), and adds both to U^n in FP64. The step
+// is linear in (U^n, data), so hi + lo gives the step of U^n; the FP32
+// kernels see hi's neighbour differences exactly, and the state no longer
+// carries an FP32 rounding per step. About three FP32 steps of traffic.
+hjm_status group_sequence_x64(const Group& g, cudaStream_t s)
+{
+    const long long N = (long long)g.nr * g.nv * g.ny * g.t.B;
+    const long long F = (long long)g.t.B * g.nsteps * 2 * g.ny;
+    CU_TRY(launch_setup(g.t, sizeof(float), s));
+    CU_TRY(launch_faces64(g.t, (double*)g.dir64, s));
+    CU_TRY(launch_split64((const double*)g.dir64, (float*)g.t.dir, (float*)g.dirlo, F, s));
+    CU_TRY(launch_terminal(g.t, g.U64, sizeof(double), s));
+    CU_TRY(cudaMemsetAsync(g.Z, 0, (size_t)N * sizeof(float), s));
+    const March<float> P = march_args<float>(g.t);
+    March<float> Plo = P;
+    Plo.dir = (const float*)g.dirlo;
+    float* hi = (float*)g.U;
+    float* lo = (float*)g.D;
+    float* A = (float*)g.A;
+    const float* Z = (const float*)g.Z;
+    for (int n = 0; n < g.nsteps; ++n) {
+        CU_TRY(launch_split64((const double*)g.U64, hi, lo, N, s));
+        hjm_status st = adi_stage<float>(P, hi, nullptr, A, Z, hi, g.gpos, g.tile, n, s, true);
+        if (st != HJM_OK) return st;
+        st = adi_stage<float>(Plo, lo, nullptr, A, Z, lo, g.gpos, g.tile, n, s, true);
+        if (st != HJM_OK) return st;
+        CU_TRY(launch_update64((double*)g.U64, hi, lo, N, s));
+    }
+    CU_TRY(launch_readout(g.t, g.U64, sizeof(double), g.prices, g.ind, g.greeks, s, true));
+    return HJM_OK;
+}
+
 // The whole batch as one CUDA-graph launch: every shape group is a branch of
 // the graph (fork from one node, join into one), so groups of different
 // sizes run concurrently and fill the GPU together. Captured the second time
@@ -507,7 +551,8 @@ bool is_device_ptr(const void* p)
 // Plan the groups of a batch and carve their buffers out of the workspace.
 hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
                 std::vector<Group>& groups, InstParams** d_params, long long** d_idx,
-                double** d_prices_all, double** d_ind_all = nullptr, double** d_greeks_all = nullptr)
+                double** d_prices_all, double** d_ind_all = nullptr, double** d_greeks_all = nullptr,
+                bool x64 = false)
 {
     // Groups hold at most kMaxGroup instruments (the set-up kernels index
     // instruments with the grid's y dimension).
@@ -544,6 +589,10 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
         const size_t N = (size_t)g.nr * g.nv * g.ny;
         bytes += (g.scheme != HJM_SCHEME_DOUGLAS ? 3 : 2) * align256(B * N * elem) +
                  tables_bytes(g.nr, g.nv, g.ny, g.nsteps, (int)B, elem);
+        if (x64) {
+            const size_t F = B * g.nsteps * 2 * g.ny;
+            bytes += align256(B * N * 8) + 2 * align256(B * N * 4) + align256(F * 8) + align256(F * 4);
+        }
     }
     const void* old = ws.block.ptr;
     cudaError_t e = ws.block.ensure(bytes);
@@ -580,6 +629,20 @@ hjm_status plan(Workspace& ws, const hjm_batch_item* items, size_t n, size_t ele
             g.Y = p;
             p += align256(B * N * elem);
         }
+        g.U64 = g.D = g.Z = g.dir64 = g.dirlo = nullptr;
+        if (x64) {
+            const size_t F = B * g.nsteps * 2 * g.ny;
+            g.U64 = p;
+            p += align256(B * N * 8);
+            g.D = p;
+            p += align256(B * N * 4);
+            g.Z = p;
+            p += align256(B * N * 4);
+            g.dir64 = p;
+            p += align256(F * 8);
+            g.dirlo = p;
+            p += align256(F * 4);
+        }
         g.t.nr = g.nr;
         g.t.nv = g.nv;
         g.t.ny = g.ny;
@@ -612,8 +675,11 @@ Workspace* stream_workspace(cudaStream_t s)
 // stream s. On return *d_prices and *d_ind (device, caller order, inside the
 // workspace) will hold the prices and rounding indicators once the stream
 // reaches them. Caller holds g_mu and has validated the items.
+// x64: MIXED's escalation march (FP32 increments on an FP64 state, Douglas
+// items only; elem is then sizeof(float)), groups in turn, no graph.
 hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, size_t elem,
-                       cudaStream_t s, double** d_prices_out, double** d_ind_out, double** d_greeks_out = nullptr)
+                       cudaStream_t s, double** d_prices_out, double** d_ind_out, double** d_greeks_out = nullptr,
+                       bool x64 = false)
 {
     std::vector<Group> groups;
     InstParams* d_params;
@@ -621,7 +687,7 @@ hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, siz
     double* d_prices;
     double* d_ind;
     double* d_greeks;
-    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices, &d_ind, &d_greeks);
+    hjm_status st = plan(ws, items, n, elem, groups, &d_params, &d_idx, &d_prices, &d_ind, &d_greeks, x64);
     if (st != HJM_OK) return st;
     // Parameters in group order, and the scatter map back to caller order.
     std::vector<InstParams> hp;
@@ -635,7 +701,12 @@ hjm_status march_batch(Workspace& ws, const hjm_batch_item* items, size_t n, siz
         }
     CU_TRY(cudaMemcpyAsync(d_params, hp.data(), n * sizeof(InstParams), cudaMemcpyHostToDevice, s));
     CU_TRY(cudaMemcpyAsync(d_idx, order.data(), n * sizeof(long long), cudaMemcpyHostToDevice, s));
-    if (g_trace_on) {
+    if (x64) {
+        for (auto& g : groups) {
+            st = group_sequence_x64(g, s);
+            if (st != HJM_OK) return st;
+        }
+    } else if (g_trace_on) {
         for (auto& g : groups) {
             st = group_sequence(g, elem, s);
             if (st != HJM_OK) return st;
@@ -676,8 +747,11 @@ static hjm_status check_waits()
 // Core of hjm_price_batch (caller holds g_mu, items validated).
 //  FP32 / FP64: one march in that precision.
 //  MIXED: the FP32 march; every instrument whose rounding indicator exceeds
-//  max(tol_rel |p|, 1e-6) (or whose price is not finite) is priced again in
-//  FP64 and reported as escalated. MIXED synchronises the stream.
+//  max(tol_rel |p|, 1e-6) (or whose price is not finite; every instrument
+//  when tol_rel = 0) is priced again, Douglas items first by the escalation
+//  march (FP32 increments on an FP64 state) and, where that bound still
+//  misses, like the Craig-Sneyd family, in FP64; they are reported as
+//  escalated. MIXED synchronises the stream.
 hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm_precision prec,
                        double tol_rel, double* prices_out, hjm_price_info* infos, cudaStream_t s)
 {
@@ -710,11 +784,47 @@ hjm_status price_batch(Workspace& ws, const hjm_batch_item* items, size_t n, hjm
         if (st != HJM_OK) return st;
     }
     if (prec == HJM_MIXED) {
+        auto misses = [&](double p, double ind) { return !isfinite(p) || !(ind <= fmax(tol_rel * fabs(p), 1e-6)); };
+        // first the escalation march for the Douglas items that miss
+        std::vector<hjm_batch_item> mid;
+        std::vector<size_t> at;
+        for (size_t i = 0; i < n; ++i)
+            if ((tol_rel == 0.0 || misses(hp[i], hi[i])) && items[i].grid.scheme == HJM_SCHEME_DOUGLAS) {
+                mid.push_back(items[i]);
+                at.push_back(i);
+            }
+        if (!mid.empty()) {
+            double* d_gm = nullptr;
+            st = march_batch(ws, mid.data(), mid.size(), sizeof(float), s, &d_prices, &d_ind, infos ? &d_gm : nullptr,
+                             true);
+            if (st != HJM_OK) return st;
+            std::vector<double> pm(mid.size()), im(mid.size()), gm(infos ? 2 * mid.size() : 0);
+            CU_TRY(cudaMemcpyAsync(pm.data(), d_prices, mid.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaMemcpyAsync(im.data(), d_ind, mid.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            if (infos)
+                CU_TRY(cudaMemcpyAsync(gm.data(), d_gm, 2 * mid.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+            CU_TRY(cudaStreamSynchronize(s));
+            if (g_trace_on) trace_collect();
+            st = check_waits();
+            if (st != HJM_OK) return st;
+            for (size_t q = 0; q < mid.size(); ++q) {
+                const size_t i = at[q];
+                hp[i] = pm[q];
+                hi[i] = im[q];
+                used[i] = HJM_MIXED;
+                esc[i] = 1;
+                if (infos) {
+                    hg[2 * i] = gm[2 * q];
+                    hg[2 * i + 1] = gm[2 * q + 1];
+                }
+            }
+        }
+        // then FP64 for what still misses (and the Craig-Sneyd family)
         std::vector<hjm_batch_item> redo;
         std::vector<size_t> where;
         for (size_t i = 0; i < n; ++i) {
-            const double lim = fmax(tol_rel * fabs(hp[i]), 1e-6);
-            if (!isfinite(hp[i]) || !(hi[i] <= lim)) {
+            const bool first = !(used[i] == HJM_MIXED);
+            if (first ? (tol_rel == 0.0 || misses(hp[i], hi[i])) : misses(hp[i], hi[i])) {
                 redo.push_back(items[i]);
                 where.push_back(i);
             }

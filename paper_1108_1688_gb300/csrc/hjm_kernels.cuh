@@ -198,7 +198,14 @@ cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStre
 // is not null also the a-posteriori rounding indicator of the march; when
 // greeks is not null also dC/dr and dC/dv at the read-out point ([B][2]).
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           double* indicators, double* greeks, cudaStream_t s);
+                           double* indicators, double* greeks, cudaStream_t s, bool incr32 = false);
+// The escalation march of MIXED (FP32 increments on an FP64 state): the state
+// split into its FP32 rounding and the FP32 remainder, U = hi + lo, and the
+// FP64 update U += x1 + x2 (count values each).
+cudaError_t launch_split64(const double* U, float* hi, float* lo, long long count, cudaStream_t s);
+// Dirichlet data of every step (the faces table) in FP64 into dir64.
+cudaError_t launch_faces64(const GroupTables& g, double* dir64, cudaStream_t s);
+cudaError_t launch_update64(double* U, const float* x1, const float* x2, long long count, cudaStream_t s);
 
 // Launch shapes of the three passes for one grid shape (heuristic default or
 // picked by the autotuner).

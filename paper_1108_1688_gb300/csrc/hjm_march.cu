@@ -680,6 +680,48 @@ cudaError_t launch_pass23(const March<T>& P, const T* in, const T* Un, T* out, i
     return cudaGetLastError();
 }
 
+// ------------------------------------- MIXED: FP32 increments, FP64 state
+
+// U = hi + lo with hi = fl32(U) and lo = fl32(U - hi): the FP32 march of hi
+// sees its neighbour differences exactly (they are FP32 numbers), and the
+// march of lo carries the part of the state FP32 cannot hold.
+__global__ void k_split64(const double* __restrict__ U, float* __restrict__ hi, float* __restrict__ lo,
+                          long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const double u = U[i];
+        const float h = (float)u;
+        hi[i] = h;
+        lo[i] = (float)(u - (double)h);
+    }
+}
+
+// U^{n+1} = U^n + (x1 + x2) in FP64.
+__global__ void k_update64(double* __restrict__ U, const float* __restrict__ x1, const float* __restrict__ x2,
+                           long long n)
+{
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        U[i] += (double)x1[i] + (double)x2[i];
+}
+
+static unsigned elementwise_grid(long long n)
+{
+    const long long b = (n + 255) / 256;
+    return (unsigned)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+cudaError_t launch_split64(const double* U, float* hi, float* lo, long long count, cudaStream_t s)
+{
+    k_split64<<<elementwise_grid(count), 256, 0, s>>>(U, hi, lo, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_update64(double* U, const float* x1, const float* x2, long long count, cudaStream_t s)
+{
+    k_update64<<<elementwise_grid(count), 256, 0, s>>>(U, x1, x2, count);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------- launchers
 
 static const size_t kSmemLimit = 227 * 1024;

@@ -621,7 +621,8 @@ __global__ void __launch_bounds__(128) k_terminal(GroupTables g, T* U)
 // Lagrange interpolation in the computational coordinates on the 4 x 4
 // nodes nearest the point, kept inside the grid.
 template <typename T>
-__global__ void k_readout(GroupTables g, const T* U, double* prices, double* indicators, double* greeks)
+__global__ void k_readout(GroupTables g, const T* U, double* prices, double* indicators, double* greeks,
+                          double u_op, double u_state, double u_incr)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= g.B) return;
@@ -685,15 +686,16 @@ __global__ void k_readout(GroupTables g, const T* U, double* prices, double* ind
     }
     if (indicators) {
         // A-posteriori rounding indicator of the march (reading of the
-        // precision-control step): unit roundoff of the march type times the
-        // price, the random-walk growth of the per-step rounding of U over
-        // the stencil, and the summed per-step increments on the stencil.
+        // precision-control step): the unit roundoff of the operator's
+        // coefficients times the price, that of the state times the
+        // random-walk growth of the per-step rounding of U over the stencil,
+        // and that of the increments times the summed per-step increments on
+        // the stencil.
         double umax = 0.0, incr = 0.0;
         for (int c = 0; c < 4; ++c)
             for (int a = 0; a < 4; ++a) umax = fmax(umax, fabs((double)Ub[(long long)(k0 + c) * nr + i0 + a]));
         for (int n = 0; n < g.nsteps; ++n) incr += (double)g.acc[(size_t)b * g.nsteps + n];
-        const double u = sizeof(T) == 4 ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
-        indicators[b] = kIndicatorC * u * (fabs(s) + sqrt((double)g.nsteps) * umax + incr);
+        indicators[b] = kIndicatorC * (u_op * fabs(s) + u_state * sqrt((double)g.nsteps) * umax + u_incr * incr);
     }
 }
 
@@ -782,14 +784,25 @@ cudaError_t launch_terminal(const GroupTables& g, void* U, size_t elem, cudaStre
     return cudaGetLastError();
 }
 
+cudaError_t launch_faces64(const GroupTables& g, double* dir64, cudaStream_t s)
+{
+    GroupTables h = g;
+    h.dir = dir64;
+    k_faces<double><<<dim3(g.nsteps, g.B), 128, 0, s>>>(h);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_readout(const GroupTables& g, const void* U, size_t elem, double* prices,
-                           double* indicators, double* greeks, cudaStream_t s)
+                           double* indicators, double* greeks, cudaStream_t s, bool incr32)
 {
     const int blocks = (g.B + 63) / 64;
+    const double u32 = 5.9604644775390625e-08, u64 = 1.1102230246251565e-16;
     if (elem == sizeof(float))
-        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices, indicators, greeks);
+        k_readout<float><<<blocks, 64, 0, s>>>(g, (const float*)U, prices, indicators, greeks, u32, u32, u32);
+    else if (incr32)  // FP32 operator and increments on an FP64 state
+        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators, greeks, u32, u64, u32);
     else
-        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators, greeks);
+        k_readout<double><<<blocks, 64, 0, s>>>(g, (const double*)U, prices, indicators, greeks, u64, u64, u64);
     return cudaGetLastError();
 }
 

@@ -89,9 +89,39 @@ def test_mixed_escalates_exactly_the_flagged_items(H, torch_dev):
     got = out.cpu().numpy()
     for i in range(len(items)):
         if flagged[i]:
-            assert got[i] == p64[i] and inf[i].escalated == 1 and inf[i].precision_used == H.HJM_FP64
+            # the escalation march (FP32 increments on an FP64 state), or FP64
+            # where its bound still misses
+            assert inf[i].escalated == 1 and inf[i].precision_used in (H.HJM_MIXED, H.HJM_FP64)
+            if inf[i].precision_used == H.HJM_FP64:
+                assert got[i] == p64[i]
+            else:
+                assert abs(got[i] - p64[i]) <= inf[i].err_estimate
+                assert inf[i].err_estimate <= max(tol * abs(got[i]), 1e-6)
         else:
             assert got[i] == p32[i] and inf[i].escalated == 0 and inf[i].precision_used == H.HJM_FP32
+
+
+def test_escalation_march_against_the_oracle(H, orc):
+    # tol_rel = 0 sends every instrument through the escalation: the Douglas
+    # ones through the march of FP32 increments on an FP64 state, whose
+    # indicator must bound its error against the oracle and whose error must
+    # be well below the FP32 march's; a Craig-Sneyd item goes to FP64.
+    items = _instruments()
+    cs = W.with_grid(W.config2_draws(1, seed=W.SEED_BASE + 43, n_r=48, n_y=16, n_v=16, n_steps=40)[0],
+                     scheme=1, theta_adi=0.5)
+    items.append(cs)
+    want = np.array([orc.price(x) for x in items])
+    p32 = H.hjm_price_batch(items, "fp32")
+    pm, inf = H.hjm_price_batch(items, "mixed", tol_rel=0.0, infos=True)
+    err32, errm = np.abs(p32 - want), np.abs(pm - want)
+    ind = np.array([i.err_estimate for i in inf])
+    used = [i.precision_used for i in inf]
+    assert all(i.escalated == 1 for i in inf)
+    assert used[-1] == H.HJM_FP64 and pm[-1] == H.hjm_price_batch([cs], "fp64")[0]
+    assert all(u == H.HJM_MIXED for u in used[:-1]), used
+    assert np.all(errm[:-1] <= ind[:-1]), list(zip(errm, ind))
+    # the state no longer carries an FP32 rounding per step
+    assert errm[:-1].sum() <= 0.25 * err32[:-1].sum(), (errm.sum(), err32.sum())
 
 
 def test_single_price_mixed(H):
@@ -100,7 +130,11 @@ def test_single_price_mixed(H):
     with H.Grid(long_bond) as g:
         p64 = g.price("fp64")
         pm, info = H.hjm_price(g.h, long_bond["inst"], "mixed", tol_rel=1e-9, with_info=True)
-        assert pm == p64 and info.escalated == 1
+        assert info.escalated == 1
+        if info.precision_used == H.HJM_FP64:
+            assert pm == p64
+        else:  # the escalation march, within its bound of the FP64 march
+            assert info.precision_used == H.HJM_MIXED and abs(pm - p64) <= info.err_estimate <= 1e-6
 
 
 @pytest.fixture(scope="module")
