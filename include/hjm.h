@@ -273,10 +273,11 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * HJM_LINES_TMA: one lane per line, the lines moved in and out in tiles of
  * 32 consecutive r nodes by the Tensor Memory Accelerator (one box copy in
  * and one box store per tile, a persistent grid in which every warp marches
- * its own tiles through a ring of shared-memory slots; FP32, n_r a multiple
- * of 4, lines of at most 256 nodes; pass 3 in groups where every instrument
- * has gamma = 0, the lane-per-line kernel otherwise; same results as 1,
- * bit for bit). Stepwise access
+ * its own tiles through a ring of shared-memory slots; pass 3 in place adds
+ * dU3 to U^n with a reduction store, so U^n is not staged; FP32, n_r a
+ * multiple of 4, lines of at most 256 nodes; pass 3 in groups where every
+ * instrument has gamma = 0, the lane-per-line kernel otherwise; same results
+ * as 1, bit for bit). Stepwise access
  * (hjm_douglas_pass) always runs the passes separately. p1_staged selects how
  * pass 1 gets its five stencil rows: 0 straight from global memory, 1 a CTA
  * copies the y planes of a strip of 4 * (32 / p1_lanes) * p1_lines v nodes

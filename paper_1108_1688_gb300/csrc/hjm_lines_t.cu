@@ -167,7 +167,10 @@ __device__ __forceinline__ bool warp_wait(unsigned bar, unsigned par)
 
 // AXIS 0: pass 2 (in: dU1 as a 3-D view (n_r, n_v, B n_y), out: dU2, the
 // same view); AXIS 1: pass 3 (in: dU2 and un: U^n as 4-D views (n_r, n_v,
-// n_y, B), out: U^{n+1}). R slots per warp, blockDim.x / 32 warps per CTA.
+// n_y, B), out: U^{n+1}); AXIS 2: pass 3 in place (out = un = U): the tile
+// of dU3 is added to U by the box store itself (a reduction store), so U^n
+// is never staged and a warp needs half the shared memory. R slots per
+// warp, blockDim.x / 32 warps per CTA.
 template <int AXIS>
 __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __grid_constant__ CUtensorMap tin,
                                                   const __grid_constant__ CUtensorMap tun,
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
     const int nr = P.nr, nv = P.nv, ny = P.ny;
     const int L = AXIS == 0 ? nv : ny;   // nodes per line
     const int colB = L * kRowB;          // one block of 32 lines
-    const int slotB = AXIS == 0 ? colB : 2 * colB;
+    const int slotB = AXIS == 1 ? 2 * colB : colB;
     const int facB = fac_bytes(L);       // one factor buffer: (sub, 1/pivot) pairs, then c'
     const unsigned bar0 = tma::su32(sm) + 32u * (unsigned)warp;
     unsigned char* slots = sm + kHeader + (size_t)warp * (R * slotB + 2 * facB);
@@ -209,6 +212,9 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         if constexpr (AXIS == 0) {
             tma::mbar_expect_tx(bar, (unsigned)colB);
             tma::load3(dst, &tin, x0, 0, (int)r, bar);
+        } else if constexpr (AXIS == 2) {
+            tma::mbar_expect_tx(bar, (unsigned)colB);
+            tma::load4(dst, &tin, x0, (int)(r % nv), 0, (int)(r / nv), bar);
         } else {
             tma::mbar_expect_tx(bar, 2u * (unsigned)colB);
             tma::load4(dst, &tin, x0, (int)(r % nv), 0, (int)(r / nv), bar);
@@ -270,6 +276,9 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
             const bool dir = i == nr - 1 || (i == 0 && fl[FL_RLO_DIR]);  // identity system
             if constexpr (AXIS == 0) {
                 if (!dir) line_solve<false>(col, nullptr, fp, fc, nv);
+            } else if constexpr (AXIS == 2) {  // dU3 (dU2 itself on an identity line), added by the store
+                if (!dir) line_solve<false>(col, nullptr, fp, fc, ny);
+                note_increment(P, fl, b, i, m, n, col[0]);
             } else {
                 const float* u = col + ny * 32;
                 if (dir) {
@@ -288,6 +297,8 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
             const int x0 = (int)(t % rt) * 32;
             if constexpr (AXIS == 0)
                 tma::store3(&tout, x0, 0, (int)r, src);
+            else if constexpr (AXIS == 2)
+                tma::reduce_add4(&tout, x0, m, 0, b, src);
             else
                 tma::store4(&tout, x0, m, 0, b, src);
             tma::bulk_commit();
@@ -336,7 +347,7 @@ cudaError_t lines_map(CUtensorMap* m, const float* U, const March<float>& P, int
 // many warps (4, 2, 1) as fit; two slots when one warp of three does not fit.
 size_t lines_smem(int axis, int L, int W, int R)
 {
-    const size_t per_warp = (size_t)R * L * kRowB * (axis == 0 ? 1 : 2) + 2 * (size_t)fac_bytes(L);
+    const size_t per_warp = (size_t)R * L * kRowB * (axis == 1 ? 2 : 1) + 2 * (size_t)fac_bytes(L);
     return (size_t)kHeader + (size_t)W * per_warp + 128;  // + alignment slack
 }
 
@@ -362,7 +373,8 @@ bool lines_shape(int axis, int L, int& W, int& R)
     return best > 0;
 }
 
-// Resident CTAs of the kernel at this shape times the SM count, cached.
+// Resident CTAs of the kernel (kind 0, 1, 2 as the template argument) at
+// this shape times the SM count, cached.
 int lines_grid(int axis, int W, size_t smem)
 {
     static std::mutex mu;
@@ -380,9 +392,10 @@ int lines_grid(int axis, int W, size_t smem)
     for (const auto& c : cache)
         if (c.first == key) return c.second;
     int nb = 0;
-    const cudaError_t e = axis == 0
-                              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<0>, 32 * W, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<1>, 32 * W, smem);
+    const cudaError_t e =
+        axis == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<0>, 32 * W, smem)
+        : axis == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<1>, 32 * W, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<2>, 32 * W, smem);
     if (e != cudaSuccess) return 0;
     cache.emplace_back(key, nb * sms);
     return nb * sms;
@@ -410,16 +423,21 @@ cudaError_t launch_lines_t(int axis, const March<float>& P, const float* in, con
     if (e == cudaSuccess) e = lines_map(&mu, axis == 0 ? in : Un, P, axis);
     if (e == cudaSuccess) e = lines_map(&mo, out, P, axis);
     if (e != cudaSuccess) return e;
+    // pass 3 in place (the Douglas stage: U^{n+1} over U^n) adds dU3 to U by
+    // the reduction store; otherwise U^n is staged next to dU2
+    const int kind = axis == 0 ? 0 : (Un == out ? 2 : 1);
     int W, R;
-    lines_shape(axis, axis == 0 ? P.nv : P.ny, W, R);
-    const size_t smem = lines_smem(axis, axis == 0 ? P.nv : P.ny, W, R);
+    lines_shape(kind, axis == 0 ? P.nv : P.ny, W, R);
+    const size_t smem = lines_smem(kind, axis == 0 ? P.nv : P.ny, W, R);
     const long long ntile = (long long)P.B * (axis == 0 ? P.ny : P.nv) * ((P.nr + 31) / 32);
-    const long long grid = std::min<long long>((ntile + W - 1) / W, lines_grid(axis, W, smem));
+    const long long grid = std::min<long long>((ntile + W - 1) / W, lines_grid(kind, W, smem));
     if (grid < 1) return cudaErrorInvalidConfiguration;
-    if (axis == 0)
+    if (kind == 0)
         k_lines_t<0><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
-    else
+    else if (kind == 1)
         k_lines_t<1><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
+    else
+        k_lines_t<2><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
     return cudaGetLastError();
 }
 
@@ -428,6 +446,8 @@ cudaError_t init_lines_t()
     cudaError_t e = cudaFuncSetAttribute(k_lines_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_lines_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lines_t<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
 

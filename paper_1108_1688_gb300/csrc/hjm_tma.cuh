@@ -93,6 +93,17 @@ __device__ __forceinline__ void store4(const CUtensorMap* tm, int c0, int c1, in
                  : "memory");
 }
 
+// The same box added element by element to the tensor's values (FP32 add in
+// the memory system, round to nearest); tracked like store4.
+__device__ __forceinline__ void reduce_add4(const CUtensorMap* tm, int c0, int c1, int c2, int c3, unsigned src)
+{
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.4d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
+            reinterpret_cast<unsigned long long>(tm)),
+        "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+        : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 
 // Until at most one of this thread's bulk groups still reads shared memory.
