@@ -23,8 +23,9 @@ rank runs its own replica of the batch on its own GPU (weak scaling); value =
 all ranks' grid-point-steps / the slowest rank's time.
 
 --precision fp64 marches in FP64; --precision mixed marches in FP32 and
-re-prices in FP64 the instruments whose rounding bound misses 1e-4 (the
-count is reported in config.mixed).
+re-prices the instruments whose rounding bound misses --mixed-tol (default
+1e-4; 0 re-prices every instrument) by FP32 increments on an FP64 state, in
+FP64 where even that misses (the count is reported in config.mixed).
 
 cpu_baseline and --impl reference time the CPU FP64 oracle (the plain C
 reference written from the paper; its OpenMP build shares the lines of each
