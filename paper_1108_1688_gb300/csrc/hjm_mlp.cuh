@@ -57,9 +57,11 @@ cudaError_t adamw(size_t n, float* w, float* m, float* v, const float* g, float 
 cudaError_t to_bf16(size_t n, const float* a, __nv_bfloat16* b, cudaStream_t s);
 // Inference forward of the whole network in one tcgen05 kernel
 // (hjm_mlp_tc.cu): y [rows] from raw inputs x [rows][9], the box [2][9], the
-// FP32 parameters P (biases, W0, W4) and their bfloat16 copy P16 (W1..W3).
+// FP32 parameters P (biases, W0, W4) and their bfloat16 copy P16 (W1..W3);
+// packed: scratch of 3 x 256 x 256 bfloat16 values (the three layers'
+// weights re-ordered for bulk copies, rewritten by every call).
 cudaError_t forward_fused(int rows, const float* x, const float* box, const float* P, const __nv_bfloat16* P16,
-                          float* y, cudaStream_t s);
+                          __nv_bfloat16* packed, float* y, cudaStream_t s);
 // CTAs of forward_fused whose bounded wait on the tensor cores ran out.
 cudaError_t forward_fused_timeouts(unsigned* count, bool reset);
 

@@ -96,18 +96,32 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// The same load split in two: the request, and the wait, which names the
+// registers the request fills (so that no use of them moves above it).
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
         "%14, %15}, [%16];\n"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[16])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
+// 8 floats from 32-byte-aligned shared memory.
+__device__ __forceinline__ void ld8(const float* p, float (&v)[8])
+{
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 4);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
 }
 
 // SiLU with the hardware exponential and an approximate division (a few
@@ -123,32 +137,52 @@ __device__ __forceinline__ void st16(unsigned char* p, const float (&v)[8])
     *reinterpret_cast<uint4*>(p) = *reinterpret_cast<uint4*>(h);
 }
 
-// Copies a layer's bfloat16 weights W[n][k] (row-major, K contiguous) into
-// the canonical layout with asynchronous 16-byte copies (no registers; they
-// travel while the epilogue runs). Thread order follows the destination
-// (conflict-free stores; each group of 8 threads reads 8 rows' 16-byte
-// pieces). Completed by cp.async.wait_all.
-__device__ __forceinline__ void copy_weights(uint32_t sW_a, const __nv_bfloat16* __restrict__ W)
+// Chunk d (16 bytes) of a layer's weights in the canonical layout holds
+// W[n][8c .. 8c + 7], n = 8 (d >> 8) + (d & 7), c = (d >> 3) & 31: the
+// order of the copy below (and of the packed weights, k_pack_weights).
+__device__ __forceinline__ void chunk_source(int d, int& n, int& c)
 {
-    for (int d = threadIdx.x; d < kWidth * kWidth / 8; d += kThr) {
-        const int n = (d >> 8) * 8 + (d & 7), c = (d >> 3) & 31;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sW_a + (uint32_t)d * 16),
-                     "l"(W + (size_t)n * kWidth + c * 8)
-                     : "memory");
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    n = (d >> 8) * 8 + (d & 7);
+    c = (d >> 3) & 31;
 }
 
-__device__ __forceinline__ void copies_done() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// One layer's packed weights (128 KB, already in the shared-memory order)
+// into sW by four bulk copies of 32 KB, completion (bytes) on the mbarrier.
+__device__ __forceinline__ void load_weights(uint32_t sW_a, const __nv_bfloat16* __restrict__ Wp, uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(kWBytes) : "memory");
+    for (int i = 0; i < 4; ++i)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                sW_a + (uint32_t)i * (kWBytes / 4)),
+            "l"(Wp + (size_t)i * (kWidth * kWidth / 4)), "r"(kWBytes / 4), "r"(bar)
+            : "memory");
+}
+
 
 __device__ __forceinline__ const __nv_bfloat16* layer_weights(const __nv_bfloat16* P16, int l)
 {
     return P16 + (l == 0 ? kOffW1 : (l == 1 ? kOffW2 : kOffW3));
 }
 
+// The three 256 x 256 layers' bfloat16 weights into the shared-memory
+// order of the MMA operand (packed[l] = 8192 chunks of 16 bytes), so that
+// a layer arrives by a few bulk copies instead of 8192 per-thread copies.
+__global__ void k_pack_weights(const __nv_bfloat16* __restrict__ P16, __nv_bfloat16* __restrict__ packed)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * kWidth * kWidth / 8) return;
+    const int l = i / (kWidth * kWidth / 8), d = i % (kWidth * kWidth / 8);
+    int n, c;
+    chunk_source(d, n, c);
+    const uint4 v = *reinterpret_cast<const uint4*>(layer_weights(P16, l) + (size_t)n * kWidth + c * 8);
+    *reinterpret_cast<uint4*>(packed + (size_t)l * kWidth * kWidth + (size_t)d * 8) = v;
+}
+
 __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __restrict__ x,
                                                       const float* __restrict__ box, const float* __restrict__ P,
-                                                      const __nv_bfloat16* __restrict__ P16, float* __restrict__ y)
+                                                      const __nv_bfloat16* __restrict__ P16p,
+                                                      float* __restrict__ y)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* sm = smem_raw + ((1024u - (su32(smem_raw) & 1023u)) & 1023u);
@@ -156,7 +190,7 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
     unsigned char* sW = sm + kABytes;
     float* aux = reinterpret_cast<float*>(sm + kABytes + kWBytes);
     float* sB = aux;                         // b1, b2, b3
-    float* sW0 = sB + 3 * kWidth;            // W0 [256 x 9]
+    float* sW0 = sB + 3 * kWidth;            // W0 transposed, [9][256]: 8 outputs' weights of an input in 32 bytes
     float* sb0 = sW0 + kWidth * kIn;
     float* sW4 = sb0 + kWidth;
     float* sb4 = sW4 + kWidth;
@@ -165,11 +199,11 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
     float* ypart = shi + kIn;                // [3][128] partial output dot products
     unsigned long long* bar = reinterpret_cast<unsigned long long*>(
         (reinterpret_cast<uintptr_t>(ypart + 3 * kTM) + 15) & ~(uintptr_t)15);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2);  // bar[0]: MMAs done, bar[1]: weights landed
     int* stop = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t bar_a = su32(bar);
+    const uint32_t bar_a = su32(bar), wbar_a = bar_a + 8u;
     for (int i = tid; i < kWidth; i += kThr) {
         sB[i] = P[kOffB1 + i];
         sB[kWidth + i] = P[kOffB2 + i];
@@ -177,7 +211,7 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
         sb0[i] = P[kOffB0 + i];
         sW4[i] = P[kOffW4 + i];
     }
-    for (int i = tid; i < kWidth * kIn; i += kThr) sW0[i] = P[kOffW0 + i];
+    for (int i = tid; i < kWidth * kIn; i += kThr) sW0[(i % kIn) * kWidth + i / kIn] = P[kOffW0 + i];
     if (tid < kIn) {
         slo[tid] = box[tid];
         shi[tid] = box[kIn + tid];
@@ -186,7 +220,9 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
         sb4[0] = P[kOffB4];
         *stop = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(bar_a) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(wbar_a) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     }
     if (warp == 0) {  // the accumulator's tensor memory (one warp allocates)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(su32(tmem_slot)),
@@ -207,7 +243,12 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
     const uint32_t t_row = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(64 * cq);
 
     const int tiles = (rows + kTM - 1) / kTM;
-    if (blockIdx.x < tiles) copy_weights(sW_a, layer_weights(P16, 0));  // the first tile's first layer
+    // thread 0: weight loads issued and completions seen (parity of the next)
+    unsigned w_issued = 0, w_seen = 0;
+    if (tid == 0 && blockIdx.x < tiles) {  // the first tile's first layer
+        load_weights(sW_a, P16p, wbar_a);
+        ++w_issued;
+    }
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int row0 = tile * kTM;
         // input layer (FP32): row r = tid % 128, the 64 outputs 64 (tid / 128) ..
@@ -221,60 +262,86 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
 #pragma unroll
             for (int k = 0; k < kIn; ++k) f[k] = 2.0f * (f[k] - slo[k]) / (shi[k] - slo[k]) - 1.0f;
             for (int c8 = 0; c8 < 8; ++c8) {
+                // 8 outputs: bias and weights as 16-byte vectors (the same
+                // addresses across the warp), the sums in the order b + sum_k
+                const int o0 = qt * 64 + c8 * 8;
                 float h[8];
+                ld8(sb0 + o0, h);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int o = qt * 64 + c8 * 8 + q;
-                    float z = sb0[o];
+                for (int k = 0; k < kIn; ++k) {
+                    float w[8];
+                    ld8(sW0 + k * kWidth + o0, w);
 #pragma unroll
-                    for (int k = 0; k < kIn; ++k) z += sW0[o * kIn + k] * f[k];
-                    h[q] = silu_f(z);
+                    for (int q = 0; q < 8; ++q) h[q] += w[q] * f[k];
                 }
-                st16(sA + op_off(r, qt * 64 + c8 * 8), h);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) h[q] = silu_f(h[q]);
+                st16(sA + op_off(r, o0), h);
             }
         }
         for (int l = 0; l < 3; ++l) {
-            copies_done();  // this layer's weights have landed (this thread's copies)
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // operands visible to the MMA
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                // this layer's weights have landed (bounded wait)
+                bool wok = false;
+                for (unsigned it = 0; it < kPolls && !wok; ++it) wok = bar_try(wbar_a, w_seen & 1u);
+                if (wok) {
+                    ++w_seen;
 #pragma unroll
-                for (int kk = 0; kk < kWidth / 16; ++kk)
-                    mma_f16(tmem, smem_desc(sA_a + kk * 2 * kLBO), smem_desc(sW_a + kk * 2 * kLBO), kk > 0);
-                mma_commit(bar_a);
+                    for (int kk = 0; kk < kWidth / 16; ++kk)
+                        mma_f16(tmem, smem_desc(sA_a + kk * 2 * kLBO), smem_desc(sW_a + kk * 2 * kLBO), kk > 0);
+                } else {
+                    atomicExch(stop, 1);
+                }
+                mma_commit(bar_a);  // (with no MMA after a failed wait: completes at once)
             }
-            bool ok = false;
-            for (unsigned it = 0; it < kPolls && !ok; ++it) ok = bar_try(bar_a, phase);
+            // one warp watches the barrier (bounded), the others wait at the
+            // CTA barrier instead of polling shared memory beside the MMAs
+            if (warp == 0) {
+                bool ok = false;
+                for (unsigned it = 0; it < kPolls && !ok; ++it) ok = bar_try(bar_a, phase);
+                if (!__all_sync(0xffffffffu, ok) && lane == 0) atomicExch(stop, 1);
+            }
             phase ^= 1u;
-            if (!ok) atomicExch(stop, 1);
             __syncthreads();
             if (*stop) break;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             // the weight buffer is free: the next layer's weights (the next
             // tile's first layer after the last) travel during the epilogue
-            copy_weights(sW_a, layer_weights(P16, l == 2 ? 0 : l + 1));
+            if (tid == 0 && (l < 2 || tile + (int)gridDim.x < tiles)) {
+                load_weights(sW_a, P16p + (size_t)(l == 2 ? 0 : l + 1) * kWidth * kWidth, wbar_a);
+                ++w_issued;
+            }
             const float* bias = sB + l * kWidth;
             float part = 0.0f;
+            // accumulator columns 16 at a time; the next 16 are requested
+            // before the current 16 are processed (one wait per block)
+            uint32_t v[2][16];
+            tmem_ld16_issue(t_row, v[0]);
+            tmem_ld_wait(v[0]);
 #pragma unroll
             for (int cb = 0; cb < 4; ++cb) {
-                float v[16];
-                tmem_ld16(t_row + 16 * cb, v);
+                if (cb + 1 < 4) tmem_ld16_issue(t_row + 16 * (cb + 1), v[(cb + 1) & 1]);
                 const int col0 = 64 * cq + 16 * cb;
 #pragma unroll
                 for (int hh = 0; hh < 2; ++hh) {
-                    float h[8];
+                    float h[8], bb[8];
+                    ld8(bias + col0 + 8 * hh, bb);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) h[q] = silu_f(v[8 * hh + q] + bias[col0 + 8 * hh + q]);
+                    for (int q = 0; q < 8; ++q) h[q] = silu_f(__uint_as_float(v[cb & 1][8 * hh + q]) + bb[q]);
                     if (l < 2) {
                         st16(sA + op_off(r_ep, col0 + 8 * hh), h);
                     } else {  // output layer: FP32 dot with the bfloat16-rounded activations
+                        float w4[8];
+                        ld8(sW4 + col0 + 8 * hh, w4);
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            part += sW4[col0 + 8 * hh + q] * __bfloat162float(__float2bfloat16_rn(h[q]));
+                        for (int q = 0; q < 8; ++q) part += w4[q] * __bfloat162float(__float2bfloat16_rn(h[q]));
                     }
                 }
+                if (cb + 1 < 4) tmem_ld_wait(v[(cb + 1) & 1]);
             }
             if (l == 2) {
                 if (cq > 0) ypart[(cq - 1) * kTM + r_ep] = part;
@@ -292,7 +359,10 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
             break;
         }
     }
-    copies_done();  // no copy left in flight into this CTA's shared memory
+    if (tid == 0 && w_issued > w_seen) {  // no copy left in flight into this CTA's shared memory
+        bool wok = false;
+        for (unsigned it = 0; it < kPolls && !wok; ++it) wok = bar_try(wbar_a, w_seen & 1u);
+    }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (warp == 0) {
@@ -305,7 +375,7 @@ __global__ void __launch_bounds__(kThr, 1) k_mlp_fused(int rows, const float* __
 }  // namespace
 
 cudaError_t forward_fused(int rows, const float* x, const float* box, const float* P, const __nv_bfloat16* P16,
-                          float* y, cudaStream_t s)
+                          __nv_bfloat16* packed, float* y, cudaStream_t s)
 {
     static int sms = 0;
     if (sms == 0) {
@@ -321,7 +391,8 @@ cudaError_t forward_fused(int rows, const float* x, const float* box, const floa
     }
     if (rows <= 0) return cudaSuccess;
     const int tiles = (rows + kTM - 1) / kTM;
-    k_mlp_fused<<<tiles < sms ? tiles : sms, kThr, kSmem, s>>>(rows, x, box, P, P16, y);
+    k_pack_weights<<<(3 * kWidth * kWidth / 8 + 255) / 256, 256, 0, s>>>(P16, packed);
+    k_mlp_fused<<<tiles < sms ? tiles : sms, kThr, kSmem, s>>>(rows, x, box, P, packed, y);
     return cudaGetLastError();
 }
 

@@ -221,6 +221,7 @@ struct hjm_surrogate {
     std::vector<float> lo, hi;  // feature box (float)
     DBuf<float> w, m, v, g, box, table, loss;
     DBuf<__nv_bfloat16> w16;
+    DBuf<__nv_bfloat16> w16p;  // W1..W3 packed for the fused inference kernel's bulk copies
     long long step = 0;
     int epoch = 0;
     Rng rng{0};
@@ -265,7 +266,8 @@ cudaError_t ensure_acts(hjm_surrogate* s, int rows, bool train)
 hjm_status forward(hjm_surrogate* s, const float* x, int rows, bool keep, cudaStream_t st)
 {
     if (!keep) {
-        SCU(forward_fused(rows, x, s->box.p, s->w.p, s->w16.p, s->y.p, st));
+        SCU(s->w16p.ensure((size_t)3 * kWidth * kWidth));
+        SCU(forward_fused(rows, x, s->box.p, s->w.p, s->w16.p, s->w16p.p, s->y.p, st));
         return HJM_OK;
     }
     const float* W = s->w.p;
@@ -511,6 +513,7 @@ extern "C" hjm_status hjm_surrogate_destroy(hjm_surrogate* s)
         s->H[l].release();
     }
     s->w16.release();
+    s->w16p.release();
     s->dZha.release();
     s->dZhb.release();
     s->idx.release();
