@@ -133,6 +133,15 @@ __device__ __forceinline__ void note_increment(const March<T>& P, const int* fl,
     atomicMax(reinterpret_cast<int*>(P.acc + (size_t)b * P.nsteps + n), __float_as_int(fabsf((float)x0)));
 }
 
+// The same with the instrument's read-out corner (FL_RI0, FL_RK0) given.
+template <typename T>
+__device__ __forceinline__ void note_increment_at(const March<T>& P, int i0, int k0, int b, int i, int k, int n,
+                                                  T x0)
+{
+    if (P.acc == nullptr || i < i0 || i >= i0 + 4 || k < k0 || k >= k0 + 4) return;
+    atomicMax(reinterpret_cast<int*>(P.acc + (size_t)b * P.nsteps + n), __float_as_int(fabsf((float)x0)));
+}
+
 // Largest number of chunks a strided line is split into, and the largest
 // chunk a thread holds in registers.
 constexpr int kMaxSplit = 8;

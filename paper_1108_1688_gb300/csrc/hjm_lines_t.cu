@@ -279,10 +279,17 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         }
         cp_commit();
     };
+    // the q-th tile's instrument flags (r_min Dirichlet, read-out corner),
+    // read a tile ahead so that the load's latency hides behind a solve
+    auto flags = [&](int q) {
+        const int* f = P.fl + (size_t)((gw + (long long)q * NW) / rt / mid) * FL_N;
+        return make_int3(f[FL_RLO_DIR], f[FL_RI0], f[FL_RK0]);
+    };
     int issued = min(R, cnt);  // tiles whose copy has been started (0 .. issued - 1)
     if (lane == 0)
         for (int q = 0; q < issued; ++q) issue(q);
     issue_factors(0);
+    int3 fnext = flags(0);
 
     for (int q = 0; q < cnt; ++q) {
         const unsigned s = (unsigned)(q % R);
@@ -307,6 +314,8 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         cp_wait_all();  // this tile's factors (the only group in flight)
         __syncwarp();
         if (q + 1 < cnt) issue_factors(q + 1);  // the other buffer: tile q - 1 is done with it
+        const int3 fl = fnext;  // (r_min Dirichlet, FL_RI0, FL_RK0) of this tile's instrument
+        if (q + 1 < cnt) fnext = flags(q + 1);
         const float2* fp = reinterpret_cast<const float2*>(facs + (q & 1) * (facB / 4));
         const float* fc = facs + (q & 1) * (facB / 4) + 2 * L;
         const long long t = gw + (long long)q * NW;
@@ -314,14 +323,13 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         const long long r = t / rt;
         const int b = (int)(r / mid), m = (int)(r % mid);  // m: y plane (pass 2) or v node (pass 3)
         float* col = reinterpret_cast<float*>(slots + s * slotB) + lane;
-        const int* fl = P.fl + (size_t)b * FL_N;
         // identity systems: r_max, and r_min when Dirichlet (lines past n_r
         // hold zeros and are solved like the others, never stored)
         bool any_dir = false;
 #pragma unroll
         for (int c = 0; c < CW; ++c) {
             const int i = i0 + 32 * c;
-            any_dir |= i == nr - 1 || (i == 0 && fl[FL_RLO_DIR]);
+            any_dir |= i == nr - 1 || (i == 0 && fl.x);
         }
         float x0[CW];
         if (!any_dir) {  // the lane's lines solved side by side
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
                 const int i = i0 + 32 * c;
                 float* cc = col + 32 * c;
                 float xc[1] = {cc[0]};  // an identity line: x = its right-hand side
-                if (i == nr - 1 || (i == 0 && fl[FL_RLO_DIR])) {
+                if (i == nr - 1 || (i == 0 && fl.x)) {
                     if constexpr (AXIS == 1) {
                         const float* u = cc + ny * RS;
                         for (int jj = 0; jj < ny; ++jj) cc[jj * RS] = u[jj * RS] + cc[jj * RS];
@@ -351,7 +359,7 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         if constexpr (AXIS != 0) {
 #pragma unroll
             for (int c = 0; c < CW; ++c)
-                if (i0 + 32 * c < nr) note_increment(P, fl, b, i0 + 32 * c, m, n, x0[c]);  // dU3 at j = 0
+                if (i0 + 32 * c < nr) note_increment_at(P, fl.y, fl.z, b, i0 + 32 * c, m, n, x0[c]);  // dU3 at j = 0
         }
         tma::fence_proxy_async_smem();  // the solved column before the store reads it
         __syncwarp();
