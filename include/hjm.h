@@ -274,8 +274,7 @@ hjm_status hjm_trace_read(hjm_trace* out, int reset);
  * 32 consecutive r nodes by the Tensor Memory Accelerator (one box copy in
  * and one box store per tile, a persistent grid in which every warp marches
  * its own tiles through a ring of shared-memory slots; pass 3 in place adds
- * dU3 to U^n with a reduction store, so U^n is not staged, and on y lines of
- * more than 128 nodes takes tiles of 64 r nodes, two lines per lane; FP32, n_r a
+ * dU3 to U^n with a reduction store, so U^n is not staged; FP32, n_r a
  * multiple of 4, lines of at most 256 nodes; pass 3 in groups where every
  * instrument has gamma = 0, the lane-per-line kernel otherwise; same results
  * as 1, bit for bit). Stepwise access

@@ -14,10 +14,7 @@
 // factors of the line-invariant systems (the v system is the same for every
 // v line of an instrument; with gamma = 0 the y system depends on v only),
 // and one box store writes the tile back. Nodes past n_r arrive as zeros
-// and are not stored (the box is clipped at the tensor's edge). The in-place
-// pass 3 on lines of more than 128 nodes takes tiles of 64 r nodes, lane i
-// owning columns i and i + 32 and solving the two lines side by side
-// (lines_cw).
+// and are not stored (the box is clipped at the tensor's edge).
 //
 // The grid is persistent: every warp marches its own tiles (tile g, g + NW,
 // g + 2 NW, ... for global warp g of NW) through a ring of R shared-memory
@@ -63,134 +60,97 @@ __device__ __forceinline__ void cp4(unsigned dst, const float* src)
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Thomas solve in place of NC columns (column q at col + 32 q, rows RS
-// floats apart) of L nodes that share one system, with its LU factors
-// fp[k] = (l_k, 1/pivot_k) and fc[k] = c'_k (Section 5):
+// Thomas solve of one column (stride 32 floats) of L nodes in place with the
+// LU factors fp[k] = (l_k, 1/pivot_k) and fc[k] = c'_k (Section 5):
 //   forward  d'_k = (d_k - l_k d'_{k-1}) / pivot_k,
 //   backward x_k = d'_k - c'_k x_{k+1};
-// UPD: the column receives u_k + x_k instead of x_k (pass 3's update; u
-// laid out like col). Eight nodes at a time: the next eight nodes' operands
-// are read into registers before the current eight are eliminated and
-// stored, so the shared-memory latency is paid once per eight nodes and not
-// on every link of the recurrence; the NC columns' recurrences run side by
-// side on each factor read. x0[q] receives column q's x_0.
-template <bool UPD, int NC, int RS>
-__device__ __forceinline__ void line_solve(float* col, const float* u, const float2* fp, const float* fc, int L,
-                                           float (&x0)[NC])
+// UPD: the column receives u_k + x_k instead of x_k (pass 3's update).
+// Eight nodes at a time: the next eight nodes' operands are read into
+// registers before the current eight are eliminated and stored, so the
+// shared-memory latency is paid once per eight nodes and not on every link
+// of the recurrence. Returns x_0.
+template <bool UPD>
+__device__ __forceinline__ float line_solve(float* col, const float* u, const float2* fp, const float* fc, int L)
 {
     constexpr int C = 8;
-    float dp[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) dp[q] = 0.f;
+    float dp = 0.f;
     int kk = 0;
     if (L >= C) {
-        float c[NC][C];
+        float c[C];
         float2 f[C];
 #pragma unroll
         for (int e = 0; e < C; ++e) {
+            c[e] = col[e * 32];
             f[e] = fp[e];
-#pragma unroll
-            for (int q = 0; q < NC; ++q) c[q][e] = col[e * RS + 32 * q];
         }
         for (; kk + C <= L; kk += C) {
-            float cn[NC][C];
+            float cn[C];
             float2 fn[C];
 #pragma unroll
             for (int e = 0; e < C; ++e) {  // the next eight (clamped: always inside the column)
-                const int k = min(kk + C + e, L - 1);
-                fn[e] = fp[k];
-#pragma unroll
-                for (int q = 0; q < NC; ++q) cn[q][e] = col[k * RS + 32 * q];
+                const int q = min(kk + C + e, L - 1);
+                cn[e] = col[q * 32];
+                fn[e] = fp[q];
             }
 #pragma unroll
-            for (int e = 0; e < C; ++e)
+            for (int e = 0; e < C; ++e) {
+                dp = (c[e] - f[e].x * dp) * f[e].y;
+                c[e] = dp;
+            }
 #pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    dp[q] = (c[q][e] - f[e].x * dp[q]) * f[e].y;
-                    c[q][e] = dp[q];
-                }
-#pragma unroll
-            for (int e = 0; e < C; ++e)
-#pragma unroll
-                for (int q = 0; q < NC; ++q) col[(kk + e) * RS + 32 * q] = c[q][e];
+            for (int e = 0; e < C; ++e) col[(kk + e) * 32] = c[e];
 #pragma unroll
             for (int e = 0; e < C; ++e) {
+                c[e] = cn[e];
                 f[e] = fn[e];
-#pragma unroll
-                for (int q = 0; q < NC; ++q) c[q][e] = cn[q][e];
             }
         }
     }
     for (; kk < L; ++kk) {
         const float2 f = fp[kk];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            dp[q] = (col[kk * RS + 32 * q] - f.x * dp[q]) * f.y;
-            col[kk * RS + 32 * q] = dp[q];
-        }
+        dp = (col[kk * 32] - f.x * dp) * f.y;
+        col[kk * 32] = dp;
     }
-    float x[NC];
-#pragma unroll
-    for (int q = 0; q < NC; ++q) {
-        x[q] = dp[q];
-        if (UPD) col[(L - 1) * RS + 32 * q] = u[(L - 1) * RS + 32 * q] + x[q];
-    }
+    float x = dp;
+    if (UPD) col[(L - 1) * 32] = u[(L - 1) * 32] + x;
     kk = L - 2;
     if (kk + 1 >= C) {
-        float c[NC][C], w[NC][C], g[C];
+        float c[C], g[C], w[C];
 #pragma unroll
         for (int e = 0; e < C; ++e) {
+            c[e] = col[(kk - e) * 32];
             g[e] = fc[kk - e];
-#pragma unroll
-            for (int q = 0; q < NC; ++q) {
-                c[q][e] = col[(kk - e) * RS + 32 * q];
-                w[q][e] = UPD ? u[(kk - e) * RS + 32 * q] : 0.f;
-            }
+            w[e] = UPD ? u[(kk - e) * 32] : 0.f;
         }
         for (; kk + 1 >= C; kk -= C) {  // nodes kk .. kk - 7
-            float cn[NC][C], wn[NC][C], gn[C];
+            float cn[C], gn[C], wn[C];
 #pragma unroll
             for (int e = 0; e < C; ++e) {
-                const int k = max(kk - C - e, 0);
-                gn[e] = fc[k];
-#pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    cn[q][e] = col[k * RS + 32 * q];
-                    wn[q][e] = UPD ? u[k * RS + 32 * q] : 0.f;
-                }
+                const int q = max(kk - C - e, 0);
+                cn[e] = col[q * 32];
+                gn[e] = fc[q];
+                wn[e] = UPD ? u[q * 32] : 0.f;
             }
 #pragma unroll
-            for (int e = 0; e < C; ++e)
+            for (int e = 0; e < C; ++e) {
+                x = c[e] - g[e] * x;
+                c[e] = UPD ? w[e] + x : x;
+            }
 #pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    x[q] = c[q][e] - g[e] * x[q];
-                    c[q][e] = UPD ? w[q][e] + x[q] : x[q];
-                }
-#pragma unroll
-            for (int e = 0; e < C; ++e)
-#pragma unroll
-                for (int q = 0; q < NC; ++q) col[(kk - e) * RS + 32 * q] = c[q][e];
+            for (int e = 0; e < C; ++e) col[(kk - e) * 32] = c[e];
 #pragma unroll
             for (int e = 0; e < C; ++e) {
+                c[e] = cn[e];
                 g[e] = gn[e];
-#pragma unroll
-                for (int q = 0; q < NC; ++q) {
-                    c[q][e] = cn[q][e];
-                    w[q][e] = wn[q][e];
-                }
+                w[e] = wn[e];
             }
         }
     }
     for (; kk >= 0; --kk) {
-        const float g = fc[kk];
-#pragma unroll
-        for (int q = 0; q < NC; ++q) {
-            x[q] = col[kk * RS + 32 * q] - g * x[q];
-            col[kk * RS + 32 * q] = UPD ? u[kk * RS + 32 * q] + x[q] : x[q];
-        }
+        x = col[kk * 32] - fc[kk] * x;
+        col[kk * 32] = UPD ? u[kk * 32] + x : x;
     }
-#pragma unroll
-    for (int q = 0; q < NC; ++q) x0[q] = x[q];
+    return x;
 }
 
 // Bounded wait of the whole warp on the copy with parity par of barrier
@@ -210,10 +170,8 @@ __device__ __forceinline__ bool warp_wait(unsigned bar, unsigned par)
 // n_y, B), out: U^{n+1}); AXIS 2: pass 3 in place (out = un = U): the tile
 // of dU3 is added to U by the box store itself (a reduction store), so U^n
 // is never staged and a warp needs half the shared memory. R slots per
-// warp, blockDim.x / 32 warps per CTA. CW: tiles of 32 CW r nodes, lane i
-// solving lines i, i + 32, ... (CW = 2 for long lines: 256-byte rows in the
-// box copies, and each factor read serves two lines).
-template <int AXIS, int CW>
+// warp, blockDim.x / 32 warps per CTA.
+template <int AXIS>
 __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __grid_constant__ CUtensorMap tin,
                                                   const __grid_constant__ CUtensorMap tun,
                                                   const __grid_constant__ CUtensorMap tout, const int n,
@@ -224,15 +182,14 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, W = blockDim.x >> 5;
     const int nr = P.nr, nv = P.nv, ny = P.ny;
     const int L = AXIS == 0 ? nv : ny;   // nodes per line
-    constexpr int RS = 32 * CW;          // floats per row of a tile
-    const int colB = L * kRowB * CW;     // one block of 32 CW lines
+    const int colB = L * kRowB;          // one block of 32 lines
     const int slotB = AXIS == 1 ? 2 * colB : colB;
     const int facB = fac_bytes(L);       // one factor buffer: (sub, 1/pivot) pairs, then c'
     const unsigned bar0 = tma::su32(sm) + 32u * (unsigned)warp;
     unsigned char* slots = sm + kHeader + (size_t)warp * (R * slotB + 2 * facB);
     const unsigned slots0 = tma::su32(slots);
     float* const facs = reinterpret_cast<float*>(slots + R * slotB);  // two buffers, tile q in q & 1
-    const int rt = (nr + RS - 1) / RS;   // tiles across r
+    const int rt = (nr + 31) >> 5;       // tiles across r
     const int mid = AXIS == 0 ? ny : nv; // tiles across the other transverse axis
     const long long ntile = (long long)P.B * mid * rt;
     const long long gw = (long long)blockIdx.x * W + warp, NW = (long long)gridDim.x * W;
@@ -250,7 +207,7 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         const long long t = gw + (long long)q * NW;
         if (t == drop) return;  // test hook: the copy never starts, its wait runs out
         const unsigned s = (unsigned)(q % R), bar = bar0 + 8u * s, dst = slots0 + s * (unsigned)slotB;
-        const int x0 = (int)(t % rt) * RS;
+        const int x0 = (int)(t % rt) * 32;
         const long long r = t / rt;
         if constexpr (AXIS == 0) {
             tma::mbar_expect_tx(bar, (unsigned)colB);
@@ -319,53 +276,33 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
         const float2* fp = reinterpret_cast<const float2*>(facs + (q & 1) * (facB / 4));
         const float* fc = facs + (q & 1) * (facB / 4) + 2 * L;
         const long long t = gw + (long long)q * NW;
-        const int i0 = (int)(t % rt) * RS + lane;  // the lane's first line; the others 32 apart
+        const int i = (int)(t % rt) * 32 + lane;
         const long long r = t / rt;
         const int b = (int)(r / mid), m = (int)(r % mid);  // m: y plane (pass 2) or v node (pass 3)
         float* col = reinterpret_cast<float*>(slots + s * slotB) + lane;
-        // identity systems: r_max, and r_min when Dirichlet (lines past n_r
-        // hold zeros and are solved like the others, never stored)
-        bool any_dir = false;
-#pragma unroll
-        for (int c = 0; c < CW; ++c) {
-            const int i = i0 + 32 * c;
-            any_dir |= i == nr - 1 || (i == 0 && fl.x);
-        }
-        float x0[CW];
-        if (!any_dir) {  // the lane's lines solved side by side
-            if constexpr (AXIS == 1)
-                line_solve<true, CW, RS>(col, col + ny * RS, fp, fc, ny, x0);
-            else
-                line_solve<false, CW, RS>(col, nullptr, fp, fc, L, x0);
-        } else {
-#pragma unroll
-            for (int c = 0; c < CW; ++c) {
-                const int i = i0 + 32 * c;
-                float* cc = col + 32 * c;
-                float xc[1] = {cc[0]};  // an identity line: x = its right-hand side
-                if (i == nr - 1 || (i == 0 && fl.x)) {
-                    if constexpr (AXIS == 1) {
-                        const float* u = cc + ny * RS;
-                        for (int jj = 0; jj < ny; ++jj) cc[jj * RS] = u[jj * RS] + cc[jj * RS];
-                    }
-                } else if constexpr (AXIS == 1) {
-                    line_solve<true, 1, RS>(cc, cc + ny * RS, fp, fc, ny, xc);
+        if (i < nr) {
+            const bool dir = i == nr - 1 || (i == 0 && fl.x);  // identity system
+            if constexpr (AXIS == 0) {
+                if (!dir) line_solve<false>(col, nullptr, fp, fc, nv);
+            } else if constexpr (AXIS == 2) {  // dU3 (dU2 itself on an identity line), added by the store
+                if (!dir) line_solve<false>(col, nullptr, fp, fc, ny);
+                note_increment_at(P, fl.y, fl.z, b, i, m, n, col[0]);
+            } else {
+                const float* u = col + ny * 32;
+                if (dir) {
+                    note_increment_at(P, fl.y, fl.z, b, i, m, n, col[0]);
+                    for (int jj = 0; jj < ny; ++jj) col[jj * 32] = u[jj * 32] + col[jj * 32];
                 } else {
-                    line_solve<false, 1, RS>(cc, nullptr, fp, fc, L, xc);
+                    const float x0 = line_solve<true>(col, u, fp, fc, ny);
+                    note_increment_at(P, fl.y, fl.z, b, i, m, n, x0);
                 }
-                x0[c] = xc[0];
             }
-        }
-        if constexpr (AXIS != 0) {
-#pragma unroll
-            for (int c = 0; c < CW; ++c)
-                if (i0 + 32 * c < nr) note_increment_at(P, fl.y, fl.z, b, i0 + 32 * c, m, n, x0[c]);  // dU3 at j = 0
         }
         tma::fence_proxy_async_smem();  // the solved column before the store reads it
         __syncwarp();
         if (lane == 0) {
             const unsigned src = slots0 + s * (unsigned)slotB;
-            const int x0 = (int)(t % rt) * RS;
+            const int x0 = (int)(t % rt) * 32;
             if constexpr (AXIS == 0)
                 tma::store3(&tout, x0, 0, (int)r, src);
             else if constexpr (AXIS == 2)
@@ -387,9 +324,9 @@ __global__ void __launch_bounds__(128) k_lines_t(const March<float> P, const __g
 // ------------------------------------------------------------------- host
 
 // Tensor map of a group's FP32 field U[b][j][k][i]: AXIS 0 the 3-D view
-// (i, k, b n_y + j) with box (32 CW, n_v, 1); AXIS 1 the 4-D view (i, k, j,
-// b) with box (32 CW, 1, n_y, 1). n_r a multiple of 4 (16-byte row strides).
-cudaError_t lines_map(CUtensorMap* m, const float* U, const March<float>& P, int axis, int CW)
+// (i, k, b n_y + j) with box (32, n_v, 1); AXIS 1 the 4-D view (i, k, j, b)
+// with box (32, 1, n_y, 1). n_r a multiple of 4 (16-byte row strides).
+cudaError_t lines_map(CUtensorMap* m, const float* U, const March<float>& P, int axis)
 {
     const tma::EncodeTiled fn = tma::encoder();
     if (!fn) return cudaErrorNotSupported;
@@ -399,14 +336,14 @@ cudaError_t lines_map(CUtensorMap* m, const float* U, const March<float>& P, int
     if (axis == 0) {
         const cuuint64_t dims[3] = {nr, nv, B * ny};
         const cuuint64_t strides[2] = {nr * 4, nr * nv * 4};
-        const cuuint32_t box[3] = {32u * CW, (cuuint32_t)nv, 1};
+        const cuuint32_t box[3] = {32, (cuuint32_t)nv, 1};
         r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(U), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[4] = {nr, nv, ny, B};
         const cuuint64_t strides[3] = {nr * 4, nr * nv * 4, nr * nv * ny * 4};
-        const cuuint32_t box[4] = {32u * CW, 1, (cuuint32_t)ny, 1};
+        const cuuint32_t box[4] = {32, 1, (cuuint32_t)ny, 1};
         r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(U), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -416,9 +353,9 @@ cudaError_t lines_map(CUtensorMap* m, const float* U, const March<float>& P, int
 
 // Warps per CTA and slots per warp for a line of L nodes: three slots, as
 // many warps (4, 2, 1) as fit; two slots when one warp of three does not fit.
-size_t lines_smem(int axis, int L, int W, int R, int CW)
+size_t lines_smem(int axis, int L, int W, int R)
 {
-    const size_t per_warp = (size_t)R * L * kRowB * CW * (axis == 1 ? 2 : 1) + 2 * (size_t)fac_bytes(L);
+    const size_t per_warp = (size_t)R * L * kRowB * (axis == 1 ? 2 : 1) + 2 * (size_t)fac_bytes(L);
     return (size_t)kHeader + (size_t)W * per_warp + 128;  // + alignment slack
 }
 
@@ -428,12 +365,12 @@ size_t lines_smem(int axis, int L, int W, int R, int CW)
 // slots 80 % slower; pass 2 was equal with two slots, slower with three),
 // and the warps per CTA (4, 2, 1) that put the most warps on an SM (228 KB
 // of shared memory, 1 KB of it reserved per CTA).
-bool lines_shape(int axis, int L, int& W, int& R, int CW = 1)
+bool lines_shape(int axis, int L, int& W, int& R)
 {
     R = 1;
     int best = 0;
     for (int w = 4; w >= 1; w /= 2) {
-        const size_t sm = lines_smem(axis, L, w, R, CW);
+        const size_t sm = lines_smem(axis, L, w, R);
         if (sm > (size_t)kSmemLimit) continue;
         const int warps = w * (int)(228 * 1024 / (sm + 1024));
         if (warps > best) {
@@ -444,32 +381,9 @@ bool lines_shape(int axis, int L, int& W, int& R, int CW = 1)
     return best > 0;
 }
 
-// Lines per lane: two for the in-place pass 3 (kind 2) on lines of more
-// than 128 nodes, where few warps fit an SM (256-byte rows in the box copies,
-// and each factor read serves two lines), one otherwise. Measured on the
-// 512 x 256 x 256 caplet (1000 steps): pass 3 105 ms with two lines per
-// lane against 124 ms with one (and 111 ms split over 4 warps per line);
-// pass 2 was slower with two (98.5 ms against 76.5 ms), and the out-of-place
-// pass 3, which stages U^n as well, would fit one warp per SM.
-int lines_cw(int kind, int L)
-{
-    int W, R;
-    return kind == 2 && L > 128 && lines_shape(kind, L, W, R, 2) ? 2 : 1;
-}
-
-template <int CW>
-int lines_occupancy(int kind, int W, size_t smem, int* nb)
-{
-    const cudaError_t e =
-        kind == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_lines_t<0, CW>, 32 * W, smem)
-        : kind == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_lines_t<1, CW>, 32 * W, smem)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(nb, k_lines_t<2, CW>, 32 * W, smem);
-    return e == cudaSuccess;
-}
-
-// Resident CTAs of the kernel (kind 0, 1, 2 as the template argument; CW)
-// at this shape times the SM count, cached.
-int lines_grid(int axis, int W, size_t smem, int CW)
+// Resident CTAs of the kernel (kind 0, 1, 2 as the template argument) at
+// this shape times the SM count, cached.
+int lines_grid(int axis, int W, size_t smem)
 {
     static std::mutex mu;
     static int dev_cached = -1, sms = 0;
@@ -482,11 +396,15 @@ int lines_grid(int axis, int W, size_t smem, int CW)
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
         dev_cached = dev;
     }
-    const auto key = std::make_pair(CW * 256 + axis * 16 + W, smem);
+    const auto key = std::make_pair(axis * 16 + W, smem);
     for (const auto& c : cache)
         if (c.first == key) return c.second;
     int nb = 0;
-    if (!(CW == 2 ? lines_occupancy<2>(axis, W, smem, &nb) : lines_occupancy<1>(axis, W, smem, &nb))) return 0;
+    const cudaError_t e =
+        axis == 0   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<0>, 32 * W, smem)
+        : axis == 1 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<1>, 32 * W, smem)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_lines_t<2>, 32 * W, smem);
+    if (e != cudaSuccess) return 0;
     cache.emplace_back(key, nb * sms);
     return nb * sms;
 }
@@ -508,43 +426,36 @@ cudaError_t launch_lines_t(int axis, const March<float>& P, const float* in, con
     if (((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out) |
           reinterpret_cast<uintptr_t>(axis == 0 ? in : Un)) & 15) != 0)
         return cudaErrorNotSupported;  // the caller falls back to the lane-per-line kernels
+    CUtensorMap mi, mu, mo;
+    cudaError_t e = lines_map(&mi, in, P, axis);
+    if (e == cudaSuccess) e = lines_map(&mu, axis == 0 ? in : Un, P, axis);
+    if (e == cudaSuccess) e = lines_map(&mo, out, P, axis);
+    if (e != cudaSuccess) return e;
     // pass 3 in place (the Douglas stage: U^{n+1} over U^n) adds dU3 to U by
     // the reduction store; otherwise U^n is staged next to dU2
     const int kind = axis == 0 ? 0 : (Un == out ? 2 : 1);
-    const int L = axis == 0 ? P.nv : P.ny;
-    const int CW = lines_cw(kind, L);
-    CUtensorMap mi, mu, mo;
-    cudaError_t e = lines_map(&mi, in, P, axis, CW);
-    if (e == cudaSuccess) e = lines_map(&mu, axis == 0 ? in : Un, P, axis, CW);
-    if (e == cudaSuccess) e = lines_map(&mo, out, P, axis, CW);
-    if (e != cudaSuccess) return e;
     int W, R;
-    lines_shape(kind, L, W, R, CW);
-    const size_t smem = lines_smem(kind, L, W, R, CW);
-    const long long ntile = (long long)P.B * (axis == 0 ? P.ny : P.nv) * ((P.nr + 32 * CW - 1) / (32 * CW));
-    const long long grid = std::min<long long>((ntile + W - 1) / W, lines_grid(kind, W, smem, CW));
+    lines_shape(kind, axis == 0 ? P.nv : P.ny, W, R);
+    const size_t smem = lines_smem(kind, axis == 0 ? P.nv : P.ny, W, R);
+    const long long ntile = (long long)P.B * (axis == 0 ? P.ny : P.nv) * ((P.nr + 31) / 32);
+    const long long grid = std::min<long long>((ntile + W - 1) / W, lines_grid(kind, W, smem));
     if (grid < 1) return cudaErrorInvalidConfiguration;
-#define HJM_LT(K, C) k_lines_t<K, C><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R)
-    if (CW == 2) {
-        if (kind == 0) HJM_LT(0, 2);
-        else if (kind == 1) HJM_LT(1, 2);
-        else HJM_LT(2, 2);
-    } else {
-        if (kind == 0) HJM_LT(0, 1);
-        else if (kind == 1) HJM_LT(1, 1);
-        else HJM_LT(2, 1);
-    }
-#undef HJM_LT
+    if (kind == 0)
+        k_lines_t<0><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
+    else if (kind == 1)
+        k_lines_t<1><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
+    else
+        k_lines_t<2><<<(unsigned)grid, 32 * W, smem, s>>>(P, mi, mu, mo, n, R);
     return cudaGetLastError();
 }
 
 cudaError_t init_lines_t()
 {
-    cudaError_t e = cudaSuccess;
-#define HJM_LT_ATTR(K, C) \
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_lines_t<K, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    HJM_LT_ATTR(0, 1) HJM_LT_ATTR(1, 1) HJM_LT_ATTR(2, 1) HJM_LT_ATTR(0, 2) HJM_LT_ATTR(1, 2) HJM_LT_ATTR(2, 2)
-#undef HJM_LT_ATTR
+    cudaError_t e = cudaFuncSetAttribute(k_lines_t<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lines_t<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_lines_t<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     return e;
 }
 

@@ -97,9 +97,8 @@ def test_tma_strided_passes_match_oracle(H, orc, name):
 @pytest.mark.parametrize("shape", [(64, 32, 32, 160), (96, 48, 48, 12), (128, 64, 64, 8), (96, 200, 16, 64)])
 def test_tma_strided_march_batches(H, orc, shape):
     # B n_y ceil(n_r / 32) tiles per pass: several per warp of the persistent
-    # grid, so every warp refills its slots; y lines of 200 nodes take the
-    # in-place pass 3 with two lines per lane (64-node tiles, the last one
-    # ragged at n_r = 96)
+    # grid, so every warp refills its slots; the last shape has y lines of
+    # 200 nodes (few warps per SM) and a ragged last tile (n_r = 96)
     nr, ny, nv, B = shape
     items = W.config2_draws(B, seed=W.SEED_BASE + 1200 + nr, n_r=nr, n_y=ny, n_v=nv, n_steps=6)
     try:
