@@ -253,12 +253,12 @@ def pass1_flops_per_point(S, M):
     difference: 15) and second sweep (r part, reaction, mixed term, scaling
     by dt: 20), the rows of I - theta dt A_r (13), and the partition solve,
     per lane: local forward elimination 8 + 9 (M - 2), backward elimination
-    5 (M - 3), the chunk's first row 9, the interface row 10, 14 per
-    parallel-cyclic-reduction level (log2 S levels), back-substitution
-    6 + 4 (M - 2)."""
+    5 (M - 3), the chunk's first row 9, the interface row divided by its
+    diagonal 14, 14 per parallel-cyclic-reduction level (log2 S levels),
+    back-substitution 4 + 4 (M - 2)."""
     levels = int(round(math.log2(S))) if S > 1 else 0
-    lane = (8 + 9 * max(M - 2, 0) + 5 * max(M - 3, 0) + (9 if M >= 3 else 0) + 10 + 14 * levels
-            + 6 + 4 * max(M - 2, 0))
+    lane = (8 + 9 * max(M - 2, 0) + 5 * max(M - 3, 0) + (9 if M >= 3 else 0) + 14 + 14 * levels
+            + 4 + 4 * max(M - 2, 0))
     return 15 + 20 + 13 + lane / M
 
 

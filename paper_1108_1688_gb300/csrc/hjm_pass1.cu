@@ -35,7 +35,8 @@ __device__ __forceinline__ float fast_rcp<float>(float x)
 }
 // FP64 march: the IEEE division. A Newton-Raphson reciprocal from the FP32
 // hardware seed (two steps of y + y (1 - x y), four FP64 fused multiply-adds
-// and two conversions) was measured 4 % slower on the FP64-bound pass 1.
+// and two conversions) was measured 4 % slower on the FP64-bound pass 1, and
+// the correctly rounded reciprocal intrinsic equal to it.
 template <>
 __device__ __forceinline__ double fast_rcp<double>(double x)
 {
@@ -153,30 +154,35 @@ __device__ __forceinline__ void seg_partition_solve(T (&a)[M], T (&b)[M], T (&c)
     T cSn = __shfl_down_sync(0xffffffffu, cS, 1, S);
     T dSn = __shfl_down_sync(0xffffffffu, dS, 1, S);
     if (sl == S - 1) aSn = cSn = dSn = T(0);
-    T al = -aE * aS;
-    T be = T(1) - aE * cS - cE * aSn;
-    T ga = -cE * cSn;
-    T de = dE - aE * dS - cE * dSn;
+    // interface row al x_{e-1} + x_e + ga x_{e+1} = de, divided by its
+    // diagonal, so that every reduction level below takes one reciprocal
+    T al, ga, de;
+    {
+        const T r = fast_rcp(T(1) - aE * cS - cE * aSn);
+        al = -aE * aS * r;
+        ga = -cE * cSn * r;
+        de = (dE - aE * dS - cE * dSn) * r;
+    }
 #pragma unroll
     for (int s = 1; s < S; s <<= 1) {
-        const T alm = __shfl_up_sync(0xffffffffu, al, s, S), bem = __shfl_up_sync(0xffffffffu, be, s, S);
-        const T gam = __shfl_up_sync(0xffffffffu, ga, s, S), dem = __shfl_up_sync(0xffffffffu, de, s, S);
-        const T alp = __shfl_down_sync(0xffffffffu, al, s, S), bep = __shfl_down_sync(0xffffffffu, be, s, S);
-        const T gap = __shfl_down_sync(0xffffffffu, ga, s, S), dep = __shfl_down_sync(0xffffffffu, de, s, S);
+        const T alm = __shfl_up_sync(0xffffffffu, al, s, S), gam = __shfl_up_sync(0xffffffffu, ga, s, S);
+        const T dem = __shfl_up_sync(0xffffffffu, de, s, S);
+        const T alp = __shfl_down_sync(0xffffffffu, al, s, S), gap = __shfl_down_sync(0xffffffffu, ga, s, S);
+        const T dep = __shfl_down_sync(0xffffffffu, de, s, S);
         // Lanes with no partner s below (above) already have al = 0 (ga = 0):
         // the first row of the line has no sub-diagonal, the last no
         // super-diagonal, and each step doubles the zeroed span. The
         // out-of-range shuffles return the lane's own (finite) values, which
-        // are then multiplied by k1 = 0 (k2 = 0).
-        const T k1 = al * fast_rcp(bem), k2 = ga * fast_rcp(bep);
-        const T nbe = be - gam * k1 - alp * k2;
-        const T nde = de - dem * k1 - dep * k2;
-        al = -alm * k1;
-        ga = -gap * k2;
-        be = nbe;
+        // are then multiplied by al = 0 (ga = 0). Eliminating x_{e-s} and
+        // x_{e+s} with the neighbours' unit-diagonal rows and dividing by the
+        // new diagonal keeps the row at unit diagonal.
+        const T r = fast_rcp(T(1) - al * gam - ga * alp);
+        const T nde = (de - al * dem - ga * dep) * r;
+        al = -al * alm * r;
+        ga = -ga * gap * r;
         de = nde;
     }
-    const T xE = de * fast_rcp(be);
+    const T xE = de;
     T xEp = __shfl_up_sync(0xffffffffu, xE, 1, S);
     if (sl == 0) xEp = T(0);
     const T xS = dS - aS * xEp - cS * xE;
