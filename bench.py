@@ -250,8 +250,9 @@ def pass1_flops_per_point(S, M):
     arithmetic (a fused multiply-add counts 2, a division 1; face rows,
     a few per line, left out), for S lanes of M nodes per r line:
     the explicit operator's first sweep (v and y parts, mixed-term row
-    difference: 15) and second sweep (r part, reaction, mixed term, scaling
-    by dt: 20), the rows of I - theta dt A_r (13), and the partition solve,
+    difference: 15) and second sweep (r part from one first difference per
+    node, reaction, mixed term, scaling by dt: 19), the rows of
+    I - theta dt A_r (13), and the partition solve,
     per lane: local forward elimination 8 + 9 (M - 2), backward elimination
     5 (M - 3), the chunk's first row 9, the interface row divided by its
     diagonal 14, 14 per parallel-cyclic-reduction level (log2 S levels),
@@ -259,7 +260,7 @@ def pass1_flops_per_point(S, M):
     levels = int(round(math.log2(S))) if S > 1 else 0
     lane = (8 + 9 * max(M - 2, 0) + 5 * max(M - 3, 0) + (9 if M >= 3 else 0) + 14 + 14 * levels
             + 4 + 4 * max(M - 2, 0))
-    return 15 + 20 + 13 + lane / M
+    return 15 + 19 + 13 + lane / M
 
 
 def recorded_traffic(kernel, workload, points_per_launch, tile=None):

@@ -345,6 +345,9 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const T yA = yin ? T(-1) : (yord == 1 ? (j == 0 ? T(2) : T(-2)) : (j == 0 ? T(4) : T(-4)));
     const T yB = yin ? T(1) : (yord == 1 ? T(0) : (j == 0 ? T(-1) : T(1)));
     const T dt = I.dt, w = I.w;
+    // dt rides on the per-line factors of the v and y parts, so the first
+    // sweep yields dt (A_v + A_y) U directly
+    const T cAd = cA * dt, cBd = cB * dt, vyd = vy * dt, kyyd = kyy * dt;
 
 #define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
     // 1. right-hand side, every node as if interior in r, in two sweeps over
@@ -360,8 +363,8 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const PV xw2 = Two<T>::splat(ST2 && !I.hv ? T(1) : T(0)), xr2 = Two<T>::splat(ST2 && I.hv ? T(1) : T(0));
     T wd[M];
     {
-        const PV cA2 = Two<T>::splat(cA), cB2 = Two<T>::splat(cB);
-        const PV vy2 = Two<T>::splat(vy), kyy2 = Two<T>::splat(kyy), yA2 = Two<T>::splat(yA), yB2 = Two<T>::splat(yB);
+        const PV cA2 = Two<T>::splat(cAd), cB2 = Two<T>::splat(cBd);
+        const PV vy2 = Two<T>::splat(vyd), kyy2 = Two<T>::splat(kyyd), yA2 = Two<T>::splat(yA), yB2 = Two<T>::splat(yB);
 #pragma unroll
         for (int m0 = 0; m0 < M; m0 += W) {
             T tCY[W];
@@ -386,7 +389,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             }
         }
     }
-    const T f1_0 = d[0];  // v and y parts at the lane's first node (r = 0 face)
+    const T f1_0 = d[0];  // dt times the v and y parts at the lane's first node (r = 0 face)
     // Neighbours across lanes by shuffles: U and wd at the chunk's ends.
     const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
     const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
@@ -396,6 +399,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
         // shifted pairs sh = (U_{m-1}, U_m), tw = (wd_{m-1}, wd_m), rolled
         PV shc = Two<T>::mk(uc_prev, uc[0]);
         PV twc = Two<T>::mk(wd_prev, wd[0]);
+        T dlast = uc[0] - uc_prev;  // FP64: U_m - U_{m-1} of the pair's first node, from the previous pair
         const PV v2 = Two<T>::splat(v), nv2 = Two<T>::splat(-v), aFy2 = Two<T>::splat(aFy);
         const PV vq2 = Two<T>::splat(vq), dt2 = Two<T>::splat(dt);
 #pragma unroll
@@ -420,16 +424,24 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
                 }
                 const PV u = Two<T>::mk(uc[m], uc[m + 1]);
                 const PV Dp = Two<T>::sub(shn, u);  // U_{m+1} - U_m
-                const PV Dm = Two<T>::sub(u, shc);  // U_m - U_{m-1}
+                PV Dm;                              // U_m - U_{m-1}
+                if constexpr (sizeof(T) == 8) {     // the previous first differences (scalar FP64)
+                    Dm = Two<T>::mk(dlast, Two<T>::x(Dp));
+                    dlast = Two<T>::y(Dp);
+                } else {                            // one paired instruction
+                    Dm = Two<T>::sub(u, shc);
+                }
                 const PV g1 = Two<T>::mul(Two<T>::mk(tC1[q], tC1[q + 1]), v2);  // zeta_rr / (J^2 h^2)
                 const PV g4F = Two<T>::fma(aFy2, Two<T>::mk(tIJ[q], tIJ[q + 1]),
                                            Two<T>::fma(nv2, Two<T>::mk(tC4V[q], tC4V[q + 1]),
                                                        Two<T>::mk(tC4B[q], tC4B[q + 1])));  // g4 / (2h) at t^n
                 PV f = Two<T>::fma(g1, Two<T>::sub(Dp, Dm), Two<T>::mul(g4F, Two<T>::add(Dp, Dm)));
-                f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
+                if constexpr (sizeof(T) == 8)  // the reaction fused (FP64: a negated operand is free)
+                    f = Two<T>::fma(Two<T>::mk(-tR[q], -tR[q + 1]), u, f);
+                else
+                    f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
                 f = Two<T>::fma(Two<T>::mul(Two<T>::mk(tC3[q], tC3[q + 1]), vq2), Two<T>::sub(twn, twc), f);
-                f = Two<T>::add(f, Two<T>::mk(d[m], d[m + 1]));
-                PV r = Two<T>::mul(dt2, f);
+                PV r = Two<T>::fma(dt2, f, Two<T>::mk(d[m], d[m + 1]));
                 if constexpr (ST2) r = Two<T>::fma(xr2, Two<T>::mk(xx[m], xx[m + 1]), r);
                 d[m] = Two<T>::x(r);
                 d[m + 1] = Two<T>::y(r);
@@ -447,9 +459,8 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             // and no mixed term (Section 7.3).
             const T u = uc[0], u1 = uc[1], u2 = M >= 3 ? uc[M >= 3 ? 2 : 1] : uc_next;
             const T fr = aFy * tl[RT_IJ * S * MP] + tl[RT_C4B * S * MP];  // mu_r / (2 h J) at t^n
-            T f = fr * (T(-3) * u + T(4) * u1 - u2) - tl[RT_R * S * MP] * u;
-            f += f1_0;  // v and y parts
-            d[0] = dt * f;
+            const T f = fr * (T(-3) * u + T(4) * u1 - u2) - tl[RT_R * S * MP] * u;
+            d[0] = dt * f + f1_0;  // f1_0: dt times the v and y parts
             if constexpr (ST2) {
                 if (I.hv) d[0] += xx[0];
             }
