@@ -199,12 +199,26 @@ MARCH_SOURCES = ("hjm_kernels.cuh", "hjm_march.cu", "hjm_pass1.cu", "hjm_pass1t.
 LINES_TMA = 15  # p2_warps / p3_warps code of the TMA-fed strided passes (HJM_LINES_TMA)
 
 
-def source_digest():
-    """Digest of the three Douglas pass kernels' sources (recorded with the ncu
-    counters, so a stale counter is detected and reported as null)."""
+# The files each kernel with recorded DRAM counters is built from (its
+# translation unit and the headers it includes): its counters in
+# profiles/traffic.json are reported only while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_pass1t": ("hjm_pass1t.cu", "hjm_kernels.cuh", "hjm_curve.cuh", "hjm_tma.cuh"),
+    "k_lines_t": ("hjm_lines_t.cu", "hjm_kernels.cuh", "hjm_curve.cuh", "hjm_tma.cuh"),
+    "k_pass1": ("hjm_pass1.cu", "hjm_kernels.cuh", "hjm_curve.cuh"),
+    "k_pass2": ("hjm_march.cu", "hjm_kernels.cuh", "hjm_curve.cuh"),
+    "k_pass3": ("hjm_march.cu", "hjm_kernels.cuh", "hjm_curve.cuh"),
+    "k_split_lines": ("hjm_march.cu", "hjm_kernels.cuh", "hjm_curve.cuh"),
+}
+
+
+def source_digest(kernel=None):
+    """Digest of one kernel's sources (KERNEL_SOURCES; stored with its ncu
+    counters, so a stale counter is detected and reported as null), or with
+    no kernel of all the Douglas pass kernels' sources."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1108_1688_gb300", "csrc")
-    for name in MARCH_SOURCES:
+    for name in (MARCH_SOURCES if kernel is None else KERNEL_SOURCES[kernel]):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode() + f.read())
     return h.hexdigest()[:16]
@@ -264,20 +278,20 @@ def pass1_flops_per_point(S, M):
 
 
 def recorded_traffic(kernel, workload, points_per_launch, tile=None):
-    """DRAM bytes per launch from the committed ncu summary of this workload,
-    if it was taken on the current kernel sources with the launch shape in
-    use; else None."""
+    """DRAM bytes per launch of pass `kernel` from the committed ncu summary
+    of this workload, if it was taken with the launch shape in use on the
+    current sources of the kernel that ran it; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
-    if d.get("source_digest") != source_digest():
-        return None
     w = d.get("workloads", {}).get(workload)
     if not w or tile is None:
         return None
     rec = w.get("tiles", {}).get(tile, {}).get("kernels", {}).get(kernel)
-    if not rec:
+    if not rec or rec.get("kernel") not in KERNEL_SOURCES:
+        return None
+    if rec.get("source_digest") != source_digest(rec["kernel"]):
         return None
     return rec["dram_bytes_per_point"] * points_per_launch
 

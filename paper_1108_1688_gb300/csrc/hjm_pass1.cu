@@ -345,9 +345,13 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
     const T yA = yin ? T(-1) : (yord == 1 ? (j == 0 ? T(2) : T(-2)) : (j == 0 ? T(4) : T(-4)));
     const T yB = yin ? T(1) : (yord == 1 ? T(0) : (j == 0 ? T(-1) : T(1)));
     const T dt = I.dt, w = I.w;
-    // dt rides on the per-line factors of the v and y parts, so the first
-    // sweep yields dt (A_v + A_y) U directly
-    const T cAd = cA * dt, cBd = cB * dt, vyd = vy * dt, kyyd = kyy * dt;
+    // FP64: dt rides on the per-line factors of the v and y parts, so the
+    // first sweep yields dt (A_v + A_y) U directly and the second adds it in
+    // one fused multiply-add (in FP32 the extra live scalars cost the
+    // correction-stage shapes a CTA per SM)
+    constexpr bool FOLD = sizeof(T) == 8;
+    const T sd = FOLD ? dt : T(1);
+    const T cAd = cA * sd, cBd = cB * sd, vyd = vy * sd, kyyd = kyy * sd;
 
 #define TABV(q, m0, arr) lds_vec<T, W>(tl + (q) * S * MP + (m0), arr)
     // 1. right-hand side, every node as if interior in r, in two sweeps over
@@ -389,7 +393,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             }
         }
     }
-    const T f1_0 = d[0];  // dt times the v and y parts at the lane's first node (r = 0 face)
+    const T f1_0 = d[0];  // the v and y parts at the lane's first node (r = 0 face; FOLD: times dt)
     // Neighbours across lanes by shuffles: U and wd at the chunk's ends.
     const T uc_prev = __shfl_up_sync(0xffffffffu, uc[M - 1], 1, S);
     const T uc_next = __shfl_down_sync(0xffffffffu, uc[0], 1, S);
@@ -441,7 +445,13 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
                 else
                     f = Two<T>::sub(f, Two<T>::mul(Two<T>::mk(tR[q], tR[q + 1]), u));
                 f = Two<T>::fma(Two<T>::mul(Two<T>::mk(tC3[q], tC3[q + 1]), vq2), Two<T>::sub(twn, twc), f);
-                PV r = Two<T>::fma(dt2, f, Two<T>::mk(d[m], d[m + 1]));
+                PV r;
+                if constexpr (FOLD) {
+                    r = Two<T>::fma(dt2, f, Two<T>::mk(d[m], d[m + 1]));
+                } else {
+                    f = Two<T>::add(f, Two<T>::mk(d[m], d[m + 1]));
+                    r = Two<T>::mul(dt2, f);
+                }
                 if constexpr (ST2) r = Two<T>::fma(xr2, Two<T>::mk(xx[m], xx[m + 1]), r);
                 d[m] = Two<T>::x(r);
                 d[m + 1] = Two<T>::y(r);
@@ -460,7 +470,7 @@ __device__ __forceinline__ void p1_line(const P1Inst<T>& I, const T* tl, int sl,
             const T u = uc[0], u1 = uc[1], u2 = M >= 3 ? uc[M >= 3 ? 2 : 1] : uc_next;
             const T fr = aFy * tl[RT_IJ * S * MP] + tl[RT_C4B * S * MP];  // mu_r / (2 h J) at t^n
             const T f = fr * (T(-3) * u + T(4) * u1 - u2) - tl[RT_R * S * MP] * u;
-            d[0] = dt * f + f1_0;  // f1_0: dt times the v and y parts
+            d[0] = FOLD ? dt * f + f1_0 : dt * (f + f1_0);
             if constexpr (ST2) {
                 if (I.hv) d[0] += xx[0];
             }

@@ -101,11 +101,23 @@ def test_recorded_traffic_is_keyed_by_sources_and_launch_shape():
     tile = sorted(shapes)[0]
     assert bench.recorded_traffic("pass1", "config2-fp32", 1000, "1,2,3,4,5,6,7") is None
     assert bench.recorded_traffic("pass1", "no-such-workload", 1000, tile) is None
-    got = bench.recorded_traffic("pass1", "config2-fp32", 1000, tile)
-    if d["source_digest"] == bench.source_digest():
-        assert got == shapes[tile]["kernels"]["pass1"]["dram_bytes_per_point"] * 1000
-    else:  # counters taken on other kernel sources are not reported
-        assert got is None
+    for kind, rec in shapes[tile]["kernels"].items():
+        got = bench.recorded_traffic(kind, "config2-fp32", 1000, tile)
+        if rec["source_digest"] == bench.source_digest(rec["kernel"]):
+            assert got == rec["dram_bytes_per_point"] * 1000
+        else:  # counters taken on other sources of that kernel are not reported
+            assert got is None
+
+
+def test_kernel_digests_cover_their_sources():
+    # every recorded kernel's digest reads files that exist, and a kernel's
+    # digest does not depend on another kernel's translation unit
+    for k, files in bench.KERNEL_SOURCES.items():
+        for f in files:
+            assert os.path.exists(os.path.join(ROOT, "paper_1108_1688_gb300", "csrc", f)), (k, f)
+        assert len(bench.source_digest(k)) == 16
+    assert "hjm_pass1.cu" not in bench.KERNEL_SOURCES["k_pass1t"]
+    assert "hjm_march.cu" not in bench.KERNEL_SOURCES["k_lines_t"]
 
 
 def test_pass1_fp64_operation_count():
